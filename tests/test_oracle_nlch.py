@@ -1,0 +1,250 @@
+"""Pins of the model oracle (oracle/nlch_oracle.c) against what the paper and the
+mathematics fix, independent of the oracle's own formulas."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests.conftest import read_golden
+
+
+def model(**kw):
+    base = dict(n=64, delta=4 / 64, kernel=0, eps=0.03, c_F=1.0, beta1=1.0, tau=1e-3,
+                nsteps=200, ic=0, ic_amp=0.05)
+    base.update(kw)
+    return O.OracleModel(**base)
+
+
+# --------------------------------------------------------------------------- RNG
+def test_splitmix64_reference_vector():
+    want = [int(r[0]) for r in read_golden("splitmix64_seed1234567.txt")]
+    got = [O.splitmix64(1234567, k) for k in range(1, 6)]
+    assert got == want
+
+
+def test_uniform_and_normal_moments():
+    xs = np.array([O.uniform(20231016, 1, i) for i in range(20000)])
+    assert xs.min() >= 0.0 and xs.max() < 1.0
+    assert abs(xs.mean() - 0.5) < 4 * math.sqrt(1 / 12 / len(xs))
+    m = model(n=128, ic=1, ic_amp=1.0)
+    # the smoothed field is (5 iid normals)/5 per node: variance 1/5 before clipping
+    u = m.initial_field(7)
+    assert abs(u.mean()) < 4 * math.sqrt(0.2 / u.size) * 3
+    assert abs(u.var() - 0.2) < 0.02
+
+
+def test_streams_are_distinct_windows():
+    assert O.draw(5, 0, 0) == O.splitmix64(5, 1)
+    assert O.draw(5, 1, 0) == O.splitmix64(5, (1 << 32) + 1)
+    assert O.draw(5, 2, 7) == O.splitmix64(5, (2 << 32) + 8)
+
+
+# --------------------------------------------------------------------------- disc
+def test_disc_counts_match_lattice_point_counts():
+    for R, cnt in read_golden("disc_counts.txt"):
+        dx, dy = O.disc(float(R))
+        assert len(dx) == int(cnt)
+        # brute force count in plain Python
+        Ri = int(R)
+        brute = sum(1 for i in range(-Ri, Ri + 1) for j in range(-Ri, Ri + 1) if i * i + j * j <= Ri * Ri)
+        assert brute == int(cnt)
+
+
+def test_constant_kernel_second_moment_is_4eps2():
+    # int_{B_delta} gamma |z|^2 dz = 4 eps^2, so that L -> -eps^2 Laplace (Section 4)
+    eps, delta = 0.03, 0.1
+    A = O.gamma(0, 0.0, eps, delta, delta)
+    # midpoint quadrature of the radial integral
+    N = 200000
+    r = (np.arange(N) + 0.5) * delta / N
+    moment = np.sum(A * r ** 2 * 2 * np.pi * r) * delta / N
+    assert moment == pytest.approx(4 * eps * eps, rel=1e-8)
+    assert O.gamma(0, delta * 1.01, eps, delta, delta) == 0.0
+
+
+def test_gaussian_kernel_matches_paper_xi():
+    # Section 4: c_F = 1, eps^2 = 0.00178, delta_hf = 0.25 give xi = c_gamma - c_F ~ 0.0253
+    # and c_gamma ~ 36 eps^2 / delta^2 (continuum).  The lattice c_gamma at h = 1/128
+    # must be close to the continuum value.
+    eps = math.sqrt(0.00178)
+    m = O.OracleModel(n=128, delta=0.25, kernel=1, delta_hf=0.25, eps=eps)
+    _, cg = m.weights(eps)
+    assert 36 * eps ** 2 / 0.25 ** 2 == pytest.approx(1.02528, rel=1e-4)
+    assert cg - 1.0 == pytest.approx(0.0253, abs=0.004)
+    # exact continuum value of the truncated Gaussian: (1 - e^{-9}) 4 eps^2 / s^2
+    s = 0.25 / 3
+    assert cg == pytest.approx((1 - math.exp(-9)) * 4 * eps ** 2 / s ** 2, rel=5e-3)
+
+
+# --------------------------------------------------------------------------- operator
+def test_L_vanishes_on_constants():
+    for kernel in (0, 1):
+        m = model(n=32, delta=3 / 32, kernel=kernel, delta_hf=3 / 32)
+        for c in (0.0, 1.0, -0.37, 0.123456789):
+            Lu = m.apply_L(np.full((32, 32), c), 0.03)
+            assert np.all(Lu == 0.0)
+
+
+def test_L_on_quadratic_closed_form():
+    # L_h(x^2)_i = -h^2 a sum_{z in D} dx^2 on a non-wrapping patch, with
+    # sum_{z in D} dx^2 = sum_dy w(w+1)(2w+1)/3, w = floor(sqrt(R^2 - dy^2)).
+    n, R, eps = 64, 4, 0.03
+    m = model(n=n, delta=R / n, eps=eps)
+    h = 1.0 / n
+    x = np.arange(n) * h
+    u = np.tile(x ** 2, (n, 1))
+    Lu = m.apply_L_open(u, eps)
+    A = 8 * eps * eps / (math.pi * (R * h) ** 4)
+    s2 = sum(w * (w + 1) * (2 * w + 1) // 3 for w in
+             (int(math.isqrt(R * R - dy * dy)) for dy in range(-R, R + 1)))
+    assert s2 == 192
+    closed = -h * h * (A * h * h) * s2
+    inner = Lu[R:n - R, R:n - R]
+    assert np.allclose(inner, closed, rtol=1e-12, atol=0)
+    assert closed == pytest.approx(-1.71887e-3, rel=1e-5)
+    # continuum limit -eps^2 * Laplace(x^2) = -2 eps^2 within the lattice error
+    assert closed == pytest.approx(-2 * eps * eps, rel=0.06)
+
+
+def test_L_on_fourier_modes_matches_fft_symbol():
+    n, R, eps = 32, 3, 0.03
+    for kernel in (0, 1):
+        m = model(n=n, delta=R / n, kernel=kernel, delta_hf=R / n)
+        w, cg = m.weights(eps)
+        dx, dy = m.offsets()
+        stencil = np.zeros((n, n))
+        for k in range(len(w)):
+            stencil[dy[k] % n, dx[k] % n] += w[k]
+        fft_sym = cg - np.real(np.fft.fft2(stencil))
+        yy, xx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+        for p, q in ((0, 0), (1, 0), (0, 3), (5, 7), (16, 16)):
+            mode = np.cos(2 * np.pi * (p * xx + q * yy) / n)
+            Lm = m.apply_L(mode, eps)
+            lam = m.symbol(p, q, eps)
+            assert np.allclose(Lm, lam * mode, atol=1e-13)
+            assert lam == pytest.approx(fft_sym[q, p], abs=1e-13)
+
+
+# --------------------------------------------------------------------------- step
+def test_pure_phases_and_zero_are_stationary():
+    m = model(n=32, delta=4 / 32)
+    for c in (1.0, -1.0, 0.0):
+        u = np.full((32, 32), c)
+        uT, mean = m.solve(u, 0.03, nsteps=25)
+        assert np.all(uT == c)
+
+
+def test_step_solves_the_implicit_inclusion():
+    # (u^k - u^{k-1})/tau + beta1 w = 0 with
+    # w - (c_gamma u^k - gamma*u^{k-1} - c_F u^{k-1}) in dI(u^k):
+    # zero where |u^k| < 1, >= 0 where u^k = 1, <= 0 where u^k = -1.
+    m = model(n=64, delta=4 / 64, ic=2, tau=5e-3)
+    eps = 0.03
+    u = m.initial_field(11)
+    _, cg = m.weights(eps)
+    hit_lo = hit_hi = False
+    for _ in range(40):
+        unew = m.step(u, eps)
+        w = -(unew - u) / (m.tau * m.beta1)
+        g = m.convolve(u, eps) + m.c_F * u
+        res = w - (cg * unew - g)
+        inner = np.abs(unew) < 1
+        assert np.all(np.abs(res[inner]) < 1e-10)
+        assert np.all(res[unew == 1.0] >= -1e-10)
+        assert np.all(res[unew == -1.0] <= 1e-10)
+        hit_hi |= bool((unew == 1.0).any())
+        hit_lo |= bool((unew == -1.0).any())
+        u = unew
+    assert hit_hi and hit_lo          # both sides of the obstacle were active
+
+
+def test_bounds_and_max_norm_growth():
+    m = model(n=64, delta=4 / 64, ic=0)
+    eps = 0.03
+    u0 = m.initial_field(3)
+    grow = 1 + m.tau * m.beta1 * m.c_F
+    u = u0
+    for k in range(1, 41):
+        u = m.step(u, eps)
+        assert np.abs(u).max() <= np.abs(u0).max() * grow ** k * (1 + 1e-14)
+    mn = model(n=64, delta=4 / 64, ic=2)
+    v = mn.initial_field(4)
+    for _ in range(10):
+        v = mn.step(v, eps)
+        assert np.abs(v).max() <= 1.0
+
+
+def test_step_is_lipschitz_with_factor_1_plus_tau_cF():
+    m = model(n=32, delta=3 / 32, ic=2)
+    eps = 0.03
+    a = m.initial_field(1)
+    b = m.initial_field(2)
+    d0 = np.abs(a - b).max()
+    grow = 1 + m.tau * m.beta1 * m.c_F
+    for k in range(1, 11):
+        a, b = m.step(a, eps), m.step(b, eps)
+        assert np.abs(a - b).max() <= d0 * grow ** k * (1 + 1e-13)
+
+
+def test_energy_decreases_when_splitting_condition_holds():
+    # E_h is non-increasing for the convex-concave splitting when the explicit part
+    # (gamma * + c_F) is positive semidefinite: min over modes of the stencil DFT >= -c_F.
+    for ic in (0, 2):
+        m = model(n=32, delta=4 / 32, ic=ic, tau=2e-2, ic_amp=0.5)
+        eps = 0.03
+        w, _ = m.weights(eps)
+        dx, dy = m.offsets()
+        st = np.zeros((32, 32))
+        for k in range(len(w)):
+            st[dy[k] % 32, dx[k] % 32] += w[k]
+        assert np.real(np.fft.fft2(st)).min() >= -m.c_F
+        u = m.initial_field(9)
+        e = m.energy(u, eps)
+        for _ in range(30):
+            u = m.step(u, eps)
+            e2 = m.energy(u, eps)
+            assert e2 <= e + 1e-14
+            e = e2
+
+
+def test_ooi_values():
+    n = 16
+    assert O.ooi(np.ones((n, n))) == 1.0
+    assert O.ooi(-np.ones((n, n))) == 0.0
+    u = np.ones((n, n))
+    u[:, : n // 2] = -1
+    assert O.ooi(u) == 0.5
+
+
+# --------------------------------------------------------------------------- ICs
+def test_nuclei_initial_condition():
+    m = model(n=128, ic=2)
+    mu = np.array([0.9815, 0.9276, 0.9162, 0.9417])
+    eta = np.array([[0.0072, -0.0039], [0.0232, 0.0208], [-0.0220, 0.0041], [-0.0099, 0.0118]])
+    u = m.initial_field(0, theta=(mu, eta))
+    assert np.abs(u).max() <= 1.0
+    # far from the four nuclei the field is ~1; at a nucleus centre it is 1 - 2 mu (to
+    # within the other nuclei's tails), and the four nuclei have area in phase -1
+    assert u[0, 0] == pytest.approx(1.0, abs=1e-3)
+    # nucleus 1 at (0.25, 0.5) + eta_1, nearest node
+    iy, ix = round((0.5 + eta[0, 1]) * 128), round((0.25 + eta[0, 0]) * 128)
+    # own Gaussian gives at most 1 - 2 mu_1 exp(-36 d^2) with d <= h/sqrt(2) to the node;
+    # the other nuclei's tails only lower it further, and the clip keeps it >= -1
+    h = 1 / 128
+    assert -1.0 <= u[iy, ix] <= 1 - 2 * mu[0] * math.exp(-36 * h * h / 2) + 1e-12
+    assert (u < 0).sum() > 4 * 50
+    mu2, eta2 = m.draw_theta(5)
+    assert np.all((mu2 >= 0.9) & (mu2 <= 1.0)) and np.all(np.abs(eta2) <= 0.025)
+
+
+def test_uniform_ic_and_rounding_to_fp32():
+    m = model(n=32, ic=0, ic_amp=0.05)
+    u = m.initial_field(20231016)
+    assert np.abs(u).max() <= 0.05
+    assert np.all(u.astype(np.float32).astype(np.float64) == u)
+    eps = m.sample_eps(1)
+    assert eps == 0.03
+    m2 = model(eps_lo=0.024, eps_hi=0.036)
+    e2 = m2.sample_eps(1)
+    assert 0.024 <= e2 <= 0.036 and e2 == 0.024 + 0.012 * O.uniform(1, 0, 0)
