@@ -66,7 +66,7 @@ def lib():
                                  ctypes.c_int]
         L.orc_initial_field.restype = None
         L.orc_initial_field.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                        ctypes.c_uint64, _dp, _dp, _dp]
+                                        ctypes.c_uint64, _dp, _dp, ctypes.c_int, _dp]
         L.orc_draw_theta.restype = None
         L.orc_draw_theta.argtypes = [ctypes.c_uint64, _dp, _dp]
         L.orc_sample_eps.restype = ctypes.c_double
@@ -135,6 +135,7 @@ class OracleModel:
     nsteps: int = 200
     ic: int = 0                # 0 uniform, 1 smoothed Gaussian noise, 2 four nuclei
     ic_amp: float = 0.05
+    ic_base_n: int = 0         # noise ICs: base lattice of the shared random field (0 = n)
     _disc: Optional[tuple] = field(default=None, repr=False)
 
     @property
@@ -171,7 +172,8 @@ class OracleModel:
                 mu[:] = theta[0]
                 eta[:] = np.asarray(theta[1], dtype=np.float64).reshape(8)
         u0 = np.zeros(self.n * self.n)
-        lib().orc_initial_field(self.n, self.ic, self.ic_amp, seed, _d(mu), _d(eta), _d(u0))
+        lib().orc_initial_field(self.n, self.ic, self.ic_amp, seed, _d(mu), _d(eta),
+                                self.ic_base_n, _d(u0))
         return u0.reshape(self.n, self.n)
 
     def draw_theta(self, seed: int):

@@ -229,27 +229,50 @@ static double orc_clip1(double v) { return v > 1.0 ? 1.0 : (v < -1.0 ? -1.0 : v)
 /* ic 1: Gaussian noise amp * N(0,1) (stream 1, two draws per node), averaged with its
  *       four periodic lattice neighbours, (c + left + right + down + up)/5 in that order,
  *       then clipped to [-1, 1]. */
+/* For ic 0 and 1 the random field is drawn on a base lattice of base_n = b*n points per
+ * side (b >= 1); the node (y, x) of the n-lattice takes the mean of the b x b base
+ * nodes (b y + a, b x + c), a, c in [-(b/2), b - b/2), summed a-major in FP64.  With
+ * b = 1 this is the field itself.  Models of different n then share one random input. */
 /* ic 2: Eq. (ic), four nuclei: u0 = 1 - 2 sum_i mu_i exp(-36 |x - xbar_i - eta_i|^2),
  *       with the minimum-image distance on the unit torus, nodes at (j h, i h), and
  *       the result clipped to [-1, 1].  theta = (mu_i, eta_i) is passed in. */
-void orc_initial_field(int n, int ic, double amp, uint64_t seed, const double *mu,
-                       const double *eta, double *u0) {
-    long N = (long)n * n;
+static void orc_noise_field(int N, int ic, double amp, uint64_t seed, double *f) {
+    long NN = (long)N * N;
     if (ic == 0) {
-        for (long i = 0; i < N; ++i) u0[i] = amp * (2.0 * orc_uniform(seed, 1, (uint32_t)i) - 1.0);
-    } else if (ic == 1) {
-        double *z = (double *)malloc(sizeof(double) * N);
-        for (long i = 0; i < N; ++i) z[i] = amp * orc_normal(seed, 1, (uint32_t)i);
+        for (long i = 0; i < NN; ++i) f[i] = amp * (2.0 * orc_uniform(seed, 1, (uint32_t)i) - 1.0);
+        return;
+    }
+    double *z = (double *)malloc(sizeof(double) * NN);
+    for (long i = 0; i < NN; ++i) z[i] = amp * orc_normal(seed, 1, (uint32_t)i);
+    for (int y = 0; y < N; ++y)
+        for (int x = 0; x < N; ++x) {
+            double s = z[y * N + x];
+            s += z[y * N + orc_wrap(x - 1, N)];
+            s += z[y * N + orc_wrap(x + 1, N)];
+            s += z[orc_wrap(y - 1, N) * N + x];
+            s += z[orc_wrap(y + 1, N) * N + x];
+            f[y * N + x] = orc_clip1(s / 5.0);
+        }
+    free(z);
+}
+
+void orc_initial_field(int n, int ic, double amp, uint64_t seed, const double *mu,
+                       const double *eta, int base_n, double *u0) {
+    long N = (long)n * n;
+    if (ic == 0 || ic == 1) {
+        int B = base_n > 0 ? base_n : n;
+        int b = B / n;
+        double *f = (double *)malloc(sizeof(double) * (size_t)B * B);
+        orc_noise_field(B, ic, amp, seed, f);
         for (int y = 0; y < n; ++y)
             for (int x = 0; x < n; ++x) {
-                double s = z[y * n + x];
-                s += z[y * n + orc_wrap(x - 1, n)];
-                s += z[y * n + orc_wrap(x + 1, n)];
-                s += z[orc_wrap(y - 1, n) * n + x];
-                s += z[orc_wrap(y + 1, n) * n + x];
-                u0[y * n + x] = orc_clip1(s / 5.0);
+                double s = 0.0;
+                for (int a = -(b / 2); a < b - b / 2; ++a)
+                    for (int c = -(b / 2); c < b - b / 2; ++c)
+                        s += f[orc_wrap(b * y + a, B) * B + orc_wrap(b * x + c, B)];
+                u0[y * n + x] = s / ((double)b * (double)b);
             }
-        free(z);
+        free(f);
     } else {
         static const double cx[4] = {0.25, 0.75, 0.5, 0.5};
         static const double cy[4] = {0.5, 0.5, 0.25, 0.75};
