@@ -1,0 +1,251 @@
+/*
+ * mfmc.h - C ABI of libmfmc: batched GPU time integration of the nonlocal,
+ * non-mass-conserving Cahn-Hilliard model with obstacle potential, and the
+ * multifidelity Monte Carlo (MFMC) estimator on top (arXiv 2310.10750).
+ *
+ * Conventions shared by every call:
+ *   - Every call returns an mfmc_status.  No C++ exception crosses this boundary.
+ *     On failure, mfmc_last_error() returns a message for the calling thread.
+ *   - Handles (mfmc_model*, mfmc_server*) are owned by the library and released by
+ *     the matching *_destroy call.  All other buffers are owned by the caller.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA device
+ *     memory of the current device.  `stream` is a cudaStream_t (NULL = default
+ *     stream).  Calls with device pointers are asynchronous on `stream`; calls with
+ *     host output pointers return after the result has been copied back.
+ *   - Fields are FP32, row-major [sample][y][x] with x fastest, n*n values each.
+ *   - A device-side wait that runs out of its iteration limit returns
+ *     MFMC_ETIMEOUT; the context stays usable.
+ */
+#ifndef MFMC_H
+#define MFMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MFMC_OK = 0,
+    MFMC_EINVAL = 1,     /* invalid argument or descriptor                         */
+    MFMC_ENOMEM = 2,     /* device or host allocation failed                       */
+    MFMC_ECUDA = 3,      /* a CUDA runtime call failed                             */
+    MFMC_ETIMEOUT = 4,   /* a bounded device-side wait gave up                     */
+    MFMC_EBUDGET = 5,    /* the MFMC budget admits no subset (Section 4)           */
+    MFMC_EBUSY = 6,      /* serving: the request is not finished yet               */
+    MFMC_ENOTFOUND = 7   /* serving: unknown ticket                                */
+} mfmc_status;
+
+/* Kernel gamma of Eq. (nonl_operator).
+ *   CONSTANT: gamma = 8 eps^2 / (pi delta^4) on the disc |z| <= delta, the constant
+ *             whose second moment is 4 eps^2, so that L u -> -eps^2 Laplace u as
+ *             delta -> 0 (the scaling Section 4 states for its kernel).
+ *   GAUSSIAN: Eq. (kernel_gauss), 4 eps^2 / (pi s^4) exp(-|z|^2 / s^2), s = delta_hf/3,
+ *             truncated at delta.  The printed prefactor has s^3; s^4 is the value
+ *             with the same second moment and the paper's c_gamma ~ 36 eps^2/delta^2. */
+typedef enum { MFMC_KERNEL_CONSTANT = 0, MFMC_KERNEL_GAUSSIAN = 1 } mfmc_kernel;
+
+/* Boundary: the periodic unit torus (the interaction collar of Section 2 is not
+ * modelled). */
+typedef enum { MFMC_BC_PERIODIC = 0 } mfmc_boundary;
+
+/* Initial field built on the device from a 64-bit seed (SplitMix64, one counter per
+ * draw: draw i of stream k is output number k*2^32 + i + 1 of the sequence started at
+ * the seed).
+ *   UNIFORM:        u0 i.i.d. U[-ic_amp, ic_amp]                            (stream 1)
+ *   SMOOTHED_GAUSS: ic_amp * N(0,1) noise (Box-Muller), averaged with the four
+ *                   periodic neighbours, clipped to [-1, 1]                 (stream 1)
+ *   NUCLEI:         Eq. (ic), four nuclei of phase -1 at (0.25,0.5), (0.75,0.5),
+ *                   (0.5,0.25), (0.5,0.75) shifted by eta_i, depth mu_i; theta drawn
+ *                   from U[0.9,1] x U[-0.025,0.025]^2 (stream 2) unless given; clipped.
+ * Fields are built in FP64 and rounded to FP32. */
+typedef enum { MFMC_IC_UNIFORM = 0, MFMC_IC_SMOOTHED_GAUSS = 1, MFMC_IC_NUCLEI = 2 } mfmc_ic;
+
+/* Disc-sum algorithm of the step kernel. AUTO lets the autotuner pick and cache. */
+typedef enum {
+    MFMC_ALGO_AUTO = 0,
+    MFMC_ALGO_DIRECT = 1,      /* sum over every disc point                       */
+    MFMC_ALGO_PREFIX = 2,      /* in-register row prefix sums: O(R) adds per point */
+    MFMC_ALGO_PREFIX_KAHAN = 3,/* prefix form with compensated accumulation       */
+    MFMC_ALGO_RESIDENT = 4,    /* whole field held in shared memory for all steps */
+    MFMC_ALGO_PLAIN = 5        /* reference form: one sample per launch, direct   */
+} mfmc_algo;
+
+/* One fidelity of the model (Section 2, Section 4).  The lattice is n x n on the unit
+ * torus, h = 1/n.  delta/h must be an integer R within 1e-9 (1 <= R <= 32) and
+ * n % 4 == 0 and n >= 8.  beta2 must be 0 (the nonlocal Allen-Cahn limit of
+ * Eq. (nonl_CH_nm) whose step is the pointwise projection onto [-1, 1]). */
+typedef struct {
+    int n;                 /* lattice points per side                              */
+    double delta;          /* horizon                                              */
+    mfmc_kernel kernel;
+    double delta_hf;       /* Gaussian width reference (kernel GAUSSIAN only)      */
+    double eps;            /* interface parameter eps (nominal)                    */
+    double eps_lo, eps_hi; /* if eps_hi > eps_lo: per-sample eps ~ U[eps_lo,eps_hi]
+                              drawn from stream 0 of the seed                     */
+    double c_F;            /* obstacle potential constant, Eq. (potential_obstacle) */
+    double beta1, beta2;   /* Eq. (nonl_CH_nm); beta1 > 0, beta2 == 0              */
+    double tau;            /* time step                                            */
+    int nsteps;            /* number of steps, T = nsteps * tau                    */
+    mfmc_boundary bc;
+    mfmc_ic ic;
+    double ic_amp;         /* amplitude / standard deviation of the noise ICs      */
+    int ic_base_n;         /* noise ICs: lattice the random field is drawn on
+                              (0 = n).  A multiple b*n: u0 at a node is the mean of
+                              the b x b block of base-lattice IC values, so models
+                              of different n share one random input per seed.     */
+    mfmc_algo algo;
+} mfmc_model_desc;
+
+/* Per-sample parameters (all optional).  eps <= 0 means "from the model" (the nominal
+ * eps, or the per-sample draw when the model has an eps range).  has_theta = 0 draws
+ * theta = (mu_i, eta_i) of Eq. (ic) from the seed. */
+typedef struct {
+    double eps;
+    int has_theta;
+    double mu[4];
+    double eta[4][2];
+} mfmc_sample_params;
+
+/* Derived constants of a model (nominal eps). */
+typedef struct {
+    int R;                 /* delta / h                                            */
+    int disc_points;       /* |D| = #{z in Z^2 : |z| <= R}                          */
+    double c_gamma;        /* sum_z h^2 gamma(|z| h), the lattice c_gamma           */
+    double xi;             /* c_gamma - c_F, Eq. (xi_constant)                      */
+    int algo;              /* mfmc_algo the solver uses for this model             */
+    size_t field_bytes;    /* n * n * 4                                             */
+} mfmc_model_info;
+
+typedef struct mfmc_model mfmc_model;
+typedef struct mfmc_server mfmc_server;
+
+/* Library version string; never NULL. */
+const char *mfmc_version(void);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *mfmc_last_error(void);
+
+/* Validate a descriptor and create a model handle (host-side only; no device work).
+ * Returns MFMC_EINVAL for: NULL pointers, n % 4 != 0 or n < 8, delta/h not an
+ * integer in [1, 32], tau <= 0, beta1 <= 0, beta2 != 0, eps <= 0, c_F < 0, nsteps < 0,
+ * an unknown kernel/ic/algo/bc, or a GAUSSIAN kernel with delta_hf <= 0. */
+mfmc_status mfmc_model_create(const mfmc_model_desc *desc, mfmc_model **out);
+
+/* Release a model handle (NULL is ignored). */
+void mfmc_model_destroy(mfmc_model *model);
+
+/* Derived constants of a model. */
+mfmc_status mfmc_model_query(const mfmc_model *model, mfmc_model_info *out);
+
+/* Host-side resolution of each sample's eps (model eps, eps range draw, or
+ * params[i].eps), ns values into eps_out (host). params may be NULL. */
+mfmc_status mfmc_sample_eps(const mfmc_model *model, const mfmc_sample_params *params,
+                            const uint64_t *seeds, size_t ns, double *eps_out);
+
+/* Build ns initial fields on the device from host seeds[ns] (and optional host
+ * params[ns]) into device u0[ns][n][n].  Section 4, Eq. (ic) for NUCLEI. */
+mfmc_status mfmc_init_fields(const mfmc_model *model, const mfmc_sample_params *params,
+                             const uint64_t *seeds, size_t ns, float *u0, void *stream);
+
+/* The hot path.  Advance ns fields of one model by model->nsteps steps of the scheme
+ *   u^k = P_[-1,1]( (u^{k-1} + tau beta1 (gamma*u^{k-1} + c_F u^{k-1}))
+ *                   / (1 + tau beta1 c_gamma) )
+ * (Eq. (nonl_CH_nm) with beta2 = 0, implicit Euler with the convolution explicit as
+ * Section 4 states, the convex part c_gamma u + dI implicit), and reduce the output of
+ * interest f = (1 + mean u(T)) / 2 (Eq. (ooi)).
+ *   eps   device, ns per-sample eps values, or NULL for the nominal eps
+ *   u0    device, [ns][n][n] FP32, read only
+ *   uT    device, [ns][n][n] FP32 final fields, or NULL
+ *   ubar  device, ns FP64 spatial means of u(T), or NULL
+ *   ooi   device, ns FP64 outputs of interest, or NULL
+ * Scratch (two field buffers for the streaming kernels) is owned by the library and
+ * reused across calls.  ns == 0 is a no-op. */
+mfmc_status mfmc_solve_fields(const mfmc_model *model, const double *eps, const float *u0,
+                              size_t ns, float *uT, double *ubar, double *ooi, void *stream);
+
+/* Same as mfmc_solve_fields with an explicit algorithm (for measurements and the
+ * reference form MFMC_ALGO_PLAIN: one sample per launch, one launch per step). */
+mfmc_status mfmc_solve_fields_algo(const mfmc_model *model, int algo, const double *eps,
+                                   const float *u0, size_t ns, float *uT, double *ubar,
+                                   double *ooi, void *stream);
+
+/* The user-level batch call (Section 3 problem statement: OoI of model f_k at
+ * parameter samples).  Sample i uses models[i], seeds[i] and params[i] (params may
+ * be NULL); samples of different models run in the same call.  Host outputs:
+ * ooi_out[ns] and, if not NULL, ubar_out[ns].  Synchronous. */
+mfmc_status mfmc_solve_batch(mfmc_model *const *models, const mfmc_sample_params *params,
+                             const uint64_t *seeds, size_t ns, double *ooi_out,
+                             double *ubar_out);
+
+/* ---------------------------------------------------------------- MFMC (Section 3) */
+
+#define MFMC_MAX_MODELS 16
+
+/* A model selection and sample allocation.  Indices are 0-based model numbers;
+ * idx[0] == 0 is the high-fidelity model f_1.  Arrays are indexed by the position j
+ * in the selected subset (0-based).  alpha[0] = 1. */
+typedef struct {
+    int K_sel;                        /* |S|                                     */
+    int idx[MFMC_MAX_MODELS];         /* i_j                                     */
+    double rho[MFMC_MAX_MODELS];      /* rho_{1,i_j}                             */
+    double sigma[MFMC_MAX_MODELS];    /* sigma_{i_j}                             */
+    double cost[MFMC_MAX_MODELS];     /* C_{i_j}                                 */
+    double alpha[MFMC_MAX_MODELS];    /* Eq. (alpha)                             */
+    double r[MFMC_MAX_MODELS];        /* Eq. (rk)                                */
+    double m_real[MFMC_MAX_MODELS];   /* Eq. (samples) or the below-B_min branch  */
+    int64_t m[MFMC_MAX_MODELS];       /* floor(m_real)                           */
+    double V;                         /* Eq. (variance_reduction_ratio)          */
+    double Bmin;                      /* Eq. (bmin)                              */
+    double mse_theory;                /* Eq. (error_theory)                      */
+    double budget;
+    int below_min_budget;             /* 1 if the Section 4 branch was used      */
+    int n_feasible;                   /* feasible subsets, Eqs. (conditiona/b)   */
+    int n_models;                     /* K                                       */
+    double rho_all[MFMC_MAX_MODELS];  /* rho_{1,k} of every model                */
+    double sigma_all[MFMC_MAX_MODELS];/* sigma_k of every model                  */
+    double mean_all[MFMC_MAX_MODELS]; /* pilot mean of every model               */
+} mfmc_plan_t;
+
+/* Pilot statistics in FP64 on the GPU (Section 3.1): for K models on the same n
+ * pilot samples, device ooi[K][n] -> host mean[K], sigma[K] (n-1 convention) and
+ * rho[K] = Cov(f_1, f_k) / (sigma_1 sigma_k).  Deterministic reduction order. */
+mfmc_status mfmc_pilot_stats(int K, int n, const double *ooi_dev, double *mean,
+                             double *sigma, double *rho, void *stream);
+
+/* Model selection and allocation (Section 3): pilot OoIs (host [K][n_pilot], model 0
+ * is f_1), costs (host [K], any unit consistent with budget), budget B.
+ * Policies: 0 smallest V with B >= B_min, else the smallest-V subset that admits the
+ * below-minimum-budget branch of Section 4; 1 smallest V regardless of B_min (Case 1);
+ * 2 smallest B_min (Case 3); 3 the explicit subset (explicit_idx[0..explicit_len-1],
+ * starting with 0).  Returns MFMC_EBUDGET when no subset fits B (the Section 4
+ * requirement B >= sum_l l C_{i_l}). */
+mfmc_status mfmc_plan(int K, int n_pilot, const double *pilot_ooi, const double *costs,
+                      double budget, int policy, const int *explicit_idx, int explicit_len,
+                      mfmc_plan_t *out);
+
+/* Eq. (MFMC_estimator) in FP64 on the GPU: ooi[j] (host) holds model i_j on the
+ * shared sample sequence, at least m_j values; Q^{(i_j)}_m is the mean of the first m.
+ * Writes the estimate to *estimate (host). */
+mfmc_status mfmc_estimate(const mfmc_plan_t *plan, const double *const *ooi,
+                          double *estimate);
+
+/* Device variant: ooi_dev[j] device pointers, estimate_dev a device double. */
+mfmc_status mfmc_estimate_device(const mfmc_plan_t *plan, const double *const *ooi_dev,
+                                 double *estimate_dev, void *stream);
+
+/* Pilot -> plan -> allocated solves -> estimate, all samples on the GPU.
+ * models[K] (models[0] = f_1); pilot seeds are seed_base + 0..n_pilot-1 and the
+ * estimation seeds are seed_base + n_pilot + 0..m_j-1 (nested, disjoint from the
+ * pilot).  costs (host [K]) may be NULL: then each model's cost is measured as GPU
+ * seconds per sample from the pilot solve.  Outputs plan_out and *estimate (host). */
+mfmc_status mfmc_run(mfmc_model *const *models, int K, int n_pilot, double budget,
+                     int policy, uint64_t seed_base, const double *costs,
+                     mfmc_plan_t *plan_out, double *estimate);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MFMC_H */

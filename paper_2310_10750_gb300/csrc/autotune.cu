@@ -1,0 +1,86 @@
+// Autotuner: for a model whose algorithm is AUTO, time every candidate disc-sum
+// algorithm on a batch large enough to fill the GPU and keep the fastest.  Results are
+// cached per (n, R, kernel) for the life of the process.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "mfmc_internal.h"
+
+namespace mfmc {
+
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int>, int> g_tune_cache;
+
+mfmc_status autotune(Model &m, cudaStream_t st) {
+    const auto key = std::make_tuple(m.d.n, m.R, (int)m.d.kernel);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            m.algo = it->second;
+            m.tuned = 1;
+            return MFMC_OK;
+        }
+    }
+    std::vector<int> cands;
+    for (int a : {MFMC_ALGO_RESIDENT, MFMC_ALGO_PREFIX, MFMC_ALGO_DIRECT})
+        if (algo_supported(m, a)) cands.push_back(a);
+    int best = cands.empty() ? MFMC_ALGO_DIRECT : cands[0];
+    if (cands.size() > 1) {
+        const size_t nn = (size_t)m.d.n * m.d.n;
+        const size_t ns = std::max<size_t>(8, std::min<size_t>(1216, (size_t)(64u << 20) / nn));
+        const int steps = std::max(1, std::min(m.d.nsteps, 16));
+        float *u0 = nullptr;
+        StepCoef *coef = nullptr;
+        double *ooi = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        mfmc_status s = MFMC_OK;
+        cudaError_t e = cudaMalloc((void **)&u0, ns * nn * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&coef, ns * sizeof(StepCoef));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&ooi, ns * sizeof(double));
+        if (e == cudaSuccess) e = cudaMemsetAsync(u0, 0, ns * nn * sizeof(float), st);
+        if (e == cudaSuccess) e = cudaEventCreate(&e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&e1);
+        if (e != cudaSuccess) s = cuda_fail(e, "autotune setup");
+        if (s == MFMC_OK) s = launch_coefficients(m, nullptr, ns, coef, st);
+        float best_ms = 1e30f;
+        for (int a : cands) {
+            if (s != MFMC_OK) break;
+            s = run_solve(m, a, coef, u0, ns, steps, nullptr, nullptr, ooi, st);  // warm-up
+            float ms_min = 1e30f;
+            for (int rep = 0; rep < 3 && s == MFMC_OK; ++rep) {
+                cudaEventRecord(e0, st);
+                s = run_solve(m, a, coef, u0, ns, steps, nullptr, nullptr, ooi, st);
+                cudaEventRecord(e1, st);
+                e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) s = cuda_fail(e, "autotune timing");
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms_min = std::min(ms_min, ms);
+            }
+            if (s == MFMC_OK && ms_min < best_ms) {
+                best_ms = ms_min;
+                best = a;
+            }
+        }
+        cudaStreamSynchronize(st);
+        cudaFree(u0);
+        cudaFree(coef);
+        cudaFree(ooi);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (s != MFMC_OK) return s;
+    }
+    m.algo = best;
+    m.tuned = 1;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+    return MFMC_OK;
+}
+
+}  // namespace mfmc

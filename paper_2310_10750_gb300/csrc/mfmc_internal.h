@@ -1,0 +1,140 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "mfmc.h"
+
+namespace mfmc {
+
+constexpr int kMaxR = 32;
+constexpr int kMaxNs = 1 << 24;
+
+// Step coefficients of one sample.  With S = sum_z what_z u_{i+z} (what_z = 1 for the
+// constant kernel, the Gaussian weight / eps^2 otherwise) the update is
+//   v = u + c1 * (S - c0 * u) + c2 * u,   u_new = min(1, max(-1, v)),
+// where c0 = sum_z what_z, c1 = tau beta1 eps^2 ahat / (1 + tau beta1 c_gamma),
+// c2 = tau beta1 c_F / (1 + tau beta1 c_gamma) and c_gamma = eps^2 ahat c0.
+// This is the scheme (u + tau beta1 (gamma*u + c_F u)) / (1 + tau beta1 c_gamma)
+// rearranged so that the increment is formed from small terms.
+struct StepCoef {
+    float c0, c1, c2, pad;
+};
+
+// A validated model: descriptor plus derived constants.
+struct Model {
+    mfmc_model_desc d;
+    int R;                    // delta / h
+    int disc;                 // |D_R|
+    int widths[kMaxR + 1];    // w(|dy|) = floor(sqrt(R^2 - dy^2))
+    double ahat;              // gamma h^2 / eps^2 at r = 0 for the constant kernel, 1 for Gaussian
+    std::vector<float> wtab;  // Gaussian: weight / eps^2 per r2 = dx^2 + dy^2 (0..R^2)
+    double chat;              // sum_z what_z (FP64)
+    int algo;                 // resolved algorithm (never AUTO after the autotuner ran)
+    int tuned;                // 1 once AUTO was resolved
+    // library-owned scratch, reused across calls on this model
+    std::mutex mu;
+    float *bufA = nullptr, *bufB = nullptr;
+    size_t buf_cap = 0;       // samples
+    double *partials = nullptr;
+    size_t partials_cap = 0;  // doubles
+    StepCoef *coef = nullptr;
+    size_t coef_cap = 0;
+    float *d_wtab = nullptr;
+    double *eps_tmp = nullptr;
+    size_t eps_cap = 0;
+    uint64_t *seeds_tmp = nullptr;
+    double *theta_tmp = nullptr;
+    size_t seeds_cap = 0;
+    // buffers of the batch call (initial fields and results), and its stream
+    float *u0buf = nullptr;
+    size_t u0_cap = 0;
+    double *resbuf = nullptr;
+    size_t res_cap = 0;
+    cudaStream_t stream = nullptr;
+    ~Model();
+};
+
+// error helpers (thread-local message)
+void set_error(const char *fmt, ...);
+mfmc_status fail(mfmc_status s, const char *fmt, ...);
+mfmc_status cuda_fail(cudaError_t e, const char *what);
+
+#define MFMC_CUDA(call)                                                   \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) return ::mfmc::cuda_fail(e_, #call);       \
+    } while (0)
+
+// SplitMix64, library side (Steele, Lea & Flood 2014): draw i of stream k of a seed is
+// output number k * 2^32 + i + 1 of the sequence whose state starts at the seed.
+__host__ __device__ inline uint64_t sm64_finalize(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+__host__ __device__ inline uint64_t sm64_draw(uint64_t seed, uint32_t stream, uint32_t i) {
+    const uint64_t pos = ((uint64_t)stream << 32) + (uint64_t)i + 1ULL;
+    return sm64_finalize(seed + pos * 0x9E3779B97F4A7C15ULL);
+}
+__host__ __device__ inline double sm64_unit(uint64_t seed, uint32_t stream, uint32_t i) {
+    return (double)(sm64_draw(seed, stream, i) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// Per-sample eps on the host: params, else the model's range draw, else nominal.
+double resolve_eps(const Model &m, const mfmc_sample_params *p, uint64_t seed);
+// Per-sample theta (mu[4], eta[8]) on the host: params or a draw from stream 2.
+void resolve_theta(const mfmc_sample_params *p, uint64_t seed, double theta[12]);
+
+template <typename T>
+mfmc_status grow_buffer(T **p, size_t *cap, size_t want) {
+    if (*cap >= want && *p) return MFMC_OK;
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (want == 0) return MFMC_OK;
+    cudaError_t e = cudaMalloc((void **)p, want * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(e, "cudaMalloc (scratch)");
+    }
+    *cap = want;
+    return MFMC_OK;
+}
+
+// Grow the model's scratch to hold ns samples (fields + partials + coefficients).
+mfmc_status ensure_scratch(Model &m, size_t ns, size_t partials_per_sample);
+
+// kernels (launch helpers), all asynchronous on `st`
+mfmc_status launch_init_fields(const Model &m, const uint64_t *seeds_dev,
+                               const double *theta_dev, size_t ns, float *u0, cudaStream_t st);
+mfmc_status launch_coefficients(const Model &m, const double *eps_dev, size_t ns,
+                                StepCoef *coef, cudaStream_t st);
+// Full solve with an explicit algorithm; scratch from the model.
+mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0, size_t ns,
+                      int nsteps, float *uT, double *ubar, double *ooi, cudaStream_t st);
+// Whether an algorithm can run this model.
+bool algo_supported(const Model &m, int algo);
+// Autotuner: time the candidate algorithms on this model once and cache the winner.
+mfmc_status autotune(Model &m, cudaStream_t st);
+
+// FP64 statistics / estimator kernels
+mfmc_status launch_pilot_stats(int K, int n, const double *ooi, double *out_dev,
+                               cudaStream_t st);
+mfmc_status launch_estimate(int K, const double *const *ooi_dev_list_dev,
+                            const int64_t *m_dev, const double *alpha_dev, double *est_dev,
+                            cudaStream_t st);
+
+// host planner (FP64)
+mfmc_status plan_from_stats(int K, const double *mean, const double *sigma,
+                            const double *rho, const double *costs, double budget, int policy,
+                            const int *explicit_idx, int explicit_len, mfmc_plan_t *out);
+
+}  // namespace mfmc
+
+struct mfmc_model : public mfmc::Model {};

@@ -1,0 +1,382 @@
+// Initial fields, step coefficients, the generic (any R, any radial kernel) step kernel,
+// the OoI finalisation and the solve drivers for every algorithm.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "mfmc_internal.h"
+#include "step_kernels.cuh"
+
+namespace mfmc {
+
+// ----------------------------------------------------------------------------- ICs
+// Built in FP64 with explicitly rounded operations (no contraction) and rounded to FP32.
+__device__ double ic_normal(uint64_t seed, uint32_t q) {
+    const double u1 = __dsub_rn(1.0, sm64_unit(seed, 1, 2u * q));
+    const double u2 = sm64_unit(seed, 1, 2u * q + 1u);
+    return __dmul_rn(sqrt(__dmul_rn(-2.0, log(u1))),
+                     cos(__dmul_rn(__dmul_rn(2.0, 3.141592653589793), u2)));
+}
+
+__device__ __forceinline__ double clip1(double v) { return v > 1.0 ? 1.0 : (v < -1.0 ? -1.0 : v); }
+
+// Base-lattice value of the noise ICs at node (Y, X) of the N x N lattice.
+__device__ double noise_base(int N, int ic, double amp, uint64_t seed, int Y, int X) {
+    const uint32_t p = (uint32_t)(Y * N + X);
+    if (ic == MFMC_IC_UNIFORM) return __dmul_rn(amp, __dsub_rn(__dmul_rn(2.0, sm64_unit(seed, 1, p)), 1.0));
+    const int xm = X == 0 ? N - 1 : X - 1, xp = X == N - 1 ? 0 : X + 1;
+    const int ym = Y == 0 ? N - 1 : Y - 1, yp = Y == N - 1 ? 0 : Y + 1;
+    double s = __dmul_rn(amp, ic_normal(seed, p));
+    s = __dadd_rn(s, __dmul_rn(amp, ic_normal(seed, (uint32_t)(Y * N + xm))));
+    s = __dadd_rn(s, __dmul_rn(amp, ic_normal(seed, (uint32_t)(Y * N + xp))));
+    s = __dadd_rn(s, __dmul_rn(amp, ic_normal(seed, (uint32_t)(ym * N + X))));
+    s = __dadd_rn(s, __dmul_rn(amp, ic_normal(seed, (uint32_t)(yp * N + X))));
+    return clip1(__ddiv_rn(s, 5.0));
+}
+
+__global__ void init_fields_kernel(int n, int ic, double amp, int base_n, const uint64_t *seeds,
+                                   const double *theta, size_t ns, float *u0) {
+    const size_t nn = (size_t)n * n;
+    const size_t total = nn * ns;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t smp = idx / nn;
+        const uint32_t p = (uint32_t)(idx - smp * nn);
+        const int y = p / n, x = p - (p / n) * n;
+        const uint64_t seed = seeds[smp];
+        double v;
+        if (ic == MFMC_IC_UNIFORM || ic == MFMC_IC_SMOOTHED_GAUSS) {
+            // mean of the b x b block of base-lattice values around the node
+            const int B = base_n, b = base_n / n;
+            double s = 0.0;
+            for (int a = -(b / 2); a < b - b / 2; ++a) {
+                int Y = b * y + a;
+                Y = Y < 0 ? Y + B : (Y >= B ? Y - B : Y);
+                for (int c = -(b / 2); c < b - b / 2; ++c) {
+                    int X = b * x + c;
+                    X = X < 0 ? X + B : (X >= B ? X - B : X);
+                    s = __dadd_rn(s, noise_base(B, ic, amp, seed, Y, X));
+                }
+            }
+            v = __ddiv_rn(s, __dmul_rn((double)b, (double)b));
+        } else {
+            // Eq. (ic): 1 - 2 sum_i mu_i exp(-36 |x - xbar_i - eta_i|^2), minimum image
+            const double cx[4] = {0.25, 0.75, 0.5, 0.5};
+            const double cy[4] = {0.5, 0.5, 0.25, 0.75};
+            const double *th = theta + smp * 12;
+            const double h = 1.0 / n;
+            double s = 0.0;
+            for (int k = 0; k < 4; ++k) {
+                double ddx = __dsub_rn(__dmul_rn((double)x, h), __dadd_rn(cx[k], th[4 + 2 * k]));
+                double ddy = __dsub_rn(__dmul_rn((double)y, h), __dadd_rn(cy[k], th[5 + 2 * k]));
+                ddx = __dsub_rn(ddx, floor(__dadd_rn(ddx, 0.5)));
+                ddy = __dsub_rn(ddy, floor(__dadd_rn(ddy, 0.5)));
+                const double r2 = __dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy));
+                s = __dadd_rn(s, __dmul_rn(th[k], exp(__dmul_rn(-36.0, r2))));
+            }
+            v = clip1(__dsub_rn(1.0, __dmul_rn(2.0, s)));
+        }
+        u0[idx] = (float)v;
+    }
+}
+
+mfmc_status launch_init_fields(const Model &m, const uint64_t *seeds_dev, const double *theta_dev,
+                               size_t ns, float *u0, cudaStream_t st) {
+    if (ns == 0) return MFMC_OK;
+    const size_t total = (size_t)m.d.n * m.d.n * ns;
+    const int block = 256;
+    const size_t blocks = std::min<size_t>((total + block - 1) / block, 152 * 64);
+    const int base_n = m.d.ic_base_n > 0 ? m.d.ic_base_n : m.d.n;
+    init_fields_kernel<<<(unsigned)blocks, block, 0, st>>>(m.d.n, (int)m.d.ic, m.d.ic_amp, base_n, seeds_dev,
+                                                           theta_dev, ns, u0);
+    MFMC_CUDA(cudaGetLastError());
+    return MFMC_OK;
+}
+
+// ----------------------------------------------------------------------------- coefficients
+__global__ void coef_kernel(const double *eps, double eps_nominal, double ahat, double chat,
+                            double tau, double beta1, double cF, size_t ns, StepCoef *out) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    const double e = eps ? eps[i] : eps_nominal;
+    const double e2 = e * e;
+    const double cg = e2 * ahat * chat;                 // lattice c_gamma of this sample
+    const double denom = 1.0 + tau * beta1 * cg;
+    StepCoef c;
+    c.c0 = (float)chat;
+    c.c1 = (float)(tau * beta1 * e2 * ahat / denom);
+    c.c2 = (float)(tau * beta1 * cF / denom);
+    c.pad = 0.f;
+    out[i] = c;
+}
+
+mfmc_status launch_coefficients(const Model &m, const double *eps_dev, size_t ns, StepCoef *coef,
+                                cudaStream_t st) {
+    if (ns == 0) return MFMC_OK;
+    coef_kernel<<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(eps_dev, m.d.eps, m.ahat, m.chat, m.d.tau,
+                                                               m.d.beta1, m.d.c_F, ns, coef);
+    MFMC_CUDA(cudaGetLastError());
+    return MFMC_OK;
+}
+
+// ----------------------------------------------------------------------------- generic step
+// Any R <= 32 and any radial kernel (weights per r2 = dx^2 + dy^2).  One output per
+// thread, 32 x 8 outputs per CTA; the disc is summed row by row, dy then dx ascending.
+struct GenericArgs {
+    const float *src;
+    float *dst;
+    const StepCoef *coef;
+    double *partials;
+    const float *wtab;  // NULL: unit weights
+    int n, R, tiles_x, tiles, sample0, last;
+};
+
+constexpr int GEN_TX = 32, GEN_TY = 8, GEN_NT = GEN_TX * GEN_TY;
+
+__global__ void __launch_bounds__(GEN_NT) step_generic_kernel(GenericArgs a) {
+    extern __shared__ float4 smem4[];
+    const int R = a.R;
+    const int R4 = (R + 3) & ~3;
+    const int SW = GEN_TX + 2 * R4, SW4 = SW / 4, SH = GEN_TY + 2 * R;
+    float *s = reinterpret_cast<float *>(smem4);
+    int *widths = reinterpret_cast<int *>(s + SH * SW);
+    float *wt = reinterpret_cast<float *>(widths + (R + 1));
+    __shared__ double red[GEN_NT / 32];
+
+    const int n = a.n, tile = blockIdx.x, sample = a.sample0 + blockIdx.y;
+    const int x0 = (tile % a.tiles_x) * GEN_TX, y0 = (tile / a.tiles_x) * GEN_TY;
+    const size_t nn = (size_t)n * n;
+    const float *__restrict__ src = a.src + (size_t)sample * nn;
+    for (int idx = threadIdx.x; idx < SH * SW4; idx += GEN_NT) {
+        const int r = idx / SW4, c4 = idx - r * SW4;
+        const int gy = wrap_idx(y0 - R + r, n), gx = wrap_idx(x0 - R4 + 4 * c4, n);
+        smem4[idx] = __ldg(reinterpret_cast<const float4 *>(src + (size_t)gy * n + gx));
+    }
+    if (threadIdx.x <= R) {
+        const int d = threadIdx.x;
+        int w = 0;
+        while ((w + 1) * (w + 1) <= R * R - d * d) ++w;
+        widths[d] = w;
+    }
+    if (a.wtab)
+        for (int i = threadIdx.x; i <= R * R; i += GEN_NT) wt[i] = a.wtab[i];
+    __syncthreads();
+
+    const int lx = threadIdx.x % GEN_TX, ly = threadIdx.x / GEN_TX;
+    float S = 0.f;
+    for (int dy = -R; dy <= R; ++dy) {
+        const int w = widths[dy < 0 ? -dy : dy];
+        const float *row = s + (ly + R + dy) * SW + lx + R4;
+        if (a.wtab) {
+            for (int dx = -w; dx <= w; ++dx) S = fmaf(wt[dx * dx + dy * dy], row[dx], S);
+        } else {
+            for (int dx = -w; dx <= w; ++dx) S += row[dx];
+        }
+    }
+    const StepCoef cf = a.coef[sample];
+    const float uc = s[(ly + R) * SW + lx + R4];
+    const float sd = fmaf(-cf.c0, uc, S);
+    float v = uc + fmaf(cf.c1, sd, cf.c2 * uc);
+    v = fminf(1.f, fmaxf(-1.f, v));
+    const int gy = y0 + ly, gx = x0 + lx;
+    double part = 0.0;
+    if (gy < n && gx < n) {
+        a.dst[(size_t)sample * nn + (size_t)gy * n + gx] = v;
+        part = v;
+    }
+    if (a.last) {
+        const double t = block_sum_fixed<GEN_NT>(part, red);
+        if (threadIdx.x == 0) a.partials[(size_t)sample * a.tiles + tile] = t;
+    }
+}
+
+static size_t generic_smem(int R) {
+    const int R4 = (R + 3) & ~3;
+    return (size_t)(GEN_TY + 2 * R) * (GEN_TX + 2 * R4) * sizeof(float) + (R + 1) * sizeof(int) +
+           (R * R + 1) * sizeof(float);
+}
+
+// ----------------------------------------------------------------------------- OoI
+__global__ void finalize_ooi_kernel(const double *partials, int tiles, size_t ns, double inv_nn,
+                                    double *ubar, double *ooi) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    double t = 0.0;
+    for (int k = 0; k < tiles; ++k) t += partials[i * tiles + k];  // tile order
+    const double mean = t * inv_nn;
+    if (ubar) ubar[i] = mean;
+    if (ooi) ooi[i] = 0.5 * (1.0 + mean);
+}
+
+__global__ void reduce_fields_kernel(const float *u, int n, double *ubar, double *ooi) {
+    __shared__ double red[256];
+    const size_t nn = (size_t)n * n;
+    const float *f = u + blockIdx.x * nn;
+    double t = 0.0;
+    for (size_t i = threadIdx.x; i < nn; i += 256) t += f[i];
+    red[threadIdx.x] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < 256; ++i) s += red[i];
+        const double mean = s / (double)nn;
+        if (ubar) ubar[blockIdx.x] = mean;
+        if (ooi) ooi[blockIdx.x] = 0.5 * (1.0 + mean);
+    }
+}
+
+bool algo_supported(const Model &m, int algo) {
+    const bool constant = m.d.kernel == MFMC_KERNEL_CONSTANT;
+    switch (algo) {
+        case MFMC_ALGO_PLAIN: return true;
+        case MFMC_ALGO_DIRECT: return true;  // tile kernel (R <= 8) or the generic kernel
+        case MFMC_ALGO_PREFIX:
+        case MFMC_ALGO_PREFIX_KAHAN: return constant && tile_launcher(m.R) != nullptr;
+        case MFMC_ALGO_RESIDENT: {
+            if (!constant || resident_launcher(m.R) == nullptr) return false;
+            const int nt = resident_threads(m.d.n);
+            return m.d.n % 4 == 0 && (m.d.n * m.d.n) % (4 * RES_RY) == 0 && nt >= 1 && nt <= 256 &&
+                   m.d.n / 4 <= nt && resident_smem(m.d.n, m.R) <= 227 * 1024 && (m.d.n % RES_RY) == 0;
+        }
+        default: return false;
+    }
+}
+
+static int tiles_for(const Model &m, int algo, int *tiles_x) {
+    int tx = GEN_TX, ty = GEN_TY;
+    const TileLauncher *L = tile_launcher(m.R);
+    const bool constant = m.d.kernel == MFMC_KERNEL_CONSTANT;
+    const bool tiled = constant && L &&
+                       ((algo == MFMC_ALGO_DIRECT && L->fn[0]) || algo == MFMC_ALGO_PREFIX ||
+                        algo == MFMC_ALGO_PREFIX_KAHAN);
+    if (tiled) {
+        tx = L->tx;
+        ty = L->ty;
+    }
+    *tiles_x = (m.d.n + tx - 1) / tx;
+    return *tiles_x * ((m.d.n + ty - 1) / ty);
+}
+
+static mfmc_status launch_generic(const Model &m, const GenericArgs &base, size_t s0, size_t cnt,
+                                  cudaStream_t st) {
+    const size_t smem = generic_smem(m.R);
+    static bool attr_done = false;
+    if (!attr_done) {
+        MFMC_CUDA(cudaFuncSetAttribute(step_generic_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       96 * 1024));
+        attr_done = true;
+    }
+    for (size_t o = 0; o < cnt; o += 65535) {
+        GenericArgs a = base;
+        a.sample0 = (int)(s0 + o);
+        const unsigned gy = (unsigned)std::min<size_t>(65535, cnt - o);
+        step_generic_kernel<<<dim3(a.tiles, gy), GEN_NT, smem, st>>>(a);
+    }
+    MFMC_CUDA(cudaGetLastError());
+    return MFMC_OK;
+}
+
+mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0, size_t ns, int nsteps,
+                      float *uT, double *ubar, double *ooi, cudaStream_t st) {
+    if (ns == 0) return MFMC_OK;
+    const int n = m.d.n;
+    const size_t nn = (size_t)n * n;
+    if (!algo_supported(m, algo)) return fail(MFMC_EINVAL, "algorithm %d does not support this model", algo);
+    if (nsteps == 0) {
+        if (uT) MFMC_CUDA(cudaMemcpyAsync(uT, u0, nn * ns * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        for (size_t o = 0; o < ns; o += 65535) {
+            const unsigned g = (unsigned)std::min<size_t>(65535, ns - o);
+            reduce_fields_kernel<<<g, 256, 0, st>>>(u0 + o * nn, n, ubar ? ubar + o : nullptr,
+                                                    ooi ? ooi + o : nullptr);
+        }
+        MFMC_CUDA(cudaGetLastError());
+        return MFMC_OK;
+    }
+    if (algo == MFMC_ALGO_RESIDENT) {
+        ResidentArgs a;
+        a.u0 = u0;
+        a.uT = uT;
+        a.coef = coef;
+        a.ubar = ubar;
+        a.ooi = ooi;
+        a.n = n;
+        a.ns = (int)ns;
+        a.nsteps = nsteps;
+        return resident_launcher(m.R)(a, st);
+    }
+    int tiles_x = 0;
+    const int tiles = tiles_for(m, algo, &tiles_x);
+    mfmc_status s = ensure_scratch(m, ns, (size_t)tiles);
+    if (s != MFMC_OK) return s;
+
+    const bool constant = m.d.kernel == MFMC_KERNEL_CONSTANT;
+    const TileLauncher *L = tile_launcher(m.R);
+    const int ai = algo == MFMC_ALGO_DIRECT ? 0 : (algo == MFMC_ALGO_PREFIX ? 1 : 2);
+    const bool tiled = algo != MFMC_ALGO_PLAIN && constant && L && L->fn[ai];
+
+    if (algo == MFMC_ALGO_PLAIN) {
+        // reference form: one sample per launch, one launch per step
+        for (size_t smp = 0; smp < ns; ++smp) {
+            const float *src = u0;
+            for (int k = 1; k <= nsteps; ++k) {
+                float *dst = (k == nsteps && uT) ? uT : ((k & 1) ? m.bufA : m.bufB);
+                GenericArgs g;
+                g.src = src;
+                g.dst = dst;
+                g.coef = coef;
+                g.partials = m.partials;
+                g.wtab = constant ? nullptr : m.d_wtab;
+                g.n = n;
+                g.R = m.R;
+                g.tiles_x = tiles_x;
+                g.tiles = tiles;
+                g.sample0 = 0;
+                g.last = k == nsteps;
+                s = launch_generic(m, g, smp, 1, st);
+                if (s != MFMC_OK) return s;
+                src = dst;
+            }
+        }
+    } else {
+        const float *src = u0;
+        for (int k = 1; k <= nsteps; ++k) {
+            float *dst = (k == nsteps && uT) ? uT : ((k & 1) ? m.bufA : m.bufB);
+            if (tiled) {
+                TileArgs t;
+                t.src = src;
+                t.dst = dst;
+                t.coef = coef;
+                t.partials = m.partials;
+                t.n = n;
+                t.tiles_x = tiles_x;
+                t.tiles = tiles;
+                t.sample0 = 0;
+                t.last = k == nsteps;
+                s = L->fn[ai](t, ns, st);
+            } else {
+                GenericArgs g;
+                g.src = src;
+                g.dst = dst;
+                g.coef = coef;
+                g.partials = m.partials;
+                g.wtab = constant ? nullptr : m.d_wtab;
+                g.n = n;
+                g.R = m.R;
+                g.tiles_x = tiles_x;
+                g.tiles = tiles;
+                g.sample0 = 0;
+                g.last = k == nsteps;
+                s = launch_generic(m, g, 0, ns, st);
+            }
+            if (s != MFMC_OK) return s;
+            src = dst;
+        }
+    }
+    finalize_ooi_kernel<<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(m.partials, tiles, ns, 1.0 / (double)nn,
+                                                                       ubar, ooi);
+    MFMC_CUDA(cudaGetLastError());
+    return MFMC_OK;
+}
+
+}  // namespace mfmc

@@ -1,0 +1,16 @@
+// Register-tiled step kernels for R in {11, 12}.
+#include "step_kernels.cuh"
+
+namespace mfmc {
+
+const TileLauncher *tile_launcher_c(int R) {
+    static const TileLauncher t11 = make_tile_launcher<11, false>();
+    static const TileLauncher t12 = make_tile_launcher<12, false>();
+    switch (R) {
+        case 11: return &t11;
+        case 12: return &t12;
+        default: return nullptr;
+    }
+}
+
+}  // namespace mfmc

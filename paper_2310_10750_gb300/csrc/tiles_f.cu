@@ -1,0 +1,14 @@
+// Register-tiled step kernels for R in {32}.
+#include "step_kernels.cuh"
+
+namespace mfmc {
+
+const TileLauncher *tile_launcher_f(int R) {
+    static const TileLauncher t32 = make_tile_launcher<32, false>();
+    switch (R) {
+        case 32: return &t32;
+        default: return nullptr;
+    }
+}
+
+}  // namespace mfmc

@@ -1,0 +1,78 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it loads, exports every entry
+point include/mfmc.h declares, and validates model descriptors on the host."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from tests.conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "mfmc.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2310_10750_gb300 import build
+    path = build.build()
+    from paper_2310_10750_gb300 import mfmc
+    return path, mfmc
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(mfmc_\w+)\s*\(", text)
+    return sorted(set(n for n in names if not n.endswith("_t")))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("mfmc_model_create", "mfmc_model_destroy", "mfmc_solve_batch", "mfmc_solve_fields",
+                     "mfmc_plan", "mfmc_estimate", "mfmc_run", "mfmc_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    path, _ = lib
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(line.split()[-1] for line in out.splitlines() if line.strip())
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    L = ctypes.CDLL(path)
+    for n in declared_functions():
+        assert hasattr(L, n)
+
+
+def test_model_validation_on_host(lib):
+    _, mfmc = lib
+    m = mfmc.Model(n=64, delta=4 / 64, eps=0.03)
+    info = m.info()
+    assert info.R == 4 and info.disc_points == 49
+    # lattice c_gamma of the constant kernel: 8 eps^2/(pi delta^4) h^2 |D|
+    assert info.c_gamma == pytest.approx(8 * 0.03 ** 2 / (3.141592653589793 * (4 / 64) ** 4) / 64 ** 2 * 49)
+    assert info.c_gamma == pytest.approx(1.7968, abs=1e-4)
+    for bad in (dict(n=62, delta=4 / 62), dict(n=64, delta=4.5 / 64), dict(n=64, delta=33 / 64),
+                dict(n=64, delta=4 / 64, tau=0.0), dict(n=64, delta=4 / 64, beta2=0.05),
+                dict(n=64, delta=4 / 64, beta1=0.0), dict(n=64, delta=4 / 64, nsteps=-1),
+                dict(n=64, delta=4 / 64, kernel=1, delta_hf=0.0), dict(n=8, delta=4 / 8),
+                dict(n=64, delta=4 / 64, ic_base_n=96), dict(n=64, delta=4 / 64, algo=9)):
+        with pytest.raises(mfmc.MfmcError) as e:
+            mfmc.Model(**bad)
+        assert e.value.status == mfmc.MFMC_EINVAL
+        assert mfmc.mfmc_last_error()
+    # the resident form needs the field in shared memory: n = 1024 is rejected
+    with pytest.raises(mfmc.MfmcError):
+        mfmc.Model(n=1024, delta=32 / 1024, algo=mfmc.ALGO_RESIDENT)
+
+
+def test_host_eps_resolution_matches_oracle_generator(lib):
+    _, mfmc = lib
+    import numpy as np
+    import oracle
+    m = mfmc.Model(n=64, delta=4 / 64, eps=0.03, eps_lo=0.024, eps_hi=0.036)
+    seeds = np.arange(20) + 20231016
+    got = mfmc.mfmc_sample_eps(m, seeds)
+    ref = oracle.OracleModel(n=64, delta=4 / 64, eps_lo=0.024, eps_hi=0.036)
+    assert [ref.sample_eps(int(s)) for s in seeds] == got.tolist()

@@ -1,0 +1,251 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (derived from the arithmetic; see the design notes):
+  * initial fields: both sides build them in FP64 and round to FP32; the only
+    difference is the last FP64 bit of log/cos/exp, so values agree to 1 FP32 ulp.
+  * one step: u_new = u + c1 (S - c0 u) + c2 u in FP32.  The final add rounds to
+    2^-24 |u|; S has at most (|D| + 2R + 4) rounded adds of values <= max|u|, scaled
+    by c1 <= 0.05; c0, c1, c2 are rounded to FP32.  Bound used:
+    |u_gpu - u_orc| <= 4e-6 max|u| per step.
+  * a solve of k steps: the step is Lipschitz with factor (1 + tau beta1 c_F), so the
+    error grows at most additively: k * 4e-6 * max|u| * e^{c_F T}; the OoI f is the mean
+    of u and gets the same bound; the target is |f_gpu - f_orc| <= 1e-5 f_orc.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+ALGOS = ["prefix", "direct", "kahan", "resident", "plain"]
+
+
+def algo_id(mf, name):
+    return {"prefix": mf.ALGO_PREFIX, "direct": mf.ALGO_DIRECT, "kahan": mf.ALGO_PREFIX_KAHAN,
+            "resident": mf.ALGO_RESIDENT, "plain": mf.ALGO_PLAIN, "auto": mf.ALGO_AUTO}[name]
+
+
+def pair(mf, n, R, steps, ic=0, eps=0.03, eps_lo=0.0, eps_hi=0.0, kernel=0, delta_hf=0.0, tau=1e-3,
+         ic_amp=0.05, ic_base_n=0, algo="prefix"):
+    g = mf.Model(n=n, delta=R / n, kernel=kernel, delta_hf=delta_hf, eps=eps, eps_lo=eps_lo, eps_hi=eps_hi,
+                 tau=tau, nsteps=steps, ic=ic, ic_amp=ic_amp, ic_base_n=ic_base_n, algo=algo_id(mf, algo))
+    o = O.OracleModel(n=n, delta=R / n, kernel=kernel, delta_hf=delta_hf, eps=eps, eps_lo=eps_lo, eps_hi=eps_hi,
+                      tau=tau, nsteps=steps, ic=ic, ic_amp=ic_amp, ic_base_n=ic_base_n)
+    return g, o
+
+
+def gpu_solve(mf, g, seeds, want_field=True, params=None):
+    import torch
+    ns = len(seeds)
+    n = g.n
+    u0 = torch.empty((ns, n, n), dtype=torch.float32, device="cuda")
+    uT = torch.empty_like(u0) if want_field else None
+    ooi = torch.empty(ns, dtype=torch.float64, device="cuda")
+    ubar = torch.empty(ns, dtype=torch.float64, device="cuda")
+    eps = torch.tensor(mf.mfmc_sample_eps(g, seeds, params), dtype=torch.float64, device="cuda")
+    mf.mfmc_init_fields(g, seeds, u0, params=params)
+    mf.mfmc_solve_fields(g, u0, ns, eps=eps, uT=uT, ooi=ooi, ubar=ubar)
+    torch.cuda.synchronize()
+    return (u0.cpu().numpy().astype(np.float64), None if uT is None else uT.cpu().numpy().astype(np.float64),
+            ooi.cpu().numpy(), ubar.cpu().numpy())
+
+
+def seeds_of(k, base=20231016):
+    return np.arange(k, dtype=np.uint64) + base
+
+
+# --------------------------------------------------------------------------- inputs
+@pytest.mark.parametrize("ic,base", [(0, 0), (1, 0), (2, 0), (1, 128), (0, 256)])
+def test_initial_fields_match_oracle(gpu_lib, ic, base):
+    mf = gpu_lib
+    g, o = pair(mf, 64, 4, 1, ic=ic, ic_base_n=base, ic_amp=0.05 if ic != 1 else 0.5)
+    seeds = seeds_of(6)
+    u0, _, _, _ = gpu_solve(mf, g, seeds, want_field=False)
+    for i, s in enumerate(seeds):
+        ref = o.initial_field(int(s))
+        d = np.abs(u0[i] - ref)
+        ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+        assert np.all(d <= ulp), (ic, base, d.max())
+        assert np.mean(d == 0) > 0.999
+
+
+def test_initial_field_explicit_theta(gpu_lib):
+    mf = gpu_lib
+    g, o = pair(mf, 128, 4, 1, ic=2)
+    mu = [0.9815, 0.9276, 0.9162, 0.9417]
+    eta = [[0.0072, -0.0039], [0.0232, 0.0208], [-0.0220, 0.0041], [-0.0099, 0.0118]]
+    params = mf.make_params(1, theta=[(mu, eta)])
+    u0, _, _, _ = gpu_solve(mf, g, seeds_of(1), want_field=False, params=params)
+    ref = o.initial_field(0, theta=(np.array(mu), np.array(eta)))
+    assert np.abs(u0[0] - ref).max() <= 1.2e-7
+
+
+# --------------------------------------------------------------------------- one step
+@pytest.mark.parametrize("algo", ALGOS)
+@pytest.mark.parametrize("n,R", [(64, 1), (64, 2), (64, 4), (128, 8), (68, 3), (96, 5), (132, 6)])
+def test_one_step_elementwise(gpu_lib, algo, n, R):
+    mf = gpu_lib
+    o = O.OracleModel(n=n, delta=R / n, eps=0.03, tau=5e-3, nsteps=1, ic=2)
+    try:
+        g = mf.Model(n=n, delta=R / n, eps=0.03, tau=5e-3, nsteps=1, ic=2, algo=algo_id(mf, algo))
+    except mf.MfmcError:
+        pytest.skip(f"{algo} does not support n={n}, R={R}")
+    seeds = seeds_of(3, base=7)
+    u0, uT, _, _ = gpu_solve(mf, g, seeds)
+    for i in range(len(seeds)):
+        ref = o.step(u0[i], 0.03)
+        assert np.abs(uT[i] - ref).max() <= 4e-6 * max(1.0, np.abs(u0[i]).max())
+        assert np.abs(uT[i]).max() <= 1.0
+
+
+# --------------------------------------------------------------------------- solves
+@pytest.mark.parametrize("algo", ALGOS + ["auto"])
+def test_plain_mc_config_64_R4(gpu_lib, algo):
+    # 64 x 64, delta = 4h, constant kernel, eps ~ U[0.024, 0.036], tau = 1e-3, 200 steps,
+    # u0 i.i.d. U[-0.05, 0.05]; 32 samples
+    mf = gpu_lib
+    g, o = pair(mf, 64, 4, 200, ic=0, eps_lo=0.024, eps_hi=0.036, algo=algo)
+    seeds = seeds_of(32)
+    u0, uT, f, ubar = gpu_solve(mf, g, seeds)
+    growth = math.exp(1.0 * 200 * 1e-3)
+    for i, s in enumerate(seeds):
+        fr, mean, ur, eps = o.solve_sample(int(s))
+        assert abs(f[i] - fr) <= 1e-5 * fr
+        tol = 200 * 4e-6 * 0.05 * growth
+        assert np.abs(uT[i] - ur).max() <= tol
+        assert abs(ubar[i] - mean) <= 2 * tol
+
+
+@pytest.mark.parametrize("algo", ["prefix", "resident", "direct"])
+def test_nuclei_obstacle_active_and_bounds_exact(gpu_lib, algo):
+    mf = gpu_lib
+    g, o = pair(mf, 64, 4, 120, ic=2, tau=5e-3, algo=algo)
+    seeds = seeds_of(4, base=99)
+    u0, uT, f, _ = gpu_solve(mf, g, seeds)
+    assert np.abs(uT).max() <= 1.0
+    assert (uT == 1.0).any() and (uT == -1.0).any()
+    for i, s in enumerate(seeds):
+        fr, _, ur, _ = o.solve_sample(int(s))
+        assert abs(f[i] - fr) <= 1e-5 * fr
+        # the projection: where the oracle is strictly inside, so is the GPU (up to tol)
+        assert np.abs(uT[i] - ur).max() <= 120 * 4e-6 * math.exp(0.6)
+
+
+def test_ragged_tiles_and_many_tiles(gpu_lib):
+    mf = gpu_lib
+    for n, R in ((68, 3), (132, 5), (200, 8)):
+        g, o = pair(mf, n, R, 20, ic=2, tau=5e-3, algo="prefix")
+        seeds = seeds_of(2, base=n)
+        _, uT, f, _ = gpu_solve(mf, g, seeds)
+        for i, s in enumerate(seeds):
+            fr, _, ur, _ = o.solve_sample(int(s))
+            assert abs(f[i] - fr) <= 1e-5 * fr
+            assert np.abs(uT[i] - ur).max() <= 20 * 4e-6 * 1.2
+
+
+def test_gaussian_kernel_generic_path(gpu_lib):
+    mf = gpu_lib
+    eps = math.sqrt(0.00178)
+    g, o = pair(mf, 64, 8, 30, ic=2, eps=eps, kernel=1, delta_hf=0.25, tau=1e-2, algo="direct")
+    seeds = seeds_of(2, base=5)
+    _, uT, f, _ = gpu_solve(mf, g, seeds)
+    for i, s in enumerate(seeds):
+        fr, _, ur, _ = o.solve_sample(int(s))
+        assert abs(f[i] - fr) <= 1e-5 * fr
+        assert np.abs(uT[i] - ur).max() <= 30 * 4e-6 * 1.5
+
+
+def test_stationary_states_exact(gpu_lib):
+    import torch
+    mf = gpu_lib
+    for algo in ("prefix", "resident", "direct", "kahan"):
+        g = mf.Model(n=64, delta=4 / 64, nsteps=50, algo=algo_id(mf, algo))
+        for c in (1.0, -1.0, 0.0):
+            u0 = torch.full((2, 64, 64), c, dtype=torch.float32, device="cuda")
+            uT = torch.empty_like(u0)
+            ooi = torch.empty(2, dtype=torch.float64, device="cuda")
+            mf.mfmc_solve_fields(g, u0, 2, uT=uT, ooi=ooi)
+            torch.cuda.synchronize()
+            assert torch.all(uT == c)
+            assert np.all(ooi.cpu().numpy() == 0.5 * (1 + c))
+
+
+def test_edge_cases(gpu_lib):
+    import torch
+    mf = gpu_lib
+    g = mf.Model(n=64, delta=4 / 64, nsteps=0)
+    u0 = torch.rand((3, 64, 64), dtype=torch.float32, device="cuda") - 0.5
+    ooi = torch.empty(3, dtype=torch.float64, device="cuda")
+    uT = torch.empty_like(u0)
+    mf.mfmc_solve_fields(g, u0, 3, uT=uT, ooi=ooi)
+    torch.cuda.synchronize()
+    assert torch.equal(uT, u0)
+    ref = [O.ooi(u0[i].cpu().numpy().astype(np.float64)) for i in range(3)]
+    assert np.allclose(ooi.cpu().numpy(), ref, rtol=0, atol=1e-14)
+    mf.mfmc_solve_fields(g, u0, 0)          # empty batch is a no-op
+    with pytest.raises(mf.MfmcError):       # output aliasing the input is rejected
+        g2 = mf.Model(n=64, delta=4 / 64, nsteps=2)
+        mf.mfmc_solve_fields(g2, u0, 3, uT=u0)
+
+
+def test_solve_batch_mixed_models(gpu_lib):
+    mf = gpu_lib
+    ga, oa = pair(mf, 64, 2, 40, ic=2, tau=5e-3, algo="auto")
+    gb, ob = pair(mf, 128, 4, 40, ic=2, tau=5e-3, algo="auto")
+    seeds = seeds_of(6, base=300)
+    models = [ga, gb, ga, gb, gb, ga]
+    f, ubar = mf.mfmc_solve_batch(models, seeds)
+    for i, s in enumerate(seeds):
+        o = oa if models[i] is ga else ob
+        fr, mean, _, _ = o.solve_sample(int(s))
+        assert abs(f[i] - fr) <= 1e-5 * fr
+        assert abs(ubar[i] - mean) <= 2e-5 * fr
+
+
+# --------------------------------------------------------------------------- full sizes
+def _gpu_batch_of_config(mf, n, R, steps, ns, algo="auto", ic=1, base=0):
+    g = mf.Model(n=n, delta=R / n, eps=0.02, eps_lo=0.016, eps_hi=0.024, tau=1e-3, nsteps=steps, ic=ic,
+                 ic_amp=0.05, ic_base_n=base, algo=algo_id(mf, algo))
+    o = O.OracleModel(n=n, delta=R / n, eps=0.02, eps_lo=0.016, eps_hi=0.024, tau=1e-3, nsteps=steps, ic=ic,
+                      ic_amp=0.05, ic_base_n=base)
+    return g, o
+
+
+@pytest.mark.slow
+def test_single_fidelity_256_R8_full_size_sampled(gpu_lib):
+    # 256 x 256, delta = 8h, 1000 steps, 512 samples in one launch configuration (the one
+    # the benchmark times); the oracle checks samples 0 and 511 element by element and every
+    # sample is checked by the exact linear-regime identity of the mean.
+    mf = gpu_lib
+    n, R, steps, ns = 256, 8, 1000, 512
+    g, o = _gpu_batch_of_config(mf, n, R, steps, ns)
+    seeds = seeds_of(ns, base=20231016 + 1000003)
+    u0, uT, f, ubar = gpu_solve(mf, g, seeds)
+    assert np.abs(uT).max() <= 1.0
+    # no node reaches the obstacle (|u| <= 0.05 e^T): mean(u^k) = (1 + c2)^k mean(u^0) exactly
+    eps = mf.mfmc_sample_eps(g, seeds)
+    for i in range(ns):
+        cg = eps[i] ** 2 * 8 / (math.pi * (R / n) ** 4) / n ** 2 * 197
+        c2 = 1e-3 / (1 + 1e-3 * cg)
+        pred = (1 + c2) ** steps * u0[i].mean()
+        assert abs(ubar[i] - pred) <= 1e-6 * np.abs(u0[i]).max() + 1e-9
+    for i in (0, ns - 1):
+        fr, mean, ur, _ = o.solve_sample(int(seeds[i]))
+        assert abs(f[i] - fr) <= 1e-5 * fr
+        assert np.abs(uT[i] - ur).max() <= steps * 4e-6 * 0.05 * math.e
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("n,R", [(512, 16), (128, 4), (64, 2)])
+def test_hierarchy_levels_sampled(gpu_lib, n, R):
+    # the MFMC hierarchy with delta = 1/32 and a shared 512^2 base field
+    mf = gpu_lib
+    g, o = _gpu_batch_of_config(mf, n, R, 1000 if n < 512 else 200, 16, base=512)
+    seeds = seeds_of(16, base=4242)
+    u0, uT, f, ubar = gpu_solve(mf, g, seeds)
+    for i in (0, 15):
+        fr, mean, ur, _ = o.solve_sample(int(seeds[i]))
+        assert abs(f[i] - fr) <= 1e-5 * fr
