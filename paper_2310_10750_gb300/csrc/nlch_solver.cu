@@ -237,7 +237,7 @@ bool algo_supported(const Model &m, int algo) {
             if (!constant || resident_launcher(m.R) == nullptr) return false;
             const int nt = resident_threads(m.d.n);
             return m.d.n % 4 == 0 && (m.d.n * m.d.n) % (4 * RES_RY) == 0 && nt >= 1 && nt <= 256 &&
-                   m.d.n / 4 <= nt && resident_smem(m.d.n, m.R) <= 227 * 1024 && (m.d.n % RES_RY) == 0;
+                   m.d.n / 4 <= nt && resident_smem(m.d.n, m.R) <= 225 * 1024 && (m.d.n % RES_RY) == 0;
         }
         default: return false;
     }

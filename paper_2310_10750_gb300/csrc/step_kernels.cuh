@@ -402,10 +402,10 @@ template <int R>
 mfmc_status launch_resident(const ResidentArgs &a, cudaStream_t st) {
     auto kern = resident_kernel<R, RES_RY>;
     const size_t smem = resident_smem(a.n, R);
-    static bool attr_done = false;
-    if (!attr_done) {
-        MFMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        attr_done = true;
+    static size_t attr_max = 0;
+    if (smem > attr_max) {
+        MFMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_max = smem;
     }
     const int nt = resident_threads(a.n);
     int per_sm = 0;
