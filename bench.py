@@ -8,6 +8,9 @@ batch.  The two field buffers (2 x 128 MiB) exceed the 129 MB L2, so no flush is
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+Profiling cases (for ncu captures, never bench values): --nsteps, --samples and --algo
+shrink or pin the solve, --no-e2e / --no-plain / --no-cpu-baseline drop the extra legs.
+
 `--impl reference` times the FP64 CPU oracle on the host cores on a bounded sample of
 the same workload.  Under torchrun each rank solves its own 512 samples (weak scaling,
 replicas: no collective on the data path; only the timing max uses one).
@@ -33,8 +36,8 @@ WORKLOAD = "single fidelity 256x256, delta=8h (197-pt disc), constant kernel, 10
 
 
 def config(algo=None):
-    c = {"workload": WORKLOAD, "n": N_LATTICE, "R": R_CELLS, "disc_points": 197, "nsteps": NSTEPS,
-         "samples_per_gpu": NSAMPLES, "tau": TAU, "eps": "0.02*U[0.8,1.2]", "ic": "smoothed Gaussian sigma=0.05",
+    c = {"workload": WORKLOAD if (NSTEPS, NSAMPLES) == (1000, 512) else "profiling case: " + WORKLOAD,
+         "n": N_LATTICE, "R": R_CELLS, "disc_points": 197, "nsteps": NSTEPS, "samples_per_gpu": NSAMPLES, "tau": TAU, "eps": "0.02*U[0.8,1.2]", "ic": "smoothed Gaussian sigma=0.05",
          "l2": "inputs larger than L2 (2 x 128 MiB field buffers per solve, L2 129 MB)"}
     if algo is not None:
         c["algo"] = algo
@@ -172,6 +175,9 @@ def run_reference(args):
 def run_ours(args):
     import numpy as np
     import torch
+    global NSTEPS, NSAMPLES
+    NSTEPS = args.nsteps or NSTEPS
+    NSAMPLES = args.samples or NSAMPLES
     ws, rank, local = dist_env()
     from paper_2310_10750_gb300 import build as pkg_build
     if rank == 0:
@@ -187,8 +193,12 @@ def run_ours(args):
     dev = torch.cuda.current_device()
     stream = torch.cuda.current_stream()
 
+    algo_req = {"auto": mfmc.ALGO_AUTO, "prefix": mfmc.ALGO_PREFIX, "direct": mfmc.ALGO_DIRECT,
+                "kahan": mfmc.ALGO_PREFIX_KAHAN, "tma": mfmc.ALGO_PREFIX_TMA}[args.algo]
     model = mfmc.Model(n=N_LATTICE, delta=R_CELLS / N_LATTICE, eps=EPS, eps_lo=EPS_LO, eps_hi=EPS_HI, tau=TAU,
-                       nsteps=NSTEPS, ic=mfmc.IC_SMOOTHED_GAUSS, ic_amp=SIGMA, algo=mfmc.ALGO_AUTO)
+                       nsteps=NSTEPS, ic=mfmc.IC_SMOOTHED_GAUSS, ic_amp=SIGMA, algo=algo_req)
+    if args.tile_variant >= 0:
+        model.set_tile_variant(args.tile_variant)
     ns = NSAMPLES
     seeds = np.arange(ns, dtype=np.uint64) + SEED_BASE + rank * ns
     u0 = torch.empty((ns, N_LATTICE, N_LATTICE), dtype=torch.float32, device="cuda")
@@ -198,8 +208,10 @@ def run_ours(args):
     for _ in range(args.warmup):
         mfmc.mfmc_solve_fields(model, u0, ns, eps=eps, ooi=ooi, stream=stream)
     torch.cuda.synchronize()
-    algo_names = {1: "direct", 2: "prefix", 3: "prefix-kahan", 4: "resident", 5: "plain"}
+    algo_names = {1: "direct", 2: "prefix", 3: "prefix-kahan", 4: "resident", 5: "plain", 6: "prefix-tma"}
     algo = algo_names.get(model.info().algo, str(model.info().algo))
+    if algo == "prefix-tma":
+        algo += f" (tile variant {model.info().tile_variant})"
 
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -225,32 +237,36 @@ def run_ours(args):
     clocks = clk.summary()
 
     # end to end through the batch call: host seeds in, host OoIs out
-    models = [model] * ns
-    mfmc.mfmc_solve_batch(models, seeds)          # warm the batch buffers
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    t = time.perf_counter()
-    for _ in range(args.steps):
-        f_host, _ = mfmc.mfmc_solve_batch(models, seeds)
-    e2e_s = (time.perf_counter() - t) / args.steps
-    if ws > 1:
-        tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = None
     h2d = ns * (8 + 8 + 12 * 8)       # seeds, eps, nuclei parameters (uploaded for every IC)
     d2h = ns * 2 * 8                  # OoI and mean per sample
+    if not args.no_e2e:
+        models = [model] * ns
+        mfmc.mfmc_solve_batch(models, seeds)          # warm the batch buffers
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            f_host, _ = mfmc.mfmc_solve_batch(models, seeds)
+        e2e_s = (time.perf_counter() - t) / args.steps
+        if ws > 1:
+            tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
 
     # plain form: one sample per launch, one launch per step (same GPU), on 4 samples
-    plain_ns = 4
-    ooi_p = torch.empty(plain_ns, dtype=torch.float64, device="cuda")
-    mfmc.mfmc_solve_fields_algo(model, mfmc.ALGO_PLAIN, u0, 1, eps=eps, ooi=ooi_p, stream=stream)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    mfmc.mfmc_solve_fields_algo(model, mfmc.ALGO_PLAIN, u0, plain_ns, eps=eps, ooi=ooi_p, stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    plain_sps = plain_ns / (e0.elapsed_time(e1) * 1e-3)
+    plain_sps = None
+    if not args.no_plain:
+        plain_ns = 4
+        ooi_p = torch.empty(plain_ns, dtype=torch.float64, device="cuda")
+        mfmc.mfmc_solve_fields_algo(model, mfmc.ALGO_PLAIN, u0, 1, eps=eps, ooi=ooi_p, stream=stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        mfmc.mfmc_solve_fields_algo(model, mfmc.ALGO_PLAIN, u0, plain_ns, eps=eps, ooi=ooi_p, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_sps = plain_ns / (e0.elapsed_time(e1) * 1e-3)
     batched_sps = ws * ns / (ms_step * 1e-3)
 
     peak_gbs, sm_max, peak_kind = load_peaks()
@@ -277,17 +293,19 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(algo),
                 "samples_per_s": batched_sps,
-                "plain_form": {"samples_per_s": plain_sps, "speedup_batched_vs_plain": batched_sps / plain_sps,
-                               "what": "one sample per launch, one launch per step, direct disc sum"},
+                "plain_form": None if plain_sps is None else {
+                    "samples_per_s": plain_sps, "speedup_batched_vs_plain": batched_sps / plain_sps,
+                    "what": "one sample per launch, one launch per step, direct disc sum"},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
                              "frac": achieved / peak_gbs, "traffic": traffic, "peak_kind": peak_kind,
-                             "kernel": f"step_tile_kernel ({algo})", "algorithmic_bytes_per_launch": bytes_launch,
+                             "kernel": ("step_tma_kernel" if algo.startswith("prefix-tma") else "step_tile_kernel") + f" ({algo})", "algorithmic_bytes_per_launch": bytes_launch,
                              "avg_launch_ms": kernel_ms},
                 "roofline_alu": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "T instr/s",
                                  "frac": alu_achieved / alu_peak, "instr_per_point": instr_per_pt},
-                "e2e": {"value": ws * ns * N_LATTICE * N_LATTICE * NSTEPS / e2e_s, "unit": METRIC,
-                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                        "what": "mfmc_solve_batch: host seeds -> device initial fields -> solve -> host OoIs"},
+                "e2e": None if e2e_s is None else {
+                    "value": ws * ns * N_LATTICE * N_LATTICE * NSTEPS / e2e_s, "unit": METRIC,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "what": "mfmc_solve_batch: host seeds -> device initial fields -> solve -> host OoIs"},
                 "gpu_launches": args.steps * launches_per_solve,
                 "clocks": clocks}
         if not args.no_cpu_baseline:
@@ -305,6 +323,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--nsteps", type=int, default=0, help="profiling: time steps per solve")
+    ap.add_argument("--samples", type=int, default=0, help="profiling: samples per GPU")
+    ap.add_argument("--algo", default="auto", choices=["auto", "prefix", "direct", "kahan", "tma"])
+    ap.add_argument("--tile-variant", type=int, default=-1, help="profiling: pin the TMA tile shape")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -69,7 +69,9 @@ typedef enum {
     MFMC_ALGO_PREFIX = 2,      /* in-register row prefix sums: O(R) adds per point */
     MFMC_ALGO_PREFIX_KAHAN = 3,/* prefix form with compensated accumulation       */
     MFMC_ALGO_RESIDENT = 4,    /* whole field held in shared memory for all steps */
-    MFMC_ALGO_PLAIN = 5        /* reference form: one sample per launch, direct   */
+    MFMC_ALGO_PLAIN = 5,       /* reference form: one sample per launch, direct   */
+    MFMC_ALGO_PREFIX_TMA = 6   /* prefix form, persistent CTAs, TMA double-buffered
+                                  tiles of a ghost-framed field                   */
 } mfmc_algo;
 
 /* One fidelity of the model (Section 2, Section 4).  The lattice is n x n on the unit
@@ -116,6 +118,7 @@ typedef struct {
     double xi;             /* c_gamma - c_F, Eq. (xi_constant)                      */
     int algo;              /* mfmc_algo the solver uses for this model             */
     size_t field_bytes;    /* n * n * 4                                             */
+    int tile_variant;      /* tile shape of the TMA kernel (0..2) the solver uses  */
 } mfmc_model_info;
 
 typedef struct mfmc_model mfmc_model;
@@ -138,6 +141,10 @@ void mfmc_model_destroy(mfmc_model *model);
 
 /* Derived constants of a model. */
 mfmc_status mfmc_model_query(const mfmc_model *model, mfmc_model_info *out);
+
+/* Pin the tile shape (0..2) of the TMA kernel instead of letting the autotuner choose
+ * (for measurements and tests).  MFMC_EINVAL for an unknown variant. */
+mfmc_status mfmc_model_set_tile_variant(mfmc_model *model, int variant);
 
 /* Host-side resolution of each sample's eps (model eps, eps range draw, or
  * params[i].eps), ns values into eps_out (host). params may be NULL. */

@@ -14,7 +14,7 @@
 namespace mfmc {
 
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int>, int> g_tune_cache;
+static std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune_cache;
 
 mfmc_status autotune(Model &m, cudaStream_t st) {
     const auto key = std::make_tuple(m.d.n, m.R, (int)m.d.kernel);
@@ -22,15 +22,22 @@ mfmc_status autotune(Model &m, cudaStream_t st) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            m.algo = it->second;
+            m.algo = it->second.first;
+            if (m.algo == MFMC_ALGO_PREFIX_TMA) m.tma_variant = it->second.second;
             m.tuned = 1;
             return MFMC_OK;
         }
     }
-    std::vector<int> cands;
-    for (int a : {MFMC_ALGO_RESIDENT, MFMC_ALGO_PREFIX, MFMC_ALGO_DIRECT})
-        if (algo_supported(m, a)) cands.push_back(a);
-    int best = cands.empty() ? MFMC_ALGO_DIRECT : cands[0];
+    // candidates: (algorithm, TMA tile variant)
+    std::vector<std::pair<int, int>> cands;
+    for (int a : {MFMC_ALGO_RESIDENT, MFMC_ALGO_PREFIX_TMA, MFMC_ALGO_PREFIX, MFMC_ALGO_DIRECT}) {
+        if (!algo_supported(m, a)) continue;
+        if (a == MFMC_ALGO_PREFIX_TMA)
+            for (int v = 0; v < 3; ++v) cands.push_back({a, v});
+        else
+            cands.push_back({a, 0});
+    }
+    std::pair<int, int> best = cands.empty() ? std::make_pair((int)MFMC_ALGO_DIRECT, 0) : cands[0];
     if (cands.size() > 1) {
         const size_t nn = (size_t)m.d.n * m.d.n;
         const size_t ns = std::max<size_t>(8, std::min<size_t>(1216, (size_t)(64u << 20) / nn));
@@ -49,13 +56,18 @@ mfmc_status autotune(Model &m, cudaStream_t st) {
         if (e != cudaSuccess) s = cuda_fail(e, "autotune setup");
         if (s == MFMC_OK) s = launch_coefficients(m, nullptr, ns, coef, st);
         float best_ms = 1e30f;
-        for (int a : cands) {
+        auto run = [&](std::pair<int, int> c) {
+            if (c.first == MFMC_ALGO_PREFIX_TMA)
+                return run_solve_tma(m, 0, c.second, coef, u0, ns, steps, nullptr, nullptr, ooi, st);
+            return run_solve(m, c.first, coef, u0, ns, steps, nullptr, nullptr, ooi, st);
+        };
+        for (auto a : cands) {
             if (s != MFMC_OK) break;
-            s = run_solve(m, a, coef, u0, ns, steps, nullptr, nullptr, ooi, st);  // warm-up
+            s = run(a);  // warm-up
             float ms_min = 1e30f;
             for (int rep = 0; rep < 3 && s == MFMC_OK; ++rep) {
                 cudaEventRecord(e0, st);
-                s = run_solve(m, a, coef, u0, ns, steps, nullptr, nullptr, ooi, st);
+                s = run(a);
                 cudaEventRecord(e1, st);
                 e = cudaEventSynchronize(e1);
                 if (e != cudaSuccess) s = cuda_fail(e, "autotune timing");
@@ -76,7 +88,8 @@ mfmc_status autotune(Model &m, cudaStream_t st) {
         if (e1) cudaEventDestroy(e1);
         if (s != MFMC_OK) return s;
     }
-    m.algo = best;
+    m.algo = best.first;
+    if (best.first == MFMC_ALGO_PREFIX_TMA) m.tma_variant = best.second;
     m.tuned = 1;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = best;

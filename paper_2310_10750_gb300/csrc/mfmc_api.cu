@@ -47,6 +47,9 @@ Model::~Model() {
     cudaFree(theta_tmp);
     cudaFree(u0buf);
     cudaFree(resbuf);
+    cudaFree(padA);
+    cudaFree(padB);
+    cudaFree(d_status);
     if (stream) cudaStreamDestroy(stream);
 }
 
@@ -120,7 +123,7 @@ static mfmc_status validate_desc(const mfmc_model_desc &d, int *R_out) {
     if (!(d.ic_amp >= 0)) return fail(MFMC_EINVAL, "ic_amp must be >= 0");
     if (d.ic_base_n < 0 || (d.ic_base_n > 0 && (d.ic_base_n % d.n != 0 || d.ic_base_n > 16384)))
         return fail(MFMC_EINVAL, "ic_base_n must be 0 or a multiple of n up to 16384");
-    if ((int)d.algo < MFMC_ALGO_AUTO || (int)d.algo > MFMC_ALGO_PLAIN) return fail(MFMC_EINVAL, "unknown algo");
+    if ((int)d.algo < MFMC_ALGO_AUTO || (int)d.algo > MFMC_ALGO_PREFIX_TMA) return fail(MFMC_EINVAL, "unknown algo");
     *R_out = R;
     return MFMC_OK;
 }
@@ -197,6 +200,14 @@ mfmc_status mfmc_model_query(const mfmc_model *m, mfmc_model_info *out) {
     out->xi = out->c_gamma - m->d.c_F;
     out->algo = m->algo;
     out->field_bytes = (size_t)m->d.n * m->d.n * sizeof(float);
+    out->tile_variant = m->tma_variant;
+    return MFMC_OK;
+}
+
+mfmc_status mfmc_model_set_tile_variant(mfmc_model *m, int variant) {
+    if (!m || variant < 0 || variant > 2) return fail(MFMC_EINVAL, "invalid tile variant");
+    std::lock_guard<std::mutex> lk(m->mu);
+    m->tma_variant = variant;
     return MFMC_OK;
 }
 
@@ -276,7 +287,7 @@ mfmc_status mfmc_solve_fields(const mfmc_model *cm, const double *eps, const flo
 mfmc_status mfmc_solve_fields_algo(const mfmc_model *cm, int algo, const double *eps, const float *u0, size_t ns,
                                    float *uT, double *ubar, double *ooi, void *stream) {
     if (!cm) return fail(MFMC_EINVAL, "NULL model");
-    if (algo < MFMC_ALGO_AUTO || algo > MFMC_ALGO_PLAIN) return fail(MFMC_EINVAL, "unknown algo");
+    if (algo < MFMC_ALGO_AUTO || algo > MFMC_ALGO_PREFIX_TMA) return fail(MFMC_EINVAL, "unknown algo");
     return solve_impl(const_cast<mfmc_model *>(cm), algo, eps, u0, ns, uT, ubar, ooi, (cudaStream_t)stream);
 }
 

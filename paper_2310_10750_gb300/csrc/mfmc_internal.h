@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -57,6 +58,14 @@ struct Model {
     double *resbuf = nullptr;
     size_t res_cap = 0;
     cudaStream_t stream = nullptr;
+    // ghost-framed scratch of the TMA path: [cap][P][P], P = n + 2 G, and its tensor maps
+    float *padA = nullptr, *padB = nullptr;
+    size_t pad_cap = 0;
+    CUtensorMap mapA, mapB;
+    int maps_valid = 0;
+    int map_sw = 0, map_sh = 0;  // box the tensor maps were encoded for
+    int tma_variant = 1;         // tile shape of the TMA kernel (autotuned)
+    int *d_status = nullptr;  // set by a device wait that gave up
     ~Model();
 };
 
@@ -118,6 +127,9 @@ mfmc_status launch_coefficients(const Model &m, const double *eps_dev, size_t ns
 // Full solve with an explicit algorithm; scratch from the model.
 mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0, size_t ns,
                       int nsteps, float *uT, double *ubar, double *ooi, cudaStream_t st);
+// The TMA pipeline with an explicit tile-shape variant (autotuner).
+mfmc_status run_solve_tma(Model &m, int kahan, int variant, const StepCoef *coef, const float *u0, size_t ns,
+                          int nsteps, float *uT, double *ubar, double *ooi, cudaStream_t st);
 // Whether an algorithm can run this model.
 bool algo_supported(const Model &m, int algo);
 // Autotuner: time the candidate algorithms on this model once and cache the winner.

@@ -6,7 +6,11 @@
 #include <cmath>
 
 #include "mfmc_internal.h"
-#include "step_kernels.cuh"
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "tma_step.cuh"
 
 namespace mfmc {
 
@@ -231,8 +235,9 @@ bool algo_supported(const Model &m, int algo) {
     switch (algo) {
         case MFMC_ALGO_PLAIN: return true;
         case MFMC_ALGO_DIRECT: return true;  // tile kernel (R <= 8) or the generic kernel
-        case MFMC_ALGO_PREFIX:
-        case MFMC_ALGO_PREFIX_KAHAN: return constant && tile_launcher(m.R) != nullptr;
+        case MFMC_ALGO_PREFIX: return constant && tile_launcher(m.R) != nullptr;
+        case MFMC_ALGO_PREFIX_KAHAN:
+        case MFMC_ALGO_PREFIX_TMA: return constant && tma_launcher(m.R) != nullptr;
         case MFMC_ALGO_RESIDENT: {
             if (!constant || resident_launcher(m.R) == nullptr) return false;
             const int nt = resident_threads(m.d.n);
@@ -248,8 +253,7 @@ static int tiles_for(const Model &m, int algo, int *tiles_x) {
     const TileLauncher *L = tile_launcher(m.R);
     const bool constant = m.d.kernel == MFMC_KERNEL_CONSTANT;
     const bool tiled = constant && L &&
-                       ((algo == MFMC_ALGO_DIRECT && L->fn[0]) || algo == MFMC_ALGO_PREFIX ||
-                        algo == MFMC_ALGO_PREFIX_KAHAN);
+                       ((algo == MFMC_ALGO_DIRECT && L->fn[0]) || algo == MFMC_ALGO_PREFIX);
     if (tiled) {
         tx = L->tx;
         ty = L->ty;
@@ -277,6 +281,131 @@ static mfmc_status launch_generic(const Model &m, const GenericArgs &base, size_
     return MFMC_OK;
 }
 
+// ----------------------------------------------------------------------------- TMA path
+// Copy unpadded fields [ns][n][n] into padded scratch [ns][P][P] including the frame.
+__global__ void pad_fields_kernel(const float *u, float *dst, int n, int G, size_t ns) {
+    const int P = n + 2 * G, P4 = P / 4;
+    const size_t total = ns * (size_t)P * P4;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const size_t smp = idx / ((size_t)P * P4);
+        const int rem = (int)(idx - smp * (size_t)P * P4);
+        const int py = rem / P4, px = (rem - (rem / P4) * P4) * 4;
+        const int y = wrap_idx(py - G, n), x = wrap_idx(px - G, n);
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(u + smp * (size_t)n * n + (size_t)y * n + x));
+        *reinterpret_cast<float4 *>(dst + smp * (size_t)P * P + (size_t)py * P + px) = v;
+    }
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+static mfmc_status encode_map(CUtensorMap *map, float *base, int P, size_t cap, int sw, int sh) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return fail(MFMC_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+    const cuuint64_t dims[3] = {(cuuint64_t)P, (cuuint64_t)P, (cuuint64_t)cap};
+    const cuuint64_t strides[2] = {(cuuint64_t)P * sizeof(float), (cuuint64_t)P * P * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)sw, (cuuint32_t)sh, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(MFMC_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return MFMC_OK;
+}
+
+static mfmc_status ensure_pad_scratch(Model &m, size_t ns, const TmaVariant &L) {
+    const int G = (m.R + 3) & ~3, P = m.d.n + 2 * G;
+    if (!m.d_status) {
+        MFMC_CUDA(cudaMalloc((void **)&m.d_status, sizeof(int)));
+        MFMC_CUDA(cudaMemset(m.d_status, 0, sizeof(int)));
+    }
+    if (m.pad_cap < ns || !m.padA || !m.padB) {
+        cudaFree(m.padA);
+        cudaFree(m.padB);
+        m.padA = m.padB = nullptr;
+        m.pad_cap = 0;
+        m.maps_valid = 0;
+        const size_t bytes = ns * (size_t)P * P * sizeof(float);
+        MFMC_CUDA(cudaMalloc((void **)&m.padA, bytes));
+        MFMC_CUDA(cudaMalloc((void **)&m.padB, bytes));
+        m.pad_cap = ns;
+    }
+    if (m.maps_valid && m.map_sw == L.sw && m.map_sh == L.sh) return MFMC_OK;
+    m.maps_valid = 0;
+    mfmc_status s = encode_map(&m.mapA, m.padA, P, m.pad_cap, L.sw, L.sh);
+    if (s == MFMC_OK) s = encode_map(&m.mapB, m.padB, P, m.pad_cap, L.sw, L.sh);
+    if (s != MFMC_OK) return s;
+    m.map_sw = L.sw;
+    m.map_sh = L.sh;
+    m.maps_valid = 1;
+    return MFMC_OK;
+}
+
+mfmc_status run_solve_tma(Model &m, int kahan, int variant, const StepCoef *coef, const float *u0, size_t ns,
+                          int nsteps, float *uT, double *ubar, double *ooi, cudaStream_t st) {
+    const TmaLauncher *TL = tma_launcher(m.R);
+    if (!TL) return fail(MFMC_EINVAL, "no TMA kernel for R = %d", m.R);
+    if (kahan) variant = 0;
+    if (variant < 0 || variant >= kTmaVariants || !TL->v[variant].fn[kahan ? 2 : 1])
+        return fail(MFMC_EINVAL, "TMA variant %d unavailable", variant);
+    const TmaVariant *L = &TL->v[variant];
+    const int n = m.d.n, G = (m.R + 3) & ~3, P = n + 2 * G;
+    const int tiles_x = (n + L->tx - 1) / L->tx;
+    const int tiles = tiles_x * ((n + L->ty - 1) / L->ty);
+    mfmc_status s = ensure_pad_scratch(m, ns, *L);
+    if (s == MFMC_OK) s = grow_buffer(&m.partials, &m.partials_cap, ns * (size_t)tiles);
+    if (s != MFMC_OK) return s;
+    {
+        const size_t total = ns * (size_t)P * (P / 4);
+        const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 32);
+        pad_fields_kernel<<<blocks, 256, 0, st>>>(u0, m.padB, n, G, ns);
+        MFMC_CUDA(cudaGetLastError());
+    }
+    int dev = 0, sms = 0;
+    MFMC_CUDA(cudaGetDevice(&dev));
+    MFMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const long long total = (long long)ns * tiles;
+    if (total > (1ll << 30)) return fail(MFMC_EINVAL, "too many tiles in one solve");
+    const int grid = (int)std::min<long long>(total, (long long)sms * L->blocks_per_sm());
+    const CUtensorMap *src = &m.mapB;
+    float *dstbuf = m.padA;
+    for (int k = 1; k <= nsteps; ++k) {
+        const bool last = k == nsteps;
+        TmaArgs a;
+        a.dst = last ? nullptr : dstbuf;
+        a.dst_plain = last ? uT : nullptr;
+        a.coef = coef;
+        a.partials = m.partials;
+        a.status = m.d_status;
+        a.n = n;
+        a.P = P;
+        a.tiles_x = tiles_x;
+        a.tiles = tiles;
+        a.total = (int)total;
+        a.last = last ? 1 : 0;
+        s = L->fn[kahan ? 2 : 1](*src, a, grid, st);
+        if (s != MFMC_OK) return s;
+        src = (dstbuf == m.padA) ? &m.mapA : &m.mapB;
+        dstbuf = (dstbuf == m.padA) ? m.padB : m.padA;
+    }
+    finalize_ooi_kernel<<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(m.partials, tiles, ns,
+                                                                       1.0 / ((double)n * n), ubar, ooi);
+    MFMC_CUDA(cudaGetLastError());
+    return MFMC_OK;
+}
+
 mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0, size_t ns, int nsteps,
                       float *uT, double *ubar, double *ooi, cudaStream_t st) {
     if (ns == 0) return MFMC_OK;
@@ -293,6 +422,9 @@ mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0,
         MFMC_CUDA(cudaGetLastError());
         return MFMC_OK;
     }
+    if (algo == MFMC_ALGO_PREFIX_TMA)
+        return run_solve_tma(m, 0, m.tma_variant, coef, u0, ns, nsteps, uT, ubar, ooi, st);
+    if (algo == MFMC_ALGO_PREFIX_KAHAN) return run_solve_tma(m, 1, 0, coef, u0, ns, nsteps, uT, ubar, ooi, st);
     if (algo == MFMC_ALGO_RESIDENT) {
         ResidentArgs a;
         a.u0 = u0;
@@ -312,7 +444,7 @@ mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0,
 
     const bool constant = m.d.kernel == MFMC_KERNEL_CONSTANT;
     const TileLauncher *L = tile_launcher(m.R);
-    const int ai = algo == MFMC_ALGO_DIRECT ? 0 : (algo == MFMC_ALGO_PREFIX ? 1 : 2);
+    const int ai = algo == MFMC_ALGO_DIRECT ? 0 : 1;
     const bool tiled = algo != MFMC_ALGO_PLAIN && constant && L && L->fn[ai];
 
     if (algo == MFMC_ALGO_PLAIN) {

@@ -1,5 +1,5 @@
 // Resident (whole field in shared memory) kernels for R in {1, ..., 6, 8}.
-#include "step_kernels.cuh"
+#include "tma_step.cuh"
 
 namespace mfmc {
 
@@ -22,6 +22,21 @@ const TileLauncher *tile_launcher_c(int R);
 const TileLauncher *tile_launcher_d(int R);
 const TileLauncher *tile_launcher_e(int R);
 const TileLauncher *tile_launcher_f(int R);
+
+const TmaLauncher *tma_launcher_a(int R);
+const TmaLauncher *tma_launcher_b(int R);
+const TmaLauncher *tma_launcher_c(int R);
+const TmaLauncher *tma_launcher_d(int R);
+const TmaLauncher *tma_launcher_e(int R);
+const TmaLauncher *tma_launcher_f(int R);
+
+const TmaLauncher *tma_launcher(int R) {
+    const TmaLauncher *(*groups[6])(int) = {tma_launcher_a, tma_launcher_b, tma_launcher_c,
+                                            tma_launcher_d, tma_launcher_e, tma_launcher_f};
+    for (auto g : groups)
+        if (const TmaLauncher *t = g(R)) return t;
+    return nullptr;
+}
 
 const TileLauncher *tile_launcher(int R) {
     const TileLauncher *(*groups[6])(int) = {tile_launcher_a, tile_launcher_b, tile_launcher_c,

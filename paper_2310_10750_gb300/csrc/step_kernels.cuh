@@ -385,7 +385,7 @@ TileLauncher make_tile_launcher() {
         L.fn[0] = nullptr;
     }
     L.fn[1] = &launch_tile<R, 1>;
-    L.fn[2] = &launch_tile<R, 2>;
+    L.fn[2] = nullptr;  // the compensated form runs on the TMA pipeline
     return L;
 }
 

@@ -1,5 +1,5 @@
 // Register-tiled step kernels for R in {1, 2, 3, 4}.
-#include "step_kernels.cuh"
+#include "tma_step.cuh"
 
 namespace mfmc {
 
@@ -13,6 +13,20 @@ const TileLauncher *tile_launcher_a(int R) {
         case 2: return &t2;
         case 3: return &t3;
         case 4: return &t4;
+        default: return nullptr;
+    }
+}
+
+const TmaLauncher *tma_launcher_a(int R) {
+    static const TmaLauncher m1 = make_tma_launcher<1>();
+    static const TmaLauncher m2 = make_tma_launcher<2>();
+    static const TmaLauncher m3 = make_tma_launcher<3>();
+    static const TmaLauncher m4 = make_tma_launcher<4>();
+    switch (R) {
+        case 1: return &m1;
+        case 2: return &m2;
+        case 3: return &m3;
+        case 4: return &m4;
         default: return nullptr;
     }
 }

@@ -1,5 +1,5 @@
 // Register-tiled step kernels for R in {5, 6, 8}.
-#include "step_kernels.cuh"
+#include "tma_step.cuh"
 
 namespace mfmc {
 
@@ -11,6 +11,18 @@ const TileLauncher *tile_launcher_b(int R) {
         case 5: return &t5;
         case 6: return &t6;
         case 8: return &t8;
+        default: return nullptr;
+    }
+}
+
+const TmaLauncher *tma_launcher_b(int R) {
+    static const TmaLauncher m5 = make_tma_launcher<5>();
+    static const TmaLauncher m6 = make_tma_launcher<6>();
+    static const TmaLauncher m8 = make_tma_launcher<8>();
+    switch (R) {
+        case 5: return &m5;
+        case 6: return &m6;
+        case 8: return &m8;
         default: return nullptr;
     }
 }

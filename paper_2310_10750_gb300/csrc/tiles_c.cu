@@ -1,5 +1,5 @@
 // Register-tiled step kernels for R in {11, 12}.
-#include "step_kernels.cuh"
+#include "tma_step.cuh"
 
 namespace mfmc {
 
@@ -9,6 +9,16 @@ const TileLauncher *tile_launcher_c(int R) {
     switch (R) {
         case 11: return &t11;
         case 12: return &t12;
+        default: return nullptr;
+    }
+}
+
+const TmaLauncher *tma_launcher_c(int R) {
+    static const TmaLauncher m11 = make_tma_launcher<11>();
+    static const TmaLauncher m12 = make_tma_launcher<12>();
+    switch (R) {
+        case 11: return &m11;
+        case 12: return &m12;
         default: return nullptr;
     }
 }

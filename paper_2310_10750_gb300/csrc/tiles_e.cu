@@ -1,5 +1,5 @@
 // Register-tiled step kernels for R in {22, 24}.
-#include "step_kernels.cuh"
+#include "tma_step.cuh"
 
 namespace mfmc {
 
@@ -9,6 +9,16 @@ const TileLauncher *tile_launcher_e(int R) {
     switch (R) {
         case 22: return &t22;
         case 24: return &t24;
+        default: return nullptr;
+    }
+}
+
+const TmaLauncher *tma_launcher_e(int R) {
+    static const TmaLauncher m22 = make_tma_launcher<22>();
+    static const TmaLauncher m24 = make_tma_launcher<24>();
+    switch (R) {
+        case 22: return &m22;
+        case 24: return &m24;
         default: return nullptr;
     }
 }

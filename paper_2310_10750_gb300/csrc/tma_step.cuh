@@ -1,0 +1,318 @@
+// Persistent streaming step kernel with TMA tile loads.
+//
+// Fields between steps live in library scratch with a periodic ghost frame of width
+// G = R4 (R rounded up to a multiple of 4): a padded n+2G square per sample whose frame
+// holds the periodic images of the opposite edges.  A tile plus its R-wide halo is then
+// one contiguous box of the padded array, fetched by one cp.async.bulk.tensor (TMA)
+// copy without any index wrapping.  Each CTA loops over (sample, tile) items with two
+// shared-memory stages: the TMA copy of the next item is in flight while the current one
+// is computed.  Every output is written to its interior position and, near an edge, to
+// its ghost images, so the next step's tiles find their halos in place.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "step_kernels.cuh"
+
+namespace mfmc {
+
+struct TmaArgs {
+    float *dst;            // padded destination (nullptr: no field output)
+    float *dst_plain;      // unpadded destination (last step with a final field), or nullptr
+    const StepCoef *coef;
+    double *partials;      // [ns][tiles], written at the last step
+    int *status;           // set to 1 when a bounded wait gives up
+    int n, P, tiles_x, tiles, total, last;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y,
+                                            int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+        "[%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+template <int R, int RY, int TXT, int TYT>
+struct TmaCfg {
+    static constexpr int R4 = (R + 3) & ~3;
+    static constexpr int TX = 4 * TXT, TY = RY * TYT;
+    static constexpr int SW = TX + 2 * R4, SH = TY + 2 * R;
+    static constexpr int STAGE_FLOATS = ((SW * SH + 255) / 256) * 256;  // 1 KB aligned stages
+    static constexpr size_t SMEM = 2 * (size_t)STAGE_FLOATS * sizeof(float) + 1024;
+    static constexpr uint32_t BOX_BYTES = (uint32_t)SW * SH * sizeof(float);
+};
+
+constexpr long long kWaitLimit = 1ll << 24;
+
+template <int R, int RY, int TXT, int TYT, int ALGO>
+__global__ void __launch_bounds__(TXT *TYT) step_tma_kernel(const __grid_constant__ CUtensorMap src_map,
+                                                            TmaArgs a) {
+    using C = TmaCfg<R, RY, TXT, TYT>;
+    constexpr int RX = 4, R4 = C::R4, SW = C::SW, NT = TXT * TYT, WIN = RX + 2 * R4;
+    constexpr DiscRows<R> disc{};
+    extern __shared__ unsigned char smem_raw[];
+    float *base = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ double red[(NT + 31) / 32];
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    __syncthreads();
+
+    const int n = a.n, G = R4;
+    auto issue = [&](int item, int stage) {
+        const int sample = item / a.tiles, tile = item - sample * a.tiles;
+        const int x0 = (tile % a.tiles_x) * C::TX, y0 = (tile / a.tiles_x) * C::TY;
+        mbar_expect_tx(&bars[stage], C::BOX_BYTES);
+        // padded coordinates of the halo corner: (G + x0 - R4, G + y0 - R) = (x0, y0 + R4 - R)
+        tma_load_3d(base + stage * C::STAGE_FLOATS, &src_map, &bars[stage], x0, y0 + R4 - R, sample);
+    };
+
+    const int tx = tid % TXT, ty = tid / TXT, ox = tx * RX, oy = ty * RY;
+    int k = 0;
+    if (tid == 0 && (int)blockIdx.x < a.total) issue(blockIdx.x, 0);
+    for (int item = blockIdx.x; item < a.total; item += gridDim.x, ++k) {
+        const int stage = k & 1;
+        if (tid == 0 && item + (int)gridDim.x < a.total) issue(item + gridDim.x, stage ^ 1);
+        // bounded wait for this stage's copy
+        long long spins = 0;
+        while (!mbar_try_wait(&bars[stage], (uint32_t)((k >> 1) & 1))) {
+            if (++spins > kWaitLimit) {
+                abort_flag = 1;
+                break;
+            }
+        }
+        __syncthreads();
+        if (abort_flag) {
+            if (tid == 0) atomicExch(a.status, 1);
+            break;
+        }
+        const float *s = base + stage * C::STAGE_FLOATS;
+        const int sample = item / a.tiles, tile = item - sample * a.tiles;
+        const int x0 = (tile % a.tiles_x) * C::TX, y0 = (tile / a.tiles_x) * C::TY;
+
+        float acc[RY][RX];
+        float cmp[ALGO == 2 ? RY : 1][RX];
+#pragma unroll
+        for (int j = 0; j < RY; ++j)
+#pragma unroll
+            for (int i = 0; i < RX; ++i) {
+                acc[j][i] = 0.f;
+                cmp[ALGO == 2 ? j : 0][i] = 0.f;
+            }
+#pragma unroll
+        for (int r = 0; r < RY + 2 * R; ++r) {
+            const float4 *rowp = reinterpret_cast<const float4 *>(s + (oy + r) * SW + ox);
+            float v[WIN];
+#pragma unroll
+            for (int q = 0; q < WIN / 4; ++q) {
+                const float4 t = rowp[q];
+                v[4 * q + 0] = t.x;
+                v[4 * q + 1] = t.y;
+                v[4 * q + 2] = t.z;
+                v[4 * q + 3] = t.w;
+            }
+            float p[RX + 2 * R + 1];
+            p[0] = 0.f;
+#pragma unroll
+            for (int q = 0; q < RX + 2 * R; ++q) p[q + 1] = p[q] + v[R4 - R + q];
+#pragma unroll
+            for (int j = 0; j < RY; ++j) {
+                const int dy = r - R - j;
+                if (dy >= -R && dy <= R) {
+                    const int w = disc.w[dy < 0 ? -dy : dy];
+#pragma unroll
+                    for (int i = 0; i < RX; ++i) {
+                        const float h = p[i + R + w + 1] - p[i + R - w];
+                        if (ALGO != 2) {
+                            acc[j][i] += h;
+                        } else {
+                            const float y = h - cmp[ALGO == 2 ? j : 0][i];
+                            const float t = acc[j][i] + y;
+                            cmp[ALGO == 2 ? j : 0][i] = (t - acc[j][i]) - y;
+                            acc[j][i] = t;
+                        }
+                    }
+                }
+            }
+        }
+
+        const StepCoef cf = a.coef[sample];
+        double part = 0.0;
+        const size_t nn = (size_t)n * n, PP = (size_t)a.P * a.P;
+#pragma unroll
+        for (int j = 0; j < RY; ++j) {
+            const float4 c4v = *reinterpret_cast<const float4 *>(s + (oy + j + R) * SW + ox + R4);
+            const float uc[4] = {c4v.x, c4v.y, c4v.z, c4v.w};
+            float o[4];
+#pragma unroll
+            for (int i = 0; i < RX; ++i) {
+                const float sd = fmaf(-cf.c0, uc[i], acc[j][i]);
+                const float v = uc[i] + fmaf(cf.c1, sd, cf.c2 * uc[i]);
+                o[i] = fminf(1.f, fmaxf(-1.f, v));
+            }
+            const int y = y0 + oy + j, x = x0 + ox;
+            if (y < n && x < n) {
+                const float4 val = make_float4(o[0], o[1], o[2], o[3]);
+                if (a.dst_plain) {
+                    *reinterpret_cast<float4 *>(a.dst_plain + sample * nn + (size_t)y * n + x) = val;
+                } else if (a.dst) {
+                    float *d = a.dst + sample * PP;
+                    const int rows[3] = {G + y, y < G ? G + y + n : -1, y >= n - G ? G + y - n : -1};
+                    const int cols[3] = {G + x, x < G ? G + x + n : -1, x >= n - G ? G + x - n : -1};
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        if (rows[q] < 0) continue;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            if (cols[c] < 0) continue;
+                            *reinterpret_cast<float4 *>(d + (size_t)rows[q] * a.P + cols[c]) = val;
+                        }
+                    }
+                }
+                if (a.last) part += ((double)o[0] + (double)o[1]) + ((double)o[2] + (double)o[3]);
+            }
+        }
+        if (a.last) {
+            const double t = block_sum_fixed<NT>(part, red);
+            if (tid == 0) a.partials[(size_t)sample * a.tiles + tile] = t;
+        }
+        __syncthreads();  // every thread is done with this stage before it is refilled
+    }
+}
+
+// Copy unpadded fields [ns][n][n] into padded scratch [ns][P][P] including the frame
+// (defined in nlch_solver.cu).
+__global__ void pad_fields_kernel(const float *u, float *dst, int n, int G, size_t ns);
+
+// --------------------------------------------------------------------------- host side
+// Tile shapes (rows per thread RY, threads along x TXT, threads along y TYT):
+//   variant 0: 4 x 16 outputs per thread, 64 x 128 tile, 128 threads
+//   variant 1: 4 x 8 outputs per thread,  64 x 128 tile, 256 threads
+//   variant 2: 4 x 8 outputs per thread,  64 x 64 tile,  128 threads
+constexpr int kTmaVariants = 3;
+
+template <int V>
+struct TmaShape;
+template <>
+struct TmaShape<0> {
+    static constexpr int RY = 16, TXT = 16, TYT = 8;
+};
+template <>
+struct TmaShape<1> {
+    static constexpr int RY = 8, TXT = 16, TYT = 16;
+};
+template <>
+struct TmaShape<2> {
+    static constexpr int RY = 8, TXT = 16, TYT = 8;
+};
+
+typedef mfmc_status (*TmaFn)(const CUtensorMap &, const TmaArgs &, int grid, cudaStream_t);
+
+struct TmaVariant {
+    int tx, ty, sw, sh, threads;
+    size_t smem;
+    TmaFn fn[3];  // [algo]: unused, prefix, prefix-Kahan
+    int (*blocks_per_sm)();
+};
+
+struct TmaLauncher {
+    TmaVariant v[kTmaVariants];
+};
+
+template <int R, int V, int ALGO>
+mfmc_status launch_tma(const CUtensorMap &map, const TmaArgs &a, int grid, cudaStream_t st) {
+    using T = TmaShape<V>;
+    using C = TmaCfg<R, T::RY, T::TXT, T::TYT>;
+    auto kern = step_tma_kernel<R, T::RY, T::TXT, T::TYT, ALGO>;
+    static bool attr_done = false;
+    if (!attr_done) {
+        MFMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+        attr_done = true;
+    }
+    kern<<<grid, T::TXT * T::TYT, C::SMEM, st>>>(map, a);
+    MFMC_CUDA(cudaGetLastError());
+    return MFMC_OK;
+}
+
+template <int R, int V>
+int tma_blocks_per_sm() {
+    using T = TmaShape<V>;
+    using C = TmaCfg<R, T::RY, T::TXT, T::TYT>;
+    auto k = step_tma_kernel<R, T::RY, T::TXT, T::TYT, 1>;
+    int per = 0;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, T::TXT * T::TYT, C::SMEM);
+    return e == cudaSuccess && per > 0 ? per : 1;
+}
+
+template <int R, int V, bool KAHAN>
+TmaVariant make_tma_variant() {
+    using T = TmaShape<V>;
+    using C = TmaCfg<R, T::RY, T::TXT, T::TYT>;
+    TmaVariant L;
+    L.tx = C::TX;
+    L.ty = C::TY;
+    L.sw = C::SW;
+    L.sh = C::SH;
+    L.threads = T::TXT * T::TYT;
+    L.smem = C::SMEM;
+    L.fn[0] = nullptr;
+    L.fn[1] = &launch_tma<R, V, 1>;
+    if constexpr (KAHAN) {
+        L.fn[2] = &launch_tma<R, V, 2>;
+    } else {
+        L.fn[2] = nullptr;
+    }
+    L.blocks_per_sm = &tma_blocks_per_sm<R, V>;
+    return L;
+}
+
+template <int R>
+TmaLauncher make_tma_launcher() {
+    TmaLauncher L;
+    L.v[0] = make_tma_variant<R, 0, true>();
+    L.v[1] = make_tma_variant<R, 1, false>();
+    L.v[2] = make_tma_variant<R, 2, false>();
+    return L;
+}
+
+// Defined in the per-R translation units.
+const TmaLauncher *tma_launcher(int R);
+
+}  // namespace mfmc

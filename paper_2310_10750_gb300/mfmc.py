@@ -25,7 +25,7 @@ MFMC_OK, MFMC_EINVAL, MFMC_ENOMEM, MFMC_ECUDA, MFMC_ETIMEOUT, MFMC_EBUDGET, MFMC
 KERNEL_CONSTANT, KERNEL_GAUSSIAN = 0, 1
 BC_PERIODIC = 0
 IC_UNIFORM, IC_SMOOTHED_GAUSS, IC_NUCLEI = 0, 1, 2
-ALGO_AUTO, ALGO_DIRECT, ALGO_PREFIX, ALGO_PREFIX_KAHAN, ALGO_RESIDENT, ALGO_PLAIN = range(6)
+ALGO_AUTO, ALGO_DIRECT, ALGO_PREFIX, ALGO_PREFIX_KAHAN, ALGO_RESIDENT, ALGO_PLAIN, ALGO_PREFIX_TMA = range(7)
 MAX_MODELS = 16
 
 
@@ -51,7 +51,8 @@ class mfmc_sample_params(ctypes.Structure):
 
 class mfmc_model_info(ctypes.Structure):
     _fields_ = [("R", ctypes.c_int), ("disc_points", ctypes.c_int), ("c_gamma", ctypes.c_double),
-                ("xi", ctypes.c_double), ("algo", ctypes.c_int), ("field_bytes", ctypes.c_size_t)]
+                ("xi", ctypes.c_double), ("algo", ctypes.c_int), ("field_bytes", ctypes.c_size_t),
+                ("tile_variant", ctypes.c_int)]
 
 
 _D16 = ctypes.c_double * MAX_MODELS
@@ -91,6 +92,7 @@ _sig("mfmc_last_error", ctypes.c_char_p, [])
 _sig("mfmc_model_create", _st, [ctypes.POINTER(mfmc_model_desc), ctypes.POINTER(_vp)])
 _sig("mfmc_model_destroy", None, [_vp])
 _sig("mfmc_model_query", _st, [_vp, ctypes.POINTER(mfmc_model_info)])
+_sig("mfmc_model_set_tile_variant", _st, [_vp, ctypes.c_int])
 _sig("mfmc_sample_eps", _st, [_vp, _vp, _vp, ctypes.c_size_t, _vp])
 _sig("mfmc_init_fields", _st, [_vp, _vp, _vp, ctypes.c_size_t, _vp, _vp])
 _sig("mfmc_solve_fields", _st, [_vp, _vp, _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp])
@@ -159,6 +161,9 @@ class Model:
             _L.mfmc_model_destroy(h)
             self.handle = None
 
+    def set_tile_variant(self, variant: int):
+        _check(_L.mfmc_model_set_tile_variant(self.handle, variant))
+
     def info(self) -> mfmc_model_info:
         out = mfmc_model_info()
         _check(_L.mfmc_model_query(self.handle, ctypes.byref(out)))
@@ -167,6 +172,10 @@ class Model:
 
 def mfmc_model_create(**kw) -> Model:
     return Model(**kw)
+
+
+def mfmc_model_set_tile_variant(model: Model, variant: int):
+    model.set_tile_variant(variant)
 
 
 def make_params(ns, eps=None, theta=None):

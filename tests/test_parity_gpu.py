@@ -11,6 +11,7 @@ Tolerances (derived from the arithmetic; see the design notes):
     error grows at most additively: k * 4e-6 * max|u| * e^{c_F T}; the OoI f is the mean
     of u and gets the same bound; the target is |f_gpu - f_orc| <= 1e-5 f_orc.
 """
+import itertools
 import math
 
 import numpy as np
@@ -20,18 +21,25 @@ import oracle as O
 
 pytestmark = pytest.mark.gpu
 
-ALGOS = ["prefix", "direct", "kahan", "resident", "plain"]
+ALGOS = ["prefix", "direct", "kahan", "resident", "plain", "tma", "tma1", "tma2"]
 
 
 def algo_id(mf, name):
     return {"prefix": mf.ALGO_PREFIX, "direct": mf.ALGO_DIRECT, "kahan": mf.ALGO_PREFIX_KAHAN,
-            "resident": mf.ALGO_RESIDENT, "plain": mf.ALGO_PLAIN, "auto": mf.ALGO_AUTO}[name]
+            "resident": mf.ALGO_RESIDENT, "plain": mf.ALGO_PLAIN, "auto": mf.ALGO_AUTO,
+            "tma": mf.ALGO_PREFIX_TMA, "tma1": mf.ALGO_PREFIX_TMA, "tma2": mf.ALGO_PREFIX_TMA}[name]
+
+
+def variant_of(name):
+    return {"tma": 0, "tma1": 1, "tma2": 2}.get(name)
 
 
 def pair(mf, n, R, steps, ic=0, eps=0.03, eps_lo=0.0, eps_hi=0.0, kernel=0, delta_hf=0.0, tau=1e-3,
          ic_amp=0.05, ic_base_n=0, algo="prefix"):
     g = mf.Model(n=n, delta=R / n, kernel=kernel, delta_hf=delta_hf, eps=eps, eps_lo=eps_lo, eps_hi=eps_hi,
                  tau=tau, nsteps=steps, ic=ic, ic_amp=ic_amp, ic_base_n=ic_base_n, algo=algo_id(mf, algo))
+    if variant_of(algo) is not None:
+        g.set_tile_variant(variant_of(algo))
     o = O.OracleModel(n=n, delta=R / n, kernel=kernel, delta_hf=delta_hf, eps=eps, eps_lo=eps_lo, eps_hi=eps_hi,
                       tau=tau, nsteps=steps, ic=ic, ic_amp=ic_amp, ic_base_n=ic_base_n)
     return g, o
@@ -91,6 +99,8 @@ def test_one_step_elementwise(gpu_lib, algo, n, R):
     o = O.OracleModel(n=n, delta=R / n, eps=0.03, tau=5e-3, nsteps=1, ic=2)
     try:
         g = mf.Model(n=n, delta=R / n, eps=0.03, tau=5e-3, nsteps=1, ic=2, algo=algo_id(mf, algo))
+        if variant_of(algo) is not None:
+            g.set_tile_variant(variant_of(algo))
     except mf.MfmcError:
         pytest.skip(f"{algo} does not support n={n}, R={R}")
     seeds = seeds_of(3, base=7)
@@ -119,7 +129,7 @@ def test_plain_mc_config_64_R4(gpu_lib, algo):
         assert abs(ubar[i] - mean) <= 2 * tol
 
 
-@pytest.mark.parametrize("algo", ["prefix", "resident", "direct"])
+@pytest.mark.parametrize("algo", ["prefix", "resident", "direct", "tma"])
 def test_nuclei_obstacle_active_and_bounds_exact(gpu_lib, algo):
     mf = gpu_lib
     g, o = pair(mf, 64, 4, 120, ic=2, tau=5e-3, algo=algo)
@@ -136,8 +146,8 @@ def test_nuclei_obstacle_active_and_bounds_exact(gpu_lib, algo):
 
 def test_ragged_tiles_and_many_tiles(gpu_lib):
     mf = gpu_lib
-    for n, R in ((68, 3), (132, 5), (200, 8)):
-        g, o = pair(mf, n, R, 20, ic=2, tau=5e-3, algo="prefix")
+    for (n, R), algo in itertools.product(((68, 3), (132, 5), (200, 8)), ("prefix", "tma", "tma1", "tma2")):
+        g, o = pair(mf, n, R, 20, ic=2, tau=5e-3, algo=algo)
         seeds = seeds_of(2, base=n)
         _, uT, f, _ = gpu_solve(mf, g, seeds)
         for i, s in enumerate(seeds):
@@ -161,8 +171,10 @@ def test_gaussian_kernel_generic_path(gpu_lib):
 def test_stationary_states_exact(gpu_lib):
     import torch
     mf = gpu_lib
-    for algo in ("prefix", "resident", "direct", "kahan"):
+    for algo in ("prefix", "resident", "direct", "kahan", "tma", "tma1", "tma2"):
         g = mf.Model(n=64, delta=4 / 64, nsteps=50, algo=algo_id(mf, algo))
+        if variant_of(algo) is not None:
+            g.set_tile_variant(variant_of(algo))
         for c in (1.0, -1.0, 0.0):
             u0 = torch.full((2, 64, 64), c, dtype=torch.float32, device="cuda")
             uT = torch.empty_like(u0)
