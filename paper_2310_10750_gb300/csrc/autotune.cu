@@ -33,7 +33,7 @@ mfmc_status autotune(Model &m, cudaStream_t st) {
     for (int a : {MFMC_ALGO_RESIDENT, MFMC_ALGO_PREFIX_TMA, MFMC_ALGO_PREFIX, MFMC_ALGO_DIRECT}) {
         if (!algo_supported(m, a)) continue;
         if (a == MFMC_ALGO_PREFIX_TMA)
-            for (int v = 0; v < 3; ++v) cands.push_back({a, v});
+            for (int v = 0; v < 5; ++v) cands.push_back({a, v});
         else
             cands.push_back({a, 0});
     }

@@ -205,7 +205,7 @@ mfmc_status mfmc_model_query(const mfmc_model *m, mfmc_model_info *out) {
 }
 
 mfmc_status mfmc_model_set_tile_variant(mfmc_model *m, int variant) {
-    if (!m || variant < 0 || variant > 2) return fail(MFMC_EINVAL, "invalid tile variant");
+    if (!m || variant < 0 || variant > 4) return fail(MFMC_EINVAL, "invalid tile variant");
     std::lock_guard<std::mutex> lk(m->mu);
     m->tma_variant = variant;
     return MFMC_OK;

@@ -61,22 +61,25 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
-template <int R, int RY, int TXT, int TYT>
+template <int R, int RY, int TXT, int TYT, int STAGES = 2>
 struct TmaCfg {
     static constexpr int R4 = (R + 3) & ~3;
     static constexpr int TX = 4 * TXT, TY = RY * TYT;
     static constexpr int SW = TX + 2 * R4, SH = TY + 2 * R;
     static constexpr int STAGE_FLOATS = ((SW * SH + 255) / 256) * 256;  // 1 KB aligned stages
-    static constexpr size_t SMEM = 2 * (size_t)STAGE_FLOATS * sizeof(float) + 1024;
+    static constexpr size_t SMEM = STAGES * (size_t)STAGE_FLOATS * sizeof(float) + 1024;
     static constexpr uint32_t BOX_BYTES = (uint32_t)SW * SH * sizeof(float);
 };
 
 constexpr long long kWaitLimit = 1ll << 24;
 
-template <int R, int RY, int TXT, int TYT, int ALGO>
+// STAGES = 2: the next item's copy is issued before computing the current one;
+// STAGES = 1: it is issued after the current item is done (less shared memory per CTA,
+// so more CTAs per SM overlap their copies with each other's compute).
+template <int R, int RY, int TXT, int TYT, int ALGO, int STAGES = 2>
 __global__ void __launch_bounds__(TXT *TYT) step_tma_kernel(const __grid_constant__ CUtensorMap src_map,
                                                             TmaArgs a) {
-    using C = TmaCfg<R, RY, TXT, TYT>;
+    using C = TmaCfg<R, RY, TXT, TYT, STAGES>;
     constexpr int RX = 4, R4 = C::R4, SW = C::SW, NT = TXT * TYT, WIN = RX + 2 * R4;
     constexpr DiscRows<R> disc{};
     extern __shared__ unsigned char smem_raw[];
@@ -107,11 +110,12 @@ __global__ void __launch_bounds__(TXT *TYT) step_tma_kernel(const __grid_constan
     int k = 0;
     if (tid == 0 && (int)blockIdx.x < a.total) issue(blockIdx.x, 0);
     for (int item = blockIdx.x; item < a.total; item += gridDim.x, ++k) {
-        const int stage = k & 1;
-        if (tid == 0 && item + (int)gridDim.x < a.total) issue(item + gridDim.x, stage ^ 1);
+        const int stage = STAGES == 2 ? (k & 1) : 0;
+        const uint32_t parity = STAGES == 2 ? (uint32_t)((k >> 1) & 1) : (uint32_t)(k & 1);
+        if (STAGES == 2 && tid == 0 && item + (int)gridDim.x < a.total) issue(item + gridDim.x, stage ^ 1);
         // bounded wait for this stage's copy
         long long spins = 0;
-        while (!mbar_try_wait(&bars[stage], (uint32_t)((k >> 1) & 1))) {
+        while (!mbar_try_wait(&bars[stage], parity)) {
             if (++spins > kWaitLimit) {
                 abort_flag = 1;
                 break;
@@ -213,6 +217,7 @@ __global__ void __launch_bounds__(TXT *TYT) step_tma_kernel(const __grid_constan
             if (tid == 0) a.partials[(size_t)sample * a.tiles + tile] = t;
         }
         __syncthreads();  // every thread is done with this stage before it is refilled
+        if (STAGES == 1 && tid == 0 && item + (int)gridDim.x < a.total) issue(item + gridDim.x, 0);
     }
 }
 
@@ -225,21 +230,30 @@ __global__ void pad_fields_kernel(const float *u, float *dst, int n, int G, size
 //   variant 0: 4 x 16 outputs per thread, 64 x 128 tile, 128 threads
 //   variant 1: 4 x 8 outputs per thread,  64 x 128 tile, 256 threads
 //   variant 2: 4 x 8 outputs per thread,  64 x 64 tile,  128 threads
-constexpr int kTmaVariants = 3;
+//   variants 3, 4: shapes 0 and 1 with a single shared-memory stage
+constexpr int kTmaVariants = 5;
 
 template <int V>
 struct TmaShape;
 template <>
 struct TmaShape<0> {
-    static constexpr int RY = 16, TXT = 16, TYT = 8;
+    static constexpr int RY = 16, TXT = 16, TYT = 8, STAGES = 2;
 };
 template <>
 struct TmaShape<1> {
-    static constexpr int RY = 8, TXT = 16, TYT = 16;
+    static constexpr int RY = 8, TXT = 16, TYT = 16, STAGES = 2;
 };
 template <>
 struct TmaShape<2> {
-    static constexpr int RY = 8, TXT = 16, TYT = 8;
+    static constexpr int RY = 8, TXT = 16, TYT = 8, STAGES = 2;
+};
+template <>
+struct TmaShape<3> {
+    static constexpr int RY = 16, TXT = 16, TYT = 8, STAGES = 1;
+};
+template <>
+struct TmaShape<4> {
+    static constexpr int RY = 8, TXT = 16, TYT = 16, STAGES = 1;
 };
 
 typedef mfmc_status (*TmaFn)(const CUtensorMap &, const TmaArgs &, int grid, cudaStream_t);
@@ -258,8 +272,8 @@ struct TmaLauncher {
 template <int R, int V, int ALGO>
 mfmc_status launch_tma(const CUtensorMap &map, const TmaArgs &a, int grid, cudaStream_t st) {
     using T = TmaShape<V>;
-    using C = TmaCfg<R, T::RY, T::TXT, T::TYT>;
-    auto kern = step_tma_kernel<R, T::RY, T::TXT, T::TYT, ALGO>;
+    using C = TmaCfg<R, T::RY, T::TXT, T::TYT, T::STAGES>;
+    auto kern = step_tma_kernel<R, T::RY, T::TXT, T::TYT, ALGO, T::STAGES>;
     static bool attr_done = false;
     if (!attr_done) {
         MFMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
@@ -273,8 +287,8 @@ mfmc_status launch_tma(const CUtensorMap &map, const TmaArgs &a, int grid, cudaS
 template <int R, int V>
 int tma_blocks_per_sm() {
     using T = TmaShape<V>;
-    using C = TmaCfg<R, T::RY, T::TXT, T::TYT>;
-    auto k = step_tma_kernel<R, T::RY, T::TXT, T::TYT, 1>;
+    using C = TmaCfg<R, T::RY, T::TXT, T::TYT, T::STAGES>;
+    auto k = step_tma_kernel<R, T::RY, T::TXT, T::TYT, 1, T::STAGES>;
     int per = 0;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, T::TXT * T::TYT, C::SMEM);
@@ -284,7 +298,7 @@ int tma_blocks_per_sm() {
 template <int R, int V, bool KAHAN>
 TmaVariant make_tma_variant() {
     using T = TmaShape<V>;
-    using C = TmaCfg<R, T::RY, T::TXT, T::TYT>;
+    using C = TmaCfg<R, T::RY, T::TXT, T::TYT, T::STAGES>;
     TmaVariant L;
     L.tx = C::TX;
     L.ty = C::TY;
@@ -309,6 +323,8 @@ TmaLauncher make_tma_launcher() {
     L.v[0] = make_tma_variant<R, 0, true>();
     L.v[1] = make_tma_variant<R, 1, false>();
     L.v[2] = make_tma_variant<R, 2, false>();
+    L.v[3] = make_tma_variant<R, 3, false>();
+    L.v[4] = make_tma_variant<R, 4, false>();
     return L;
 }
 

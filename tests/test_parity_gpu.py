@@ -21,17 +21,18 @@ import oracle as O
 
 pytestmark = pytest.mark.gpu
 
-ALGOS = ["prefix", "direct", "kahan", "resident", "plain", "tma", "tma1", "tma2"]
+ALGOS = ["prefix", "direct", "kahan", "resident", "plain", "tma", "tma1", "tma2", "tma3", "tma4"]
 
 
 def algo_id(mf, name):
     return {"prefix": mf.ALGO_PREFIX, "direct": mf.ALGO_DIRECT, "kahan": mf.ALGO_PREFIX_KAHAN,
             "resident": mf.ALGO_RESIDENT, "plain": mf.ALGO_PLAIN, "auto": mf.ALGO_AUTO,
-            "tma": mf.ALGO_PREFIX_TMA, "tma1": mf.ALGO_PREFIX_TMA, "tma2": mf.ALGO_PREFIX_TMA}[name]
+            "tma": mf.ALGO_PREFIX_TMA, "tma1": mf.ALGO_PREFIX_TMA, "tma2": mf.ALGO_PREFIX_TMA,
+            "tma3": mf.ALGO_PREFIX_TMA, "tma4": mf.ALGO_PREFIX_TMA}[name]
 
 
 def variant_of(name):
-    return {"tma": 0, "tma1": 1, "tma2": 2}.get(name)
+    return {"tma": 0, "tma1": 1, "tma2": 2, "tma3": 3, "tma4": 4}.get(name)
 
 
 def pair(mf, n, R, steps, ic=0, eps=0.03, eps_lo=0.0, eps_hi=0.0, kernel=0, delta_hf=0.0, tau=1e-3,
@@ -146,7 +147,7 @@ def test_nuclei_obstacle_active_and_bounds_exact(gpu_lib, algo):
 
 def test_ragged_tiles_and_many_tiles(gpu_lib):
     mf = gpu_lib
-    for (n, R), algo in itertools.product(((68, 3), (132, 5), (200, 8)), ("prefix", "tma", "tma1", "tma2")):
+    for (n, R), algo in itertools.product(((68, 3), (132, 5), (200, 8)), ("prefix", "tma", "tma1", "tma2", "tma3", "tma4")):
         g, o = pair(mf, n, R, 20, ic=2, tau=5e-3, algo=algo)
         seeds = seeds_of(2, base=n)
         _, uT, f, _ = gpu_solve(mf, g, seeds)
@@ -171,7 +172,7 @@ def test_gaussian_kernel_generic_path(gpu_lib):
 def test_stationary_states_exact(gpu_lib):
     import torch
     mf = gpu_lib
-    for algo in ("prefix", "resident", "direct", "kahan", "tma", "tma1", "tma2"):
+    for algo in ("prefix", "resident", "direct", "kahan", "tma", "tma1", "tma2", "tma3", "tma4"):
         g = mf.Model(n=64, delta=4 / 64, nsteps=50, algo=algo_id(mf, algo))
         if variant_of(algo) is not None:
             g.set_tile_variant(variant_of(algo))
