@@ -178,6 +178,25 @@ mfmc_status mfmc_solve_fields_algo(const mfmc_model *model, int algo, const doub
                                    const float *u0, size_t ns, float *uT, double *ubar,
                                    double *ooi, void *stream);
 
+/* Allocation-free variant of mfmc_solve_fields, for callers that cannot allocate device
+ * memory while they solve (a framework that reserves all device memory up front through
+ * its own allocator, or a latency-critical loop that must not synchronise on, or risk the
+ * failure of, cudaMalloc).  The paper has no counterpart: this is a property of the
+ * library, not of the method.
+ * Same arguments and results as mfmc_solve_fields, computed with the register-tiled
+ * prefix kernel; the scratch (two field buffers, coefficients, tile partials) is a fixed
+ * 32 MiB device array inside the library that every GPU loading the library holds until
+ * exit.  Limits: ns <= 4096, ns * n * n * 4 <= 16,482,304 bytes (e.g. 62 fields of
+ * 256 x 256, 1006 fields of 64 x 64), ns * tiles <= 65536; larger batches return
+ * MFMC_EINVAL with the limits in the message.  Constant kernel and R in
+ * {1,2,3,4,5,6,8,11,12,16,22,24,32} only.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress), so make it before any stream capture.
+ * All calls share the one array and it keeps the last call's contents; calls whose work
+ * overlaps on the GPU (other streams, other threads) race on it. */
+mfmc_status mfmc_solve_fields_noalloc(const mfmc_model *model, const double *eps, const float *u0,
+                                      size_t ns, float *uT, double *ubar, double *ooi,
+                                      void *stream);
+
 /* The user-level batch call (Section 3 problem statement: OoI of model f_k at
  * parameter samples).  Sample i uses models[i], seeds[i] and params[i] (params may
  * be NULL); samples of different models run in the same call.  Host outputs:
