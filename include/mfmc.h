@@ -102,12 +102,14 @@ typedef struct {
 
 /* Per-sample parameters (all optional).  eps <= 0 means "from the model" (the nominal
  * eps, or the per-sample draw when the model has an eps range).  has_theta = 0 draws
- * theta = (mu_i, eta_i) of Eq. (ic) from the seed. */
+ * theta = (mu_i, eta_i) of Eq. (ic) from the seed.  nsteps <= 0 means the model's
+ * number of steps (mfmc_solve_batch and the server honour a per-sample value). */
 typedef struct {
     double eps;
     int has_theta;
     double mu[4];
     double eta[4][2];
+    int nsteps;
 } mfmc_sample_params;
 
 /* Derived constants of a model (nominal eps). */
@@ -269,6 +271,41 @@ mfmc_status mfmc_estimate_device(const mfmc_plan_t *plan, const double *const *o
 mfmc_status mfmc_run(mfmc_model *const *models, int K, int n_pilot, double budget,
                      int policy, uint64_t seed_base, const double *costs,
                      mfmc_plan_t *plan_out, double *estimate);
+
+/* ---------------------------------------------------------------- serving */
+
+/* Serving statistics.  Latencies are submit-to-completion wall seconds. */
+typedef struct {
+    uint64_t submitted, completed, rejected;
+    double p50_latency_s, p99_latency_s, mean_latency_s;
+    double samples_per_s;          /* completed / (last completion - first submit) */
+    size_t peak_bytes;             /* peak device bytes held by admitted requests  */
+    int peak_inflight;
+} mfmc_server_stats;
+
+/* Continuous-batching request loop on one GPU: a host thread admits submitted solve
+ * requests while their fields fit in hbm_budget_bytes and fewer than max_slots are in
+ * flight, keeps their fields resident on the device, and advances all admitted
+ * requests together between admissions, so requests that arrive while others run join
+ * the work already on the GPU. */
+mfmc_status mfmc_server_create(size_t hbm_budget_bytes, int max_slots, mfmc_server **out);
+
+/* Queue one solve (model, optional params, seed); returns a ticket.  The model must
+ * outlive the request.  Thread-safe. */
+mfmc_status mfmc_submit(mfmc_server *srv, const mfmc_model *model,
+                        const mfmc_sample_params *params, uint64_t seed, uint64_t *ticket);
+
+/* MFMC_OK with the result once done (the ticket is then released), MFMC_EBUSY while
+ * queued or running, MFMC_ENOTFOUND for an unknown ticket. */
+mfmc_status mfmc_poll(mfmc_server *srv, uint64_t ticket, double *ooi, double *latency_s);
+
+/* Block until every submitted request has completed. */
+mfmc_status mfmc_server_drain(mfmc_server *srv);
+
+mfmc_status mfmc_server_get_stats(mfmc_server *srv, mfmc_server_stats *out);
+
+/* Stop the loop thread and release device memory (NULL is ignored). */
+void mfmc_server_destroy(mfmc_server *srv);
 
 #ifdef __cplusplus
 }

@@ -252,7 +252,8 @@ mfmc_status mfmc_init_fields(const mfmc_model *cm, const mfmc_sample_params *par
 }
 
 static mfmc_status solve_impl(mfmc_model *m, int algo, const double *eps, const float *u0, size_t ns, float *uT,
-                              double *ubar, double *ooi, cudaStream_t st) {
+                              double *ubar, double *ooi, cudaStream_t st, int nsteps = -1) {
+    if (nsteps < 0) nsteps = m->d.nsteps;
     if (ns == 0) return MFMC_OK;
     if (!u0) return fail(MFMC_EINVAL, "NULL u0");
     if (uT && uT == u0) return fail(MFMC_EINVAL, "uT must not alias u0");
@@ -274,7 +275,7 @@ static mfmc_status solve_impl(mfmc_model *m, int algo, const double *eps, const 
     }
     s = launch_coefficients(*m, eps, ns, m->coef, st);
     if (s != MFMC_OK) return s;
-    return run_solve(*m, algo, m->coef, u0, ns, m->d.nsteps, uT, ubar, ooi, st);
+    return run_solve(*m, algo, m->coef, u0, ns, nsteps, uT, ubar, ooi, st);
 }
 
 mfmc_status mfmc_solve_fields(const mfmc_model *cm, const double *eps, const float *u0, size_t ns, float *uT,
@@ -299,18 +300,24 @@ mfmc_status mfmc_solve_batch(mfmc_model *const *models, const mfmc_sample_params
     if (ns == 0) return MFMC_OK;
     if (!models || !seeds || !ooi_out) return fail(MFMC_EINVAL, "NULL argument");
     if (ns > (size_t)kMaxNs) return fail(MFMC_EINVAL, "too many samples");
-    std::map<mfmc_model *, std::vector<size_t>> groups;
-    std::vector<mfmc_model *> order;
+    // groups of (model, number of steps), in order of first appearance
+    typedef std::pair<mfmc_model *, int> Key;
+    std::map<Key, std::vector<size_t>> groups;
+    std::vector<Key> order;
     for (size_t i = 0; i < ns; ++i) {
         if (!models[i]) return fail(MFMC_EINVAL, "NULL model at sample %zu", i);
-        auto it = groups.find(models[i]);
-        if (it == groups.end()) order.push_back(models[i]);
-        groups[models[i]].push_back(i);
+        const int k = (params && params[i].nsteps > 0) ? params[i].nsteps : models[i]->d.nsteps;
+        const Key key(models[i], k);
+        auto it = groups.find(key);
+        if (it == groups.end()) order.push_back(key);
+        groups[key].push_back(i);
     }
+    // groups of one model run one after the other on that model's stream and buffers
     std::vector<std::vector<double>> host_res(order.size());
     for (size_t g = 0; g < order.size(); ++g) {
-        mfmc_model *m = order[g];
-        const std::vector<size_t> &idx = groups[m];
+        mfmc_model *m = order[g].first;
+        const int gsteps = order[g].second;
+        const std::vector<size_t> &idx = groups[order[g]];
         const size_t k = idx.size();
         const size_t nn = (size_t)m->d.n * m->d.n;
         {
@@ -334,16 +341,25 @@ mfmc_status mfmc_solve_batch(mfmc_model *const *models, const mfmc_sample_params
         mfmc_status s = mfmc_init_fields(m, params ? pp.data() : nullptr, sd.data(), k, m->u0buf, m->stream);
         if (s != MFMC_OK) return s;
         s = solve_impl(m, m->tuned ? m->algo : (int)m->d.algo, m->eps_tmp, m->u0buf, k, nullptr, m->resbuf + k,
-                       m->resbuf, m->stream);
+                       m->resbuf, m->stream, gsteps);
         if (s != MFMC_OK) return s;
         host_res[g].resize(2 * k);
         MFMC_CUDA(cudaMemcpyAsync(host_res[g].data(), m->resbuf, 2 * k * sizeof(double), cudaMemcpyDeviceToHost,
                                   m->stream));
+        // the next group of the same model reuses its buffers
+        bool again = false;
+        for (size_t h = g + 1; h < order.size(); ++h) again |= order[h].first == m;
+        if (again) MFMC_CUDA(cudaStreamSynchronize(m->stream));
     }
     for (size_t g = 0; g < order.size(); ++g) {
-        mfmc_model *m = order[g];
+        mfmc_model *m = order[g].first;
         MFMC_CUDA(cudaStreamSynchronize(m->stream));
-        const std::vector<size_t> &idx = groups[m];
+        if (m->d_status) {
+            int flag = 0;
+            MFMC_CUDA(cudaMemcpy(&flag, m->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+            if (flag) return fail(MFMC_ETIMEOUT, "a device-side wait gave up");
+        }
+        const std::vector<size_t> &idx = groups[order[g]];
         const size_t k = idx.size();
         for (size_t q = 0; q < k; ++q) {
             ooi_out[idx[q]] = host_res[g][q];

@@ -64,7 +64,7 @@ struct Model {
     CUtensorMap mapA, mapB;
     int maps_valid = 0;
     int map_sw = 0, map_sh = 0;  // box the tensor maps were encoded for
-    int tma_variant = 1;         // tile shape of the TMA kernel (autotuned)
+    int tma_variant = 4;         // tile shape of the TMA kernel (autotuned; 4 is the default)
     int *d_status = nullptr;  // set by a device wait that gave up
     ~Model();
 };
@@ -127,6 +127,25 @@ mfmc_status launch_coefficients(const Model &m, const double *eps_dev, size_t ns
 // Full solve with an explicit algorithm; scratch from the model.
 mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0, size_t ns,
                       int nsteps, float *uT, double *ubar, double *ooi, cudaStream_t st);
+// Buffers of one run of the TMA pipeline (model scratch, or a serving cohort's own).
+struct TmaBuffers {
+    float *padA = nullptr, *padB = nullptr;
+    CUtensorMap mapA, mapB;
+    size_t cap = 0;
+    double *partials = nullptr;
+    int *status = nullptr;
+};
+mfmc_status encode_map(CUtensorMap *map, float *base, int P, size_t cap, int sw, int sh);
+int tma_tiles(const Model &m, int variant, int *tiles_x);
+// stream-ordered allocation on alloc_st (cudaMallocAsync) and release (cudaFreeAsync)
+mfmc_status tma_alloc_buffers(const Model &m, int variant, size_t ns, TmaBuffers *b, cudaStream_t alloc_st);
+void tma_free_buffers(TmaBuffers *b, cudaStream_t st);
+// steps_ps (device, ns ints, or nullptr): per-sample step counts, nsteps = their maximum.
+mfmc_status run_solve_tma_core(const Model &m, int kahan, int variant, const StepCoef *coef, const float *u0,
+                               size_t ns, int nsteps, const int *steps_ps, float *uT, double *ubar, double *ooi,
+                               const TmaBuffers &b, cudaStream_t st);
+mfmc_status run_resident_steps(const Model &m, const StepCoef *coef, const float *u0, size_t ns, int nsteps,
+                               const int *steps_ps, float *uT, double *ubar, double *ooi, cudaStream_t st);
 // The TMA pipeline with an explicit tile-shape variant (autotuner).
 mfmc_status run_solve_tma(Model &m, int kahan, int variant, const StepCoef *coef, const float *u0, size_t ns,
                           int nsteps, float *uT, double *ubar, double *ooi, cudaStream_t st);

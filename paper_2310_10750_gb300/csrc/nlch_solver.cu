@@ -311,7 +311,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-static mfmc_status encode_map(CUtensorMap *map, float *base, int P, size_t cap, int sw, int sh) {
+mfmc_status encode_map(CUtensorMap *map, float *base, int P, size_t cap, int sw, int sh) {
     auto enc = tensor_map_encoder();
     if (!enc) return fail(MFMC_ECUDA, "cuTensorMapEncodeTiled is unavailable");
     const cuuint64_t dims[3] = {(cuuint64_t)P, (cuuint64_t)P, (cuuint64_t)cap};
@@ -353,8 +353,46 @@ static mfmc_status ensure_pad_scratch(Model &m, size_t ns, const TmaVariant &L) 
     return MFMC_OK;
 }
 
-mfmc_status run_solve_tma(Model &m, int kahan, int variant, const StepCoef *coef, const float *u0, size_t ns,
-                          int nsteps, float *uT, double *ubar, double *ooi, cudaStream_t st) {
+int tma_tiles(const Model &m, int variant, int *tiles_x) {
+    const TmaLauncher *TL = tma_launcher(m.R);
+    const TmaVariant &L = TL->v[variant];
+    *tiles_x = (m.d.n + L.tx - 1) / L.tx;
+    return *tiles_x * ((m.d.n + L.ty - 1) / L.ty);
+}
+
+mfmc_status tma_alloc_buffers(const Model &m, int variant, size_t ns, TmaBuffers *b, cudaStream_t alloc_st) {
+    const TmaLauncher *TL = tma_launcher(m.R);
+    if (!TL) return fail(MFMC_EINVAL, "no TMA kernel for R = %d", m.R);
+    const TmaVariant &L = TL->v[variant];
+    const int G = (m.R + 3) & ~3, P = m.d.n + 2 * G;
+    int tiles_x = 0;
+    const int tiles = tma_tiles(m, variant, &tiles_x);
+    const size_t bytes = ns * (size_t)P * P * sizeof(float);
+    // stream-ordered allocations: no device-wide synchronisation
+    MFMC_CUDA(cudaMallocAsync((void **)&b->padA, bytes, alloc_st));
+    MFMC_CUDA(cudaMallocAsync((void **)&b->padB, bytes, alloc_st));
+    MFMC_CUDA(cudaMallocAsync((void **)&b->partials, ns * (size_t)tiles * sizeof(double), alloc_st));
+    MFMC_CUDA(cudaMallocAsync((void **)&b->status, sizeof(int), alloc_st));
+    MFMC_CUDA(cudaMemsetAsync(b->status, 0, sizeof(int), alloc_st));
+    b->cap = ns;
+    mfmc_status s = encode_map(&b->mapA, b->padA, P, ns, L.sw, L.sh);
+    if (s == MFMC_OK) s = encode_map(&b->mapB, b->padB, P, ns, L.sw, L.sh);
+    return s;
+}
+
+void tma_free_buffers(TmaBuffers *b, cudaStream_t st) {
+    if (b->padA) cudaFreeAsync(b->padA, st);
+    if (b->padB) cudaFreeAsync(b->padB, st);
+    if (b->partials) cudaFreeAsync(b->partials, st);
+    if (b->status) cudaFreeAsync(b->status, st);
+    b->padA = b->padB = nullptr;
+    b->partials = nullptr;
+    b->status = nullptr;
+}
+
+mfmc_status run_solve_tma_core(const Model &m, int kahan, int variant, const StepCoef *coef, const float *u0,
+                               size_t ns, int nsteps, const int *steps_ps, float *uT, double *ubar, double *ooi,
+                               const TmaBuffers &b, cudaStream_t st) {
     const TmaLauncher *TL = tma_launcher(m.R);
     if (!TL) return fail(MFMC_EINVAL, "no TMA kernel for R = %d", m.R);
     if (kahan) variant = 0;
@@ -362,15 +400,12 @@ mfmc_status run_solve_tma(Model &m, int kahan, int variant, const StepCoef *coef
         return fail(MFMC_EINVAL, "TMA variant %d unavailable", variant);
     const TmaVariant *L = &TL->v[variant];
     const int n = m.d.n, G = (m.R + 3) & ~3, P = n + 2 * G;
-    const int tiles_x = (n + L->tx - 1) / L->tx;
-    const int tiles = tiles_x * ((n + L->ty - 1) / L->ty);
-    mfmc_status s = ensure_pad_scratch(m, ns, *L);
-    if (s == MFMC_OK) s = grow_buffer(&m.partials, &m.partials_cap, ns * (size_t)tiles);
-    if (s != MFMC_OK) return s;
+    int tiles_x = 0;
+    const int tiles = tma_tiles(m, variant, &tiles_x);
     {
         const size_t total = ns * (size_t)P * (P / 4);
         const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 32);
-        pad_fields_kernel<<<blocks, 256, 0, st>>>(u0, m.padB, n, G, ns);
+        pad_fields_kernel<<<blocks, 256, 0, st>>>(u0, b.padB, n, G, ns);
         MFMC_CUDA(cudaGetLastError());
     }
     int dev = 0, sms = 0;
@@ -379,31 +414,72 @@ mfmc_status run_solve_tma(Model &m, int kahan, int variant, const StepCoef *coef
     const long long total = (long long)ns * tiles;
     if (total > (1ll << 30)) return fail(MFMC_EINVAL, "too many tiles in one solve");
     const int grid = (int)std::min<long long>(total, (long long)sms * L->blocks_per_sm());
-    const CUtensorMap *src = &m.mapB;
-    float *dstbuf = m.padA;
+    const CUtensorMap *src = &b.mapB;
+    float *dstbuf = b.padA;
     for (int k = 1; k <= nsteps; ++k) {
         const bool last = k == nsteps;
         TmaArgs a;
-        a.dst = last ? nullptr : dstbuf;
-        a.dst_plain = last ? uT : nullptr;
+        a.dst = (last && !steps_ps) ? nullptr : dstbuf;
+        a.dst_plain = (last && !steps_ps) ? uT : nullptr;
         a.coef = coef;
-        a.partials = m.partials;
-        a.status = m.d_status;
+        a.partials = b.partials;
+        a.status = b.status;
+        a.steps_ps = steps_ps;
+        a.step = k;
         a.n = n;
         a.P = P;
         a.tiles_x = tiles_x;
         a.tiles = tiles;
         a.total = (int)total;
-        a.last = last ? 1 : 0;
-        s = L->fn[kahan ? 2 : 1](*src, a, grid, st);
+        a.last = (last && !steps_ps) ? 1 : 0;
+        mfmc_status s = L->fn[kahan ? 2 : 1](*src, a, grid, st);
         if (s != MFMC_OK) return s;
-        src = (dstbuf == m.padA) ? &m.mapA : &m.mapB;
-        dstbuf = (dstbuf == m.padA) ? m.padB : m.padA;
+        src = (dstbuf == b.padA) ? &b.mapA : &b.mapB;
+        dstbuf = (dstbuf == b.padA) ? b.padB : b.padA;
     }
-    finalize_ooi_kernel<<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(m.partials, tiles, ns,
+    finalize_ooi_kernel<<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(b.partials, tiles, ns,
                                                                        1.0 / ((double)n * n), ubar, ooi);
     MFMC_CUDA(cudaGetLastError());
     return MFMC_OK;
+}
+
+mfmc_status run_solve_tma(Model &m, int kahan, int variant, const StepCoef *coef, const float *u0, size_t ns,
+                          int nsteps, float *uT, double *ubar, double *ooi, cudaStream_t st) {
+    const TmaLauncher *TL = tma_launcher(m.R);
+    if (!TL) return fail(MFMC_EINVAL, "no TMA kernel for R = %d", m.R);
+    if (kahan) variant = 0;
+    if (variant < 0 || variant >= kTmaVariants) return fail(MFMC_EINVAL, "TMA variant %d unavailable", variant);
+    int tiles_x = 0;
+    const int tiles = tma_tiles(m, variant, &tiles_x);
+    mfmc_status s = ensure_pad_scratch(m, ns, TL->v[variant]);
+    if (s == MFMC_OK) s = grow_buffer(&m.partials, &m.partials_cap, ns * (size_t)tiles);
+    if (s != MFMC_OK) return s;
+    TmaBuffers b;
+    b.padA = m.padA;
+    b.padB = m.padB;
+    b.mapA = m.mapA;
+    b.mapB = m.mapB;
+    b.cap = m.pad_cap;
+    b.partials = m.partials;
+    b.status = m.d_status;
+    return run_solve_tma_core(m, kahan, variant, coef, u0, ns, nsteps, nullptr, uT, ubar, ooi, b, st);
+}
+
+mfmc_status run_resident_steps(const Model &m, const StepCoef *coef, const float *u0, size_t ns, int nsteps,
+                               const int *steps_ps, float *uT, double *ubar, double *ooi, cudaStream_t st) {
+    ResidentArgs a;
+    a.u0 = u0;
+    a.uT = uT;
+    a.coef = coef;
+    a.ubar = ubar;
+    a.ooi = ooi;
+    a.steps_ps = steps_ps;
+    a.n = m.d.n;
+    a.ns = (int)ns;
+    a.nsteps = nsteps;
+    ResidentFn f = resident_launcher(m.R);
+    if (!f) return fail(MFMC_EINVAL, "no resident kernel for R = %d", m.R);
+    return f(a, st);
 }
 
 mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0, size_t ns, int nsteps,
@@ -425,18 +501,7 @@ mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0,
     if (algo == MFMC_ALGO_PREFIX_TMA)
         return run_solve_tma(m, 0, m.tma_variant, coef, u0, ns, nsteps, uT, ubar, ooi, st);
     if (algo == MFMC_ALGO_PREFIX_KAHAN) return run_solve_tma(m, 1, 0, coef, u0, ns, nsteps, uT, ubar, ooi, st);
-    if (algo == MFMC_ALGO_RESIDENT) {
-        ResidentArgs a;
-        a.u0 = u0;
-        a.uT = uT;
-        a.coef = coef;
-        a.ubar = ubar;
-        a.ooi = ooi;
-        a.n = n;
-        a.ns = (int)ns;
-        a.nsteps = nsteps;
-        return resident_launcher(m.R)(a, st);
-    }
+    if (algo == MFMC_ALGO_RESIDENT) return run_resident_steps(m, coef, u0, ns, nsteps, nullptr, uT, ubar, ooi, st);
     int tiles_x = 0;
     const int tiles = tiles_for(m, algo, &tiles_x);
     mfmc_status s = ensure_scratch(m, ns, (size_t)tiles);

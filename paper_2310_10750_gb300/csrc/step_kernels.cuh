@@ -213,6 +213,7 @@ struct ResidentArgs {
     const StepCoef *coef;
     double *ubar;
     double *ooi;
+    const int *steps_ps;  // per-sample step counts (serving), or nullptr: nsteps for all
     int n;
     int ns;
     int nsteps;
@@ -253,7 +254,8 @@ __global__ void __launch_bounds__(256) resident_kernel(ResidentArgs a) {
         __syncthreads();
 
         float o[RY][RX];
-        for (int step = 0; step < a.nsteps; ++step) {
+        const int nsteps = a.steps_ps ? a.steps_ps[sample] : a.nsteps;
+        for (int step = 0; step < nsteps; ++step) {
             float acc[RY][RX];
 #pragma unroll
             for (int j = 0; j < RY; ++j)

@@ -24,8 +24,20 @@ struct TmaArgs {
     const StepCoef *coef;
     double *partials;      // [ns][tiles], written at the last step
     int *status;           // set to 1 when a bounded wait gives up
+    const int *steps_ps;   // per-sample step counts (serving), or nullptr: every sample runs `step`
+    int step;              // 1-based index of this step
     int n, P, tiles_x, tiles, total, last;
 };
+
+// A sample takes part in step `a.step` while a.step <= its own step count.
+__device__ __forceinline__ bool item_active(const TmaArgs &a, int item) {
+    return a.steps_ps == nullptr || a.step <= a.steps_ps[item / a.tiles];
+}
+
+__device__ __forceinline__ int next_active(const TmaArgs &a, int item, int stride) {
+    while (item < a.total && !item_active(a, item)) item += stride;
+    return item;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -108,11 +120,14 @@ __global__ void __launch_bounds__(TXT *TYT) step_tma_kernel(const __grid_constan
 
     const int tx = tid % TXT, ty = tid / TXT, ox = tx * RX, oy = ty * RY;
     int k = 0;
-    if (tid == 0 && (int)blockIdx.x < a.total) issue(blockIdx.x, 0);
-    for (int item = blockIdx.x; item < a.total; item += gridDim.x, ++k) {
+    const int stride = gridDim.x;
+    const int first = next_active(a, blockIdx.x, stride);
+    if (tid == 0 && first < a.total) issue(first, 0);
+    for (int item = first, nxt; item < a.total; item = nxt, ++k) {
+        nxt = next_active(a, item + stride, stride);
         const int stage = STAGES == 2 ? (k & 1) : 0;
         const uint32_t parity = STAGES == 2 ? (uint32_t)((k >> 1) & 1) : (uint32_t)(k & 1);
-        if (STAGES == 2 && tid == 0 && item + (int)gridDim.x < a.total) issue(item + gridDim.x, stage ^ 1);
+        if (STAGES == 2 && tid == 0 && nxt < a.total) issue(nxt, stage ^ 1);
         // bounded wait for this stage's copy
         long long spins = 0;
         while (!mbar_try_wait(&bars[stage], parity)) {
@@ -129,6 +144,7 @@ __global__ void __launch_bounds__(TXT *TYT) step_tma_kernel(const __grid_constan
         const float *s = base + stage * C::STAGE_FLOATS;
         const int sample = item / a.tiles, tile = item - sample * a.tiles;
         const int x0 = (tile % a.tiles_x) * C::TX, y0 = (tile / a.tiles_x) * C::TY;
+        const bool last = a.last || (a.steps_ps != nullptr && a.step == a.steps_ps[sample]);
 
         float acc[RY][RX];
         float cmp[ALGO == 2 ? RY : 1][RX];
@@ -209,15 +225,15 @@ __global__ void __launch_bounds__(TXT *TYT) step_tma_kernel(const __grid_constan
                         }
                     }
                 }
-                if (a.last) part += ((double)o[0] + (double)o[1]) + ((double)o[2] + (double)o[3]);
+                if (last) part += ((double)o[0] + (double)o[1]) + ((double)o[2] + (double)o[3]);
             }
         }
-        if (a.last) {
+        if (last) {
             const double t = block_sum_fixed<NT>(part, red);
             if (tid == 0) a.partials[(size_t)sample * a.tiles + tile] = t;
         }
         __syncthreads();  // every thread is done with this stage before it is refilled
-        if (STAGES == 1 && tid == 0 && item + (int)gridDim.x < a.total) issue(item + gridDim.x, 0);
+        if (STAGES == 1 && tid == 0 && nxt < a.total) issue(nxt, 0);
     }
 }
 

@@ -46,7 +46,7 @@ class mfmc_model_desc(ctypes.Structure):
 
 class mfmc_sample_params(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("has_theta", ctypes.c_int), ("mu", ctypes.c_double * 4),
-                ("eta", (ctypes.c_double * 2) * 4)]
+                ("eta", (ctypes.c_double * 2) * 4), ("nsteps", ctypes.c_int)]
 
 
 class mfmc_model_info(ctypes.Structure):
@@ -105,6 +105,22 @@ _sig("mfmc_estimate", _st, [ctypes.POINTER(mfmc_plan_t), _vp, _vp])
 _sig("mfmc_estimate_device", _st, [ctypes.POINTER(mfmc_plan_t), _vp, _vp, _vp])
 _sig("mfmc_run", _st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_uint64, _vp,
                        ctypes.POINTER(mfmc_plan_t), _vp])
+
+
+class mfmc_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("p50_latency_s", ctypes.c_double), ("p99_latency_s", ctypes.c_double),
+                ("mean_latency_s", ctypes.c_double), ("samples_per_s", ctypes.c_double),
+                ("peak_bytes", ctypes.c_size_t), ("peak_inflight", ctypes.c_int)]
+
+
+_sig("mfmc_server_create", _st, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_vp)])
+_sig("mfmc_submit", _st, [_vp, _vp, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)])
+_sig("mfmc_poll", _st, [_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)])
+_sig("mfmc_server_drain", _st, [_vp])
+_sig("mfmc_server_get_stats", _st, [_vp, ctypes.POINTER(mfmc_server_stats)])
+_sig("mfmc_server_destroy", None, [_vp])
+_sig("mfmc_solve_fields_noalloc", _st, [_vp, _vp, _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp])
 
 
 def _check(status):
@@ -178,12 +194,15 @@ def mfmc_model_set_tile_variant(model: Model, variant: int):
     model.set_tile_variant(variant)
 
 
-def make_params(ns, eps=None, theta=None):
-    """Array of mfmc_sample_params (eps per sample, optional nuclei theta = (mu[4], eta[4,2]))."""
+def make_params(ns, eps=None, theta=None, nsteps=None):
+    """Array of mfmc_sample_params (eps per sample, optional nuclei theta = (mu[4], eta[4,2]),
+    optional per-sample step counts)."""
     arr = (mfmc_sample_params * ns)()
     for i in range(ns):
         if eps is not None:
             arr[i].eps = float(eps[i])
+        if nsteps is not None:
+            arr[i].nsteps = int(nsteps[i])
         if theta is not None and theta[i] is not None:
             mu, eta = theta[i]
             arr[i].has_theta = 1
@@ -275,3 +294,47 @@ def mfmc_run(models: Sequence[Model], n_pilot, budget, policy=0, seed_base=0, co
     _check(_L.mfmc_run(ctypes.addressof(handles), K, n_pilot, float(budget), policy, seed_base,
                        None if C is None else C.ctypes.data, ctypes.byref(plan), ctypes.addressof(est)))
     return plan, est.value
+
+
+class Server:
+    """Owning wrapper of an mfmc_server (continuous-batching request loop)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int):
+        h = _vp()
+        _check(_L.mfmc_server_create(hbm_budget_bytes, max_slots, ctypes.byref(h)))
+        self.handle = h.value
+
+    def submit(self, model: Model, seed: int, params=None) -> int:
+        t = ctypes.c_uint64()
+        p = None if params is None else ctypes.addressof(params)
+        _check(_L.mfmc_submit(self.handle, model.handle, p, seed, ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int):
+        """(ooi, latency_s) when done, None while busy; raises for unknown tickets."""
+        f, lat = ctypes.c_double(), ctypes.c_double()
+        st = _L.mfmc_poll(self.handle, ticket, ctypes.byref(f), ctypes.byref(lat))
+        if st == MFMC_EBUSY:
+            return None
+        _check(st)
+        return f.value, lat.value
+
+    def drain(self):
+        _check(_L.mfmc_server_drain(self.handle))
+
+    def stats(self) -> dict:
+        s = mfmc_server_stats()
+        _check(_L.mfmc_server_get_stats(self.handle, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _L.mfmc_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def mfmc_server_create(hbm_budget_bytes: int, max_slots: int) -> Server:
+    return Server(hbm_budget_bytes, max_slots)
