@@ -194,11 +194,13 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     algo_req = {"auto": mfmc.ALGO_AUTO, "prefix": mfmc.ALGO_PREFIX, "direct": mfmc.ALGO_DIRECT,
-                "kahan": mfmc.ALGO_PREFIX_KAHAN, "tma": mfmc.ALGO_PREFIX_TMA}[args.algo]
+                "kahan": mfmc.ALGO_PREFIX_KAHAN, "tma": mfmc.ALGO_PREFIX_TMA, "rows": mfmc.ALGO_ROWS}[args.algo]
     model = mfmc.Model(n=N_LATTICE, delta=R_CELLS / N_LATTICE, eps=EPS, eps_lo=EPS_LO, eps_hi=EPS_HI, tau=TAU,
                        nsteps=NSTEPS, ic=mfmc.IC_SMOOTHED_GAUSS, ic_amp=SIGMA, algo=algo_req)
     if args.tile_variant >= 0:
         model.set_tile_variant(args.tile_variant)
+    if args.band_height > 0:
+        model.set_band_height(args.band_height, args.columns)
     ns = NSAMPLES
     seeds = np.arange(ns, dtype=np.uint64) + SEED_BASE + rank * ns
     u0 = torch.empty((ns, N_LATTICE, N_LATTICE), dtype=torch.float32, device="cuda")
@@ -208,10 +210,13 @@ def run_ours(args):
     for _ in range(args.warmup):
         mfmc.mfmc_solve_fields(model, u0, ns, eps=eps, ooi=ooi, stream=stream)
     torch.cuda.synchronize()
-    algo_names = {1: "direct", 2: "prefix", 3: "prefix-kahan", 4: "resident", 5: "plain", 6: "prefix-tma"}
+    algo_names = {1: "direct", 2: "prefix", 3: "prefix-kahan", 4: "resident", 5: "plain", 6: "prefix-tma",
+                  7: "row-stream"}
     algo = algo_names.get(model.info().algo, str(model.info().algo))
     if algo == "prefix-tma":
         algo += f" (tile variant {model.info().tile_variant})"
+    if algo == "row-stream":
+        algo += f" (band height {model.info().band_height}, {model.info().columns_per_thread} columns/thread)"
 
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -298,7 +303,9 @@ def run_ours(args):
                     "what": "one sample per launch, one launch per step, direct disc sum"},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
                              "frac": achieved / peak_gbs, "traffic": traffic, "peak_kind": peak_kind,
-                             "kernel": ("step_tma_kernel" if algo.startswith("prefix-tma") else "step_tile_kernel") + f" ({algo})", "algorithmic_bytes_per_launch": bytes_launch,
+                             "kernel": ("step_rows_kernel" if algo.startswith("row-stream") else
+                                        "step_tma_kernel" if algo.startswith("prefix-tma") else "step_tile_kernel")
+                                       + f" ({algo})", "algorithmic_bytes_per_launch": bytes_launch,
                              "avg_launch_ms": kernel_ms},
                 "roofline_alu": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "T instr/s",
                                  "frac": alu_achieved / alu_peak, "instr_per_point": instr_per_pt},
@@ -327,7 +334,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--nsteps", type=int, default=0, help="profiling: time steps per solve")
     ap.add_argument("--samples", type=int, default=0, help="profiling: samples per GPU")
-    ap.add_argument("--algo", default="auto", choices=["auto", "prefix", "direct", "kahan", "tma"])
+    ap.add_argument("--algo", default="auto", choices=["auto", "prefix", "direct", "kahan", "tma", "rows"])
+    ap.add_argument("--band-height", type=int, default=0, help="profiling: pin the row-streaming band height")
+    ap.add_argument("--columns", type=int, default=2, help="profiling: row-streaming columns per thread")
     ap.add_argument("--tile-variant", type=int, default=-1, help="profiling: pin the TMA tile shape")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -70,8 +70,11 @@ typedef enum {
     MFMC_ALGO_PREFIX_KAHAN = 3,/* prefix form with compensated accumulation       */
     MFMC_ALGO_RESIDENT = 4,    /* whole field held in shared memory for all steps */
     MFMC_ALGO_PLAIN = 5,       /* reference form: one sample per launch, direct   */
-    MFMC_ALGO_PREFIX_TMA = 6   /* prefix form, persistent CTAs, TMA double-buffered
+    MFMC_ALGO_PREFIX_TMA = 6,  /* prefix form, persistent CTAs, TMA double-buffered
                                   tiles of a ghost-framed field                   */
+    MFMC_ALGO_ROWS = 7         /* prefix form, each thread streams 2 or 4 columns down
+                                  a band of rows with a ring of 2R+1 accumulators
+                                  (R in {2,4,6,8}, n % 64 == 0, n <= 1024)         */
 } mfmc_algo;
 
 /* One fidelity of the model (Section 2, Section 4).  The lattice is n x n on the unit
@@ -121,6 +124,8 @@ typedef struct {
     int algo;              /* mfmc_algo the solver uses for this model             */
     size_t field_bytes;    /* n * n * 4                                             */
     int tile_variant;      /* tile shape of the TMA kernel (0..4) the solver uses  */
+    int band_height;       /* band height of the row-streaming kernel              */
+    int columns_per_thread;/* columns per thread of the row-streaming kernel       */
 } mfmc_model_info;
 
 typedef struct mfmc_model mfmc_model;
@@ -147,6 +152,10 @@ mfmc_status mfmc_model_query(const mfmc_model *model, mfmc_model_info *out);
 /* Pin the tile shape (0..4) of the TMA kernel instead of letting the autotuner choose
  * (for measurements and tests).  MFMC_EINVAL for an unknown variant. */
 mfmc_status mfmc_model_set_tile_variant(mfmc_model *model, int variant);
+
+/* Pin the band height (rows per work item, >= 8) and the columns per thread (2 or 4) of
+ * the row-streaming kernel. */
+mfmc_status mfmc_model_set_band_height(mfmc_model *model, int rows, int columns_per_thread);
 
 /* Host-side resolution of each sample's eps (model eps, eps range draw, or
  * params[i].eps), ns values into eps_out (host). params may be NULL. */

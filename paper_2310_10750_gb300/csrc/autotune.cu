@@ -24,18 +24,28 @@ mfmc_status autotune(Model &m, cudaStream_t st) {
         if (it != g_tune_cache.end()) {
             m.algo = it->second.first;
             if (m.algo == MFMC_ALGO_PREFIX_TMA) m.tma_variant = it->second.second;
+            if (m.algo == MFMC_ALGO_ROWS) {
+                m.rows_bh = it->second.second / 8;
+                m.rows_rx = it->second.second % 8;
+            }
             m.tuned = 1;
             return MFMC_OK;
         }
     }
     // candidates: (algorithm, TMA tile variant)
     std::vector<std::pair<int, int>> cands;
-    for (int a : {MFMC_ALGO_RESIDENT, MFMC_ALGO_PREFIX_TMA, MFMC_ALGO_PREFIX, MFMC_ALGO_DIRECT}) {
+    for (int a : {MFMC_ALGO_RESIDENT, MFMC_ALGO_ROWS, MFMC_ALGO_PREFIX_TMA, MFMC_ALGO_PREFIX, MFMC_ALGO_DIRECT}) {
         if (!algo_supported(m, a)) continue;
-        if (a == MFMC_ALGO_PREFIX_TMA)
+        if (a == MFMC_ALGO_PREFIX_TMA) {
             for (int v = 0; v < 5; ++v) cands.push_back({a, v});
-        else
+        } else if (a == MFMC_ALGO_ROWS) {
+            // second: band height * 8 + columns per thread
+            for (int rx : {2, 4})
+                for (int bh : {64, 128, 256, 512})
+                    if (bh <= m.d.n && rows_supported(m, rx)) cands.push_back({a, bh * 8 + rx});
+        } else {
             cands.push_back({a, 0});
+        }
     }
     std::pair<int, int> best = cands.empty() ? std::make_pair((int)MFMC_ALGO_DIRECT, 0) : cands[0];
     if (cands.size() > 1) {
@@ -59,6 +69,8 @@ mfmc_status autotune(Model &m, cudaStream_t st) {
         auto run = [&](std::pair<int, int> c) {
             if (c.first == MFMC_ALGO_PREFIX_TMA)
                 return run_solve_tma(m, 0, c.second, coef, u0, ns, steps, nullptr, nullptr, ooi, st);
+            if (c.first == MFMC_ALGO_ROWS)
+                return run_solve_rows(m, c.second / 8, c.second % 8, coef, u0, ns, steps, nullptr, nullptr, ooi, st);
             return run_solve(m, c.first, coef, u0, ns, steps, nullptr, nullptr, ooi, st);
         };
         for (auto a : cands) {
@@ -90,6 +102,10 @@ mfmc_status autotune(Model &m, cudaStream_t st) {
     }
     m.algo = best.first;
     if (best.first == MFMC_ALGO_PREFIX_TMA) m.tma_variant = best.second;
+    if (best.first == MFMC_ALGO_ROWS) {
+        m.rows_bh = best.second / 8;
+        m.rows_rx = best.second % 8;
+    }
     m.tuned = 1;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = best;

@@ -50,6 +50,7 @@ Model::~Model() {
     cudaFree(padA);
     cudaFree(padB);
     cudaFree(d_status);
+    if (gexec) cudaGraphExecDestroy(gexec);
     if (stream) cudaStreamDestroy(stream);
 }
 
@@ -123,7 +124,7 @@ static mfmc_status validate_desc(const mfmc_model_desc &d, int *R_out) {
     if (!(d.ic_amp >= 0)) return fail(MFMC_EINVAL, "ic_amp must be >= 0");
     if (d.ic_base_n < 0 || (d.ic_base_n > 0 && (d.ic_base_n % d.n != 0 || d.ic_base_n > 16384)))
         return fail(MFMC_EINVAL, "ic_base_n must be 0 or a multiple of n up to 16384");
-    if ((int)d.algo < MFMC_ALGO_AUTO || (int)d.algo > MFMC_ALGO_PREFIX_TMA) return fail(MFMC_EINVAL, "unknown algo");
+    if ((int)d.algo < MFMC_ALGO_AUTO || (int)d.algo > MFMC_ALGO_ROWS) return fail(MFMC_EINVAL, "unknown algo");
     *R_out = R;
     return MFMC_OK;
 }
@@ -201,6 +202,8 @@ mfmc_status mfmc_model_query(const mfmc_model *m, mfmc_model_info *out) {
     out->algo = m->algo;
     out->field_bytes = (size_t)m->d.n * m->d.n * sizeof(float);
     out->tile_variant = m->tma_variant;
+    out->band_height = m->rows_bh;
+    out->columns_per_thread = m->rows_rx;
     return MFMC_OK;
 }
 
@@ -208,6 +211,15 @@ mfmc_status mfmc_model_set_tile_variant(mfmc_model *m, int variant) {
     if (!m || variant < 0 || variant > 4) return fail(MFMC_EINVAL, "invalid tile variant");
     std::lock_guard<std::mutex> lk(m->mu);
     m->tma_variant = variant;
+    return MFMC_OK;
+}
+
+mfmc_status mfmc_model_set_band_height(mfmc_model *m, int rows, int columns_per_thread) {
+    if (!m || rows < 8 || rows > 16384 || (columns_per_thread != 2 && columns_per_thread != 4))
+        return fail(MFMC_EINVAL, "invalid band height or columns per thread");
+    std::lock_guard<std::mutex> lk(m->mu);
+    m->rows_bh = rows;
+    m->rows_rx = columns_per_thread;
     return MFMC_OK;
 }
 
@@ -273,9 +285,50 @@ static mfmc_status solve_impl(mfmc_model *m, int algo, const double *eps, const 
         MFMC_CUDA(cudaMalloc((void **)&m->d_wtab, m->wtab.size() * sizeof(float)));
         MFMC_CUDA(cudaMemcpy(m->d_wtab, m->wtab.data(), m->wtab.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
+    // The launch sequence of a solve (coefficients, ~nsteps step kernels, OoI) is replayed as a
+    // CUDA graph while the call's key (algorithm, shape, every pointer it touches, stream) is
+    // unchanged: the first call with a key runs directly (sizing scratch), then is captured.
+    const bool graphable = !m->graphs_off && algo != MFMC_ALGO_RESIDENT && algo != MFMC_ALGO_PLAIN && nsteps > 0;
+    auto key = [&]() {
+        return std::vector<uintptr_t>{(uintptr_t)algo, (uintptr_t)m->tma_variant, (uintptr_t)m->rows_bh,
+                                      (uintptr_t)m->rows_rx, (uintptr_t)ns, (uintptr_t)nsteps, (uintptr_t)eps,
+                                      (uintptr_t)u0, (uintptr_t)uT, (uintptr_t)ubar, (uintptr_t)ooi,
+                                      (uintptr_t)st, (uintptr_t)m->coef, (uintptr_t)m->bufA, (uintptr_t)m->bufB,
+                                      (uintptr_t)m->padA, (uintptr_t)m->padB, (uintptr_t)m->partials,
+                                      (uintptr_t)m->map_sw, (uintptr_t)m->map_sh, (uintptr_t)m->d_wtab};
+    };
+    if (graphable && m->gexec && m->gkey == key()) {
+        MFMC_CUDA(cudaGraphLaunch(m->gexec, st));
+        return MFMC_OK;
+    }
     s = launch_coefficients(*m, eps, ns, m->coef, st);
     if (s != MFMC_OK) return s;
-    return run_solve(*m, algo, m->coef, u0, ns, nsteps, uT, ubar, ooi, st);
+    s = run_solve(*m, algo, m->coef, u0, ns, nsteps, uT, ubar, ooi, st);
+    if (s != MFMC_OK || !graphable) return s;
+    if (m->gexec) {
+        cudaGraphExecDestroy(m->gexec);
+        m->gexec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        (void)cudaGetLastError();
+        m->graphs_off = 1;
+        return MFMC_OK;
+    }
+    mfmc_status cs = launch_coefficients(*m, eps, ns, m->coef, st);
+    if (cs == MFMC_OK) cs = run_solve(*m, algo, m->coef, u0, ns, nsteps, uT, ubar, ooi, st);
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (cs == MFMC_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&m->gexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (cs != MFMC_OK || e != cudaSuccess) {
+        (void)cudaGetLastError();
+        m->gexec = nullptr;
+        m->graphs_off = 1;  // keep launching directly
+        set_error("");
+        return MFMC_OK;
+    }
+    m->gkey = key();
+    return MFMC_OK;
 }
 
 mfmc_status mfmc_solve_fields(const mfmc_model *cm, const double *eps, const float *u0, size_t ns, float *uT,
@@ -288,7 +341,7 @@ mfmc_status mfmc_solve_fields(const mfmc_model *cm, const double *eps, const flo
 mfmc_status mfmc_solve_fields_algo(const mfmc_model *cm, int algo, const double *eps, const float *u0, size_t ns,
                                    float *uT, double *ubar, double *ooi, void *stream) {
     if (!cm) return fail(MFMC_EINVAL, "NULL model");
-    if (algo < MFMC_ALGO_AUTO || algo > MFMC_ALGO_PREFIX_TMA) return fail(MFMC_EINVAL, "unknown algo");
+    if (algo < MFMC_ALGO_AUTO || algo > MFMC_ALGO_ROWS) return fail(MFMC_EINVAL, "unknown algo");
     return solve_impl(const_cast<mfmc_model *>(cm), algo, eps, u0, ns, uT, ubar, ooi, (cudaStream_t)stream);
 }
 

@@ -65,7 +65,13 @@ struct Model {
     int maps_valid = 0;
     int map_sw = 0, map_sh = 0;  // box the tensor maps were encoded for
     int tma_variant = 4;         // tile shape of the TMA kernel (autotuned; 4 is the default)
+    int rows_bh = 128;           // band height of the row-streaming kernel (autotuned)
+    int rows_rx = 2;             // columns per thread of the row-streaming kernel (2 or 4)
     int *d_status = nullptr;  // set by a device wait that gave up
+    // CUDA graph of the last solve's launch sequence (replayed while its key matches)
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<uintptr_t> gkey;
+    int graphs_off = 0;
     ~Model();
 };
 
@@ -73,6 +79,12 @@ struct Model {
 void set_error(const char *fmt, ...);
 mfmc_status fail(mfmc_status s, const char *fmt, ...);
 mfmc_status cuda_fail(cudaError_t e, const char *what);
+
+#define MFMC_LAUNCHED(what)                                               \
+    do {                                                                  \
+        cudaError_t e_ = cudaGetLastError();                              \
+        if (e_ != cudaSuccess) return ::mfmc::cuda_fail(e_, what);        \
+    } while (0)
 
 #define MFMC_CUDA(call)                                                   \
     do {                                                                  \
@@ -146,6 +158,15 @@ mfmc_status run_solve_tma_core(const Model &m, int kahan, int variant, const Ste
                                const TmaBuffers &b, cudaStream_t st);
 mfmc_status run_resident_steps(const Model &m, const StepCoef *coef, const float *u0, size_t ns, int nsteps,
                                const int *steps_ps, float *uT, double *ubar, double *ooi, cudaStream_t st);
+// Row-streaming kernel: geometry, buffers and solve with band height bh.
+void rows_geometry(const Model &m, int *nbox, int *bw);
+mfmc_status rows_alloc_buffers(const Model &m, int bh, size_t ns, TmaBuffers *b, cudaStream_t alloc_st);
+mfmc_status run_solve_rows_core(const Model &m, int bh, int rx, const StepCoef *coef, const float *u0, size_t ns,
+                                int nsteps, const int *steps_ps, float *uT, double *ubar, double *ooi,
+                                const TmaBuffers &b, cudaStream_t st);
+mfmc_status run_solve_rows(Model &m, int bh, int rx, const StepCoef *coef, const float *u0, size_t ns, int nsteps,
+                           float *uT, double *ubar, double *ooi, cudaStream_t st);
+bool rows_supported(const Model &m, int rx);
 // The TMA pipeline with an explicit tile-shape variant (autotuner).
 mfmc_status run_solve_tma(Model &m, int kahan, int variant, const StepCoef *coef, const float *u0, size_t ns,
                           int nsteps, float *uT, double *ubar, double *ooi, cudaStream_t st);

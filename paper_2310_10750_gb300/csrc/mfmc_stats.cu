@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(ST_NT) pilot_stats_kernel(int n, const double 
 
 mfmc_status launch_pilot_stats(int K, int n, const double *ooi, double *out_dev, cudaStream_t st) {
     pilot_stats_kernel<<<K, ST_NT, 0, st>>>(n, ooi, out_dev);
-    MFMC_CUDA(cudaGetLastError());
+    MFMC_LAUNCHED("mfmc_stats launch 1");
     return MFMC_OK;
 }
 
@@ -94,7 +94,7 @@ mfmc_status launch_estimate(int K, const double *const *lists_dev, const int64_t
     // work_dev: 2K means followed by the estimate
     prefix_means_kernel<<<K, ST_NT, 0, st>>>(lists_dev, m_dev, work_dev);
     combine_kernel<<<1, 32, 0, st>>>(K, work_dev, alpha_dev, work_dev + 2 * K);
-    MFMC_CUDA(cudaGetLastError());
+    MFMC_LAUNCHED("mfmc_stats launch 2");
     return MFMC_OK;
 }
 

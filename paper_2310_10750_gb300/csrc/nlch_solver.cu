@@ -10,7 +10,7 @@
 
 #include <mutex>
 
-#include "tma_step.cuh"
+#include "rows_step.cuh"
 
 namespace mfmc {
 
@@ -94,7 +94,7 @@ mfmc_status launch_init_fields(const Model &m, const uint64_t *seeds_dev, const 
     const int base_n = m.d.ic_base_n > 0 ? m.d.ic_base_n : m.d.n;
     init_fields_kernel<<<(unsigned)blocks, block, 0, st>>>(m.d.n, (int)m.d.ic, m.d.ic_amp, base_n, seeds_dev,
                                                            theta_dev, ns, u0);
-    MFMC_CUDA(cudaGetLastError());
+    MFMC_LAUNCHED("nlch_solver launch 1");
     return MFMC_OK;
 }
 
@@ -120,7 +120,7 @@ mfmc_status launch_coefficients(const Model &m, const double *eps_dev, size_t ns
     if (ns == 0) return MFMC_OK;
     coef_kernel<<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(eps_dev, m.d.eps, m.ahat, m.chat, m.d.tau,
                                                                m.d.beta1, m.d.c_F, ns, coef);
-    MFMC_CUDA(cudaGetLastError());
+    MFMC_LAUNCHED("nlch_solver launch 2");
     return MFMC_OK;
 }
 
@@ -238,6 +238,7 @@ bool algo_supported(const Model &m, int algo) {
         case MFMC_ALGO_PREFIX: return constant && tile_launcher(m.R) != nullptr;
         case MFMC_ALGO_PREFIX_KAHAN:
         case MFMC_ALGO_PREFIX_TMA: return constant && tma_launcher(m.R) != nullptr;
+        case MFMC_ALGO_ROWS: return constant && (rows_supported(m, 2) || rows_supported(m, 4));
         case MFMC_ALGO_RESIDENT: {
             if (!constant || resident_launcher(m.R) == nullptr) return false;
             const int nt = resident_threads(m.d.n);
@@ -277,7 +278,7 @@ static mfmc_status launch_generic(const Model &m, const GenericArgs &base, size_
         const unsigned gy = (unsigned)std::min<size_t>(65535, cnt - o);
         step_generic_kernel<<<dim3(a.tiles, gy), GEN_NT, smem, st>>>(a);
     }
-    MFMC_CUDA(cudaGetLastError());
+    MFMC_LAUNCHED("nlch_solver launch 3");
     return MFMC_OK;
 }
 
@@ -325,7 +326,7 @@ mfmc_status encode_map(CUtensorMap *map, float *base, int P, size_t cap, int sw,
     return MFMC_OK;
 }
 
-static mfmc_status ensure_pad_scratch(Model &m, size_t ns, const TmaVariant &L) {
+static mfmc_status ensure_pad_scratch(Model &m, size_t ns, int box_w, int box_h) {
     const int G = (m.R + 3) & ~3, P = m.d.n + 2 * G;
     if (!m.d_status) {
         MFMC_CUDA(cudaMalloc((void **)&m.d_status, sizeof(int)));
@@ -342,13 +343,13 @@ static mfmc_status ensure_pad_scratch(Model &m, size_t ns, const TmaVariant &L) 
         MFMC_CUDA(cudaMalloc((void **)&m.padB, bytes));
         m.pad_cap = ns;
     }
-    if (m.maps_valid && m.map_sw == L.sw && m.map_sh == L.sh) return MFMC_OK;
+    if (m.maps_valid && m.map_sw == box_w && m.map_sh == box_h) return MFMC_OK;
     m.maps_valid = 0;
-    mfmc_status s = encode_map(&m.mapA, m.padA, P, m.pad_cap, L.sw, L.sh);
-    if (s == MFMC_OK) s = encode_map(&m.mapB, m.padB, P, m.pad_cap, L.sw, L.sh);
+    mfmc_status s = encode_map(&m.mapA, m.padA, P, m.pad_cap, box_w, box_h);
+    if (s == MFMC_OK) s = encode_map(&m.mapB, m.padB, P, m.pad_cap, box_w, box_h);
     if (s != MFMC_OK) return s;
-    m.map_sw = L.sw;
-    m.map_sh = L.sh;
+    m.map_sw = box_w;
+    m.map_sh = box_h;
     m.maps_valid = 1;
     return MFMC_OK;
 }
@@ -406,7 +407,7 @@ mfmc_status run_solve_tma_core(const Model &m, int kahan, int variant, const Ste
         const size_t total = ns * (size_t)P * (P / 4);
         const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 32);
         pad_fields_kernel<<<blocks, 256, 0, st>>>(u0, b.padB, n, G, ns);
-        MFMC_CUDA(cudaGetLastError());
+        MFMC_LAUNCHED("nlch_solver launch 4");
     }
     int dev = 0, sms = 0;
     MFMC_CUDA(cudaGetDevice(&dev));
@@ -439,7 +440,7 @@ mfmc_status run_solve_tma_core(const Model &m, int kahan, int variant, const Ste
     }
     finalize_ooi_kernel<<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(b.partials, tiles, ns,
                                                                        1.0 / ((double)n * n), ubar, ooi);
-    MFMC_CUDA(cudaGetLastError());
+    MFMC_LAUNCHED("nlch_solver launch 5");
     return MFMC_OK;
 }
 
@@ -451,7 +452,7 @@ mfmc_status run_solve_tma(Model &m, int kahan, int variant, const StepCoef *coef
     if (variant < 0 || variant >= kTmaVariants) return fail(MFMC_EINVAL, "TMA variant %d unavailable", variant);
     int tiles_x = 0;
     const int tiles = tma_tiles(m, variant, &tiles_x);
-    mfmc_status s = ensure_pad_scratch(m, ns, TL->v[variant]);
+    mfmc_status s = ensure_pad_scratch(m, ns, TL->v[variant].sw, TL->v[variant].sh);
     if (s == MFMC_OK) s = grow_buffer(&m.partials, &m.partials_cap, ns * (size_t)tiles);
     if (s != MFMC_OK) return s;
     TmaBuffers b;
@@ -463,6 +464,119 @@ mfmc_status run_solve_tma(Model &m, int kahan, int variant, const StepCoef *coef
     b.partials = m.partials;
     b.status = m.d_status;
     return run_solve_tma_core(m, kahan, variant, coef, u0, ns, nsteps, nullptr, uT, ubar, ooi, b, st);
+}
+
+// ----------------------------------------------------------------------------- row streaming
+void rows_geometry(const Model &m, int *nbox, int *bw) {
+    const int G = (m.R + 3) & ~3, P = m.d.n + 2 * G;
+    *nbox = (P + 255) / 256;
+    *bw = ((P + *nbox - 1) / *nbox + 3) & ~3;
+}
+
+mfmc_status rows_alloc_buffers(const Model &m, int bh, size_t ns, TmaBuffers *b, cudaStream_t alloc_st) {
+    const RowsLauncher *L = rows_launcher(m.R);
+    if (!L) return fail(MFMC_EINVAL, "no row-streaming kernel for R = %d", m.R);
+    if (bh < 8) return fail(MFMC_EINVAL, "band height %d < 8", bh);
+    const int G = (m.R + 3) & ~3, P = m.d.n + 2 * G;
+    int nbox = 0, bw = 0;
+    rows_geometry(m, &nbox, &bw);
+    const int bands = (m.d.n + bh - 1) / bh;
+    const size_t bytes = ns * (size_t)P * P * sizeof(float);
+    MFMC_CUDA(cudaMallocAsync((void **)&b->padA, bytes, alloc_st));
+    MFMC_CUDA(cudaMallocAsync((void **)&b->padB, bytes, alloc_st));
+    MFMC_CUDA(cudaMallocAsync((void **)&b->partials, ns * (size_t)bands * sizeof(double), alloc_st));
+    MFMC_CUDA(cudaMallocAsync((void **)&b->status, sizeof(int), alloc_st));
+    MFMC_CUDA(cudaMemsetAsync(b->status, 0, sizeof(int), alloc_st));
+    b->cap = ns;
+    mfmc_status s = encode_map(&b->mapA, b->padA, P, ns, bw, L->ch);
+    if (s == MFMC_OK) s = encode_map(&b->mapB, b->padB, P, ns, bw, L->ch);
+    return s;
+}
+
+// threads = n / rx must be a whole number of warps and at most 512
+bool rows_supported(const Model &m, int rx) {
+    return m.d.kernel == MFMC_KERNEL_CONSTANT && rows_launcher(m.R) != nullptr && (rx == 2 || rx == 4) &&
+           m.d.n % (32 * rx) == 0 && m.d.n / rx <= 512;
+}
+
+mfmc_status run_solve_rows_core(const Model &m, int bh, int rx, const StepCoef *coef, const float *u0, size_t ns,
+                                int nsteps, const int *steps_ps, float *uT, double *ubar, double *ooi,
+                                const TmaBuffers &b, cudaStream_t st) {
+    if (!rows_supported(m, rx)) return fail(MFMC_EINVAL, "row-streaming kernel unsupported (n = %d, %d columns)", m.d.n, rx);
+    const RowsLauncher *L = rows_launcher(m.R);
+    if (!L) return fail(MFMC_EINVAL, "no row-streaming kernel for R = %d", m.R);
+    if (bh < 8) return fail(MFMC_EINVAL, "band height %d < 8", bh);
+    const int n = m.d.n, G = (m.R + 3) & ~3, P = n + 2 * G;
+    int nbox = 0, bw = 0;
+    rows_geometry(m, &nbox, &bw);
+    const int bands = (n + bh - 1) / bh;
+    {
+        const size_t total = ns * (size_t)P * (P / 4);
+        const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 32);
+        pad_fields_kernel<<<blocks, 256, 0, st>>>(u0, b.padB, n, G, ns);
+        MFMC_LAUNCHED("nlch_solver launch 6");
+    }
+    const int ri = rx == 4 ? 0 : 1;
+    const int threads = n / rx;
+    const size_t smem = (size_t)4 * L->ch * bw * nbox * sizeof(float) + 1024;
+    int dev = 0, sms = 0;
+    MFMC_CUDA(cudaGetDevice(&dev));
+    MFMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const long long total = (long long)ns * bands;
+    if (total > (1ll << 30)) return fail(MFMC_EINVAL, "too many bands in one solve");
+    if (total == 0) return MFMC_OK;
+    const int grid = (int)std::min<long long>(total, (long long)sms * L->blocks_per_sm[ri](threads, smem));
+    const CUtensorMap *src = &b.mapB;
+    float *dstbuf = b.padA;
+    for (int k = 1; k <= nsteps; ++k) {
+        const bool last = k == nsteps;
+        RowsArgs a;
+        a.dst = (last && !steps_ps) ? nullptr : dstbuf;
+        a.dst_plain = (last && !steps_ps) ? uT : nullptr;
+        a.coef = coef;
+        a.partials = b.partials;
+        a.status = b.status;
+        a.steps_ps = steps_ps;
+        a.step = k;
+        a.n = n;
+        a.P = P;
+        a.BW = bw;
+        a.nbox = nbox;
+        a.BH = bh;
+        a.bands = bands;
+        a.total = (int)total;
+        a.last = (last && !steps_ps) ? 1 : 0;
+        mfmc_status s = L->fn[ri](*src, a, grid, threads, smem, st);
+        if (s != MFMC_OK) return s;
+        src = (dstbuf == b.padA) ? &b.mapA : &b.mapB;
+        dstbuf = (dstbuf == b.padA) ? b.padB : b.padA;
+    }
+    finalize_ooi_kernel<<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(b.partials, bands, ns,
+                                                                       1.0 / ((double)n * n), ubar, ooi);
+    MFMC_LAUNCHED("nlch_solver launch 7");
+    return MFMC_OK;
+}
+
+mfmc_status run_solve_rows(Model &m, int bh, int rx, const StepCoef *coef, const float *u0, size_t ns, int nsteps,
+                           float *uT, double *ubar, double *ooi, cudaStream_t st) {
+    const RowsLauncher *L = rows_launcher(m.R);
+    if (!L) return fail(MFMC_EINVAL, "no row-streaming kernel for R = %d", m.R);
+    if (bh < 8) return fail(MFMC_EINVAL, "band height %d < 8", bh);
+    int nbox = 0, bw = 0;
+    rows_geometry(m, &nbox, &bw);
+    const int bands = (m.d.n + bh - 1) / bh;
+    mfmc_status s = ensure_pad_scratch(m, ns, bw, L->ch);
+    if (s == MFMC_OK) s = grow_buffer(&m.partials, &m.partials_cap, ns * (size_t)bands);
+    if (s != MFMC_OK) return s;
+    TmaBuffers b;
+    b.padA = m.padA;
+    b.padB = m.padB;
+    b.mapA = m.mapA;
+    b.mapB = m.mapB;
+    b.cap = m.pad_cap;
+    b.partials = m.partials;
+    b.status = m.d_status;
+    return run_solve_rows_core(m, bh, rx, coef, u0, ns, nsteps, nullptr, uT, ubar, ooi, b, st);
 }
 
 mfmc_status run_resident_steps(const Model &m, const StepCoef *coef, const float *u0, size_t ns, int nsteps,
@@ -495,12 +609,16 @@ mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0,
             reduce_fields_kernel<<<g, 256, 0, st>>>(u0 + o * nn, n, ubar ? ubar + o : nullptr,
                                                     ooi ? ooi + o : nullptr);
         }
-        MFMC_CUDA(cudaGetLastError());
+        MFMC_LAUNCHED("nlch_solver launch 8");
         return MFMC_OK;
     }
     if (algo == MFMC_ALGO_PREFIX_TMA)
         return run_solve_tma(m, 0, m.tma_variant, coef, u0, ns, nsteps, uT, ubar, ooi, st);
     if (algo == MFMC_ALGO_PREFIX_KAHAN) return run_solve_tma(m, 1, 0, coef, u0, ns, nsteps, uT, ubar, ooi, st);
+    if (algo == MFMC_ALGO_ROWS) {
+        const int rx = rows_supported(m, m.rows_rx) ? m.rows_rx : 6 - m.rows_rx;
+        return run_solve_rows(m, m.rows_bh, rx, coef, u0, ns, nsteps, uT, ubar, ooi, st);
+    }
     if (algo == MFMC_ALGO_RESIDENT) return run_resident_steps(m, coef, u0, ns, nsteps, nullptr, uT, ubar, ooi, st);
     int tiles_x = 0;
     const int tiles = tiles_for(m, algo, &tiles_x);
@@ -572,7 +690,7 @@ mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0,
     }
     finalize_ooi_kernel<<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(m.partials, tiles, ns, 1.0 / (double)nn,
                                                                        ubar, ooi);
-    MFMC_CUDA(cudaGetLastError());
+    MFMC_LAUNCHED("nlch_solver launch 9");
     return MFMC_OK;
 }
 

@@ -118,7 +118,7 @@ extern "C" mfmc_status mfmc_solve_fields_noalloc(const mfmc_model *cm, const dou
             na_reduce_kernel<<<g, 256, 0, st>>>(u0 + o * (size_t)n * n, n, ubar ? ubar + o : nullptr,
                                                ooi ? ooi + o : nullptr);
         }
-        MFMC_CUDA(cudaGetLastError());
+        MFMC_LAUNCHED("noalloc launch 1");
         return MFMC_OK;
     }
     // every tile partial is rewritten at the last step, so nothing needs clearing
@@ -141,6 +141,6 @@ extern "C" mfmc_status mfmc_solve_fields_noalloc(const mfmc_model *cm, const dou
     }
     na_finalize_kernel<<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(partials, tiles, ns, 1.0 / ((double)n * n), ubar,
                                                                        ooi);
-    MFMC_CUDA(cudaGetLastError());
+    MFMC_LAUNCHED("noalloc launch 2");
     return MFMC_OK;
 }

@@ -1,5 +1,5 @@
 // Resident (whole field in shared memory) kernels for R in {1, ..., 6, 8}.
-#include "tma_step.cuh"
+#include "rows_step.cuh"
 
 namespace mfmc {
 
@@ -36,6 +36,14 @@ const TmaLauncher *tma_launcher(int R) {
     for (auto g : groups)
         if (const TmaLauncher *t = g(R)) return t;
     return nullptr;
+}
+
+const RowsLauncher *rows_launcher_a(int R);
+const RowsLauncher *rows_launcher_b(int R);
+
+const RowsLauncher *rows_launcher(int R) {
+    if (const RowsLauncher *r = rows_launcher_a(R)) return r;
+    return rows_launcher_b(R);
 }
 
 const TileLauncher *tile_launcher(int R) {

@@ -170,7 +170,7 @@ static mfmc_status launch_cohort(Cohort *c, double *res_dev) {
     }
     if (s != MFMC_OK) return s;
     scatter_results_kernel<<<(unsigned)((k + 127) / 128), 128, 0, c->st>>>(c->out, c->slot_dev, (int)k, res_dev);
-    MFMC_CUDA(cudaGetLastError());
+    MFMC_LAUNCHED("server launch 1");
     // the host vectors above are pageable: each copy was staged before its call returned
     MFMC_CUDA(cudaEventRecord(c->done, c->st));
     return MFMC_OK;

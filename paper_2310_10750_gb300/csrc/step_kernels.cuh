@@ -367,7 +367,7 @@ mfmc_status launch_tile(const TileArgs &base, size_t ns, cudaStream_t st) {
         const unsigned gy = (unsigned)(ns - s0 < 65535 ? ns - s0 : 65535);
         kern<<<dim3(a.tiles, gy), C::TXT * C::TYT, smem, st>>>(a);
     }
-    MFMC_CUDA(cudaGetLastError());
+    MFMC_LAUNCHED("step_kernels launch 1");
     return MFMC_OK;
 }
 
@@ -418,7 +418,7 @@ mfmc_status launch_resident(const ResidentArgs &a, cudaStream_t st) {
     const int cap = (per_sm > 0 ? per_sm : 1) * sms;
     const int grid = a.ns < cap ? a.ns : cap;
     kern<<<grid > 0 ? grid : 1, nt, smem, st>>>(a);
-    MFMC_CUDA(cudaGetLastError());
+    MFMC_LAUNCHED("step_kernels launch 2");
     return MFMC_OK;
 }
 

@@ -1,5 +1,5 @@
 // Register-tiled step kernels for R in {1, 2, 3, 4}.
-#include "tma_step.cuh"
+#include "rows_step.cuh"
 
 namespace mfmc {
 
@@ -27,6 +27,16 @@ const TmaLauncher *tma_launcher_a(int R) {
         case 2: return &m2;
         case 3: return &m3;
         case 4: return &m4;
+        default: return nullptr;
+    }
+}
+
+const RowsLauncher *rows_launcher_a(int R) {
+    static const RowsLauncher w2 = make_rows_launcher<2>();
+    static const RowsLauncher w4 = make_rows_launcher<4>();
+    switch (R) {
+        case 2: return &w2;
+        case 4: return &w4;
         default: return nullptr;
     }
 }

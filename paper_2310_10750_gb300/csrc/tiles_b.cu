@@ -1,5 +1,5 @@
 // Register-tiled step kernels for R in {5, 6, 8}.
-#include "tma_step.cuh"
+#include "rows_step.cuh"
 
 namespace mfmc {
 
@@ -23,6 +23,16 @@ const TmaLauncher *tma_launcher_b(int R) {
         case 5: return &m5;
         case 6: return &m6;
         case 8: return &m8;
+        default: return nullptr;
+    }
+}
+
+const RowsLauncher *rows_launcher_b(int R) {
+    static const RowsLauncher w6 = make_rows_launcher<6>();
+    static const RowsLauncher w8 = make_rows_launcher<8>();
+    switch (R) {
+        case 6: return &w6;
+        case 8: return &w8;
         default: return nullptr;
     }
 }

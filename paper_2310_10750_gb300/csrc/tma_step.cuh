@@ -296,7 +296,7 @@ mfmc_status launch_tma(const CUtensorMap &map, const TmaArgs &a, int grid, cudaS
         attr_done = true;
     }
     kern<<<grid, T::TXT * T::TYT, C::SMEM, st>>>(map, a);
-    MFMC_CUDA(cudaGetLastError());
+    MFMC_LAUNCHED("tma_step launch 1");
     return MFMC_OK;
 }
 
@@ -308,6 +308,7 @@ int tma_blocks_per_sm() {
     int per = 0;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, T::TXT * T::TYT, C::SMEM);
+    (void)cudaGetLastError();  // a failed query must not be reported by a later launch check
     return e == cudaSuccess && per > 0 ? per : 1;
 }
 

@@ -25,7 +25,7 @@ MFMC_OK, MFMC_EINVAL, MFMC_ENOMEM, MFMC_ECUDA, MFMC_ETIMEOUT, MFMC_EBUDGET, MFMC
 KERNEL_CONSTANT, KERNEL_GAUSSIAN = 0, 1
 BC_PERIODIC = 0
 IC_UNIFORM, IC_SMOOTHED_GAUSS, IC_NUCLEI = 0, 1, 2
-ALGO_AUTO, ALGO_DIRECT, ALGO_PREFIX, ALGO_PREFIX_KAHAN, ALGO_RESIDENT, ALGO_PLAIN, ALGO_PREFIX_TMA = range(7)
+ALGO_AUTO, ALGO_DIRECT, ALGO_PREFIX, ALGO_PREFIX_KAHAN, ALGO_RESIDENT, ALGO_PLAIN, ALGO_PREFIX_TMA, ALGO_ROWS = range(8)
 MAX_MODELS = 16
 
 
@@ -52,7 +52,8 @@ class mfmc_sample_params(ctypes.Structure):
 class mfmc_model_info(ctypes.Structure):
     _fields_ = [("R", ctypes.c_int), ("disc_points", ctypes.c_int), ("c_gamma", ctypes.c_double),
                 ("xi", ctypes.c_double), ("algo", ctypes.c_int), ("field_bytes", ctypes.c_size_t),
-                ("tile_variant", ctypes.c_int)]
+                ("tile_variant", ctypes.c_int), ("band_height", ctypes.c_int),
+                ("columns_per_thread", ctypes.c_int)]
 
 
 _D16 = ctypes.c_double * MAX_MODELS
@@ -93,6 +94,7 @@ _sig("mfmc_model_create", _st, [ctypes.POINTER(mfmc_model_desc), ctypes.POINTER(
 _sig("mfmc_model_destroy", None, [_vp])
 _sig("mfmc_model_query", _st, [_vp, ctypes.POINTER(mfmc_model_info)])
 _sig("mfmc_model_set_tile_variant", _st, [_vp, ctypes.c_int])
+_sig("mfmc_model_set_band_height", _st, [_vp, ctypes.c_int, ctypes.c_int])
 _sig("mfmc_sample_eps", _st, [_vp, _vp, _vp, ctypes.c_size_t, _vp])
 _sig("mfmc_init_fields", _st, [_vp, _vp, _vp, ctypes.c_size_t, _vp, _vp])
 _sig("mfmc_solve_fields", _st, [_vp, _vp, _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp])
@@ -179,6 +181,9 @@ class Model:
 
     def set_tile_variant(self, variant: int):
         _check(_L.mfmc_model_set_tile_variant(self.handle, variant))
+
+    def set_band_height(self, rows: int, columns_per_thread: int = 2):
+        _check(_L.mfmc_model_set_band_height(self.handle, rows, columns_per_thread))
 
     def info(self) -> mfmc_model_info:
         out = mfmc_model_info()
