@@ -323,12 +323,247 @@ def run_ours(args):
     return 0
 
 
+# --------------------------------------------------------------------------- other workloads
+def _seeds(base, count, offset=0):
+    import numpy as np
+    return (np.arange(count, dtype=np.uint64) + np.uint64(base + offset))
+
+
+def _batched_cost(mfmc, model, ns, seed_base):
+    """GPU seconds per sample of a batched solve (fields built on the device), and the OoIs."""
+    import numpy as np
+    import torch
+    n = model.n
+    seeds = _seeds(seed_base, ns)
+    u0 = torch.empty((ns, n, n), dtype=torch.float32, device="cuda")
+    ooi = torch.empty(ns, dtype=torch.float64, device="cuda")
+    eps = torch.tensor(mfmc.mfmc_sample_eps(model, seeds), dtype=torch.float64, device="cuda")
+    mfmc.mfmc_init_fields(model, seeds, u0)
+    mfmc.mfmc_solve_fields(model, u0, ns, eps=eps, ooi=ooi)      # tune + warm
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    mfmc.mfmc_solve_fields(model, u0, ns, eps=eps, ooi=ooi)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e-3 / ns
+
+
+def run_hierarchy(args):
+    """MFMC hierarchy with a fixed physical horizon delta = 1/32 (512^2/R=16, 256^2/8,
+    128^2/4, 64^2/2), 1000 steps, the four-nuclei initial condition of Eq. (ic) whose
+    theta is the shared random input, eps = 0.02 U[0.8, 1.2].  Pilot of 64 samples,
+    costs measured as batched GPU seconds per sample, 10 replicate MC and MFMC estimates
+    per budget, MSE against a validation mean of HF samples."""
+    import numpy as np
+    import torch
+    from paper_2310_10750_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2310_10750_gb300 import mfmc
+    base = 20231016 + 1000003 * 2
+    levels = [(512, 16), (256, 8), (128, 4), (64, 2)]
+    common = dict(eps=0.02, eps_lo=0.016, eps_hi=0.024, tau=1e-3, nsteps=1000, ic=mfmc.IC_NUCLEI)
+    models = [mfmc.Model(n=n, delta=R / n, **common) for n, R in levels]
+    cost = [_batched_cost(mfmc, m, bs, base + 10 ** 7) for m, bs in zip(models, (128, 512, 1024, 2048))]
+    names = {1: "direct", 2: "prefix", 4: "resident", 6: "prefix-tma", 7: "row-stream"}
+    algos = [names.get(m.info().algo, str(m.info().algo)) for m in models]
+    plain_cost = None
+    if not args.no_plain:
+        m0 = models[0]
+        u0 = torch.empty((1, 512, 512), dtype=torch.float32, device="cuda")
+        mfmc.mfmc_init_fields(m0, _seeds(base, 1), u0)
+        ooi = torch.empty(1, dtype=torch.float64, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mfmc.mfmc_solve_fields_algo(m0, mfmc.ALGO_PLAIN, u0, 1, ooi=ooi)
+        e1.record()
+        torch.cuda.synchronize()
+        plain_cost = e0.elapsed_time(e1) * 1e-3
+    # pilot on shared seeds
+    n_pilot = 64
+    pilot = np.stack([mfmc.mfmc_solve_batch([m] * n_pilot, _seeds(base, n_pilot))[0] for m in models])
+    # validation mean of the high-fidelity OoI
+    n_val = args.validation
+    t = time.perf_counter()
+    chunk = 4096                                         # bounded device memory per call
+    fval = np.concatenate([mfmc.mfmc_solve_batch([models[0]] * min(chunk, n_val - o),
+                                                 _seeds(base, min(chunk, n_val - o), 5 * 10 ** 6 + o))[0]
+                           for o in range(0, n_val, chunk)])
+    q_val = float(np.mean(fval))
+    t_val = time.perf_counter() - t
+    reps = 10
+    rows = []
+    next_seed = [base + 10 ** 5]
+
+    def take(count):
+        s0 = next_seed[0]
+        next_seed[0] += count
+        return s0
+
+    for b in (10.0, 30.0, 100.0, 300.0):
+        B = b * cost[0]
+        plan = mfmc.mfmc_plan(pilot, cost, B, 0)
+        p = plan.as_dict()
+        est_mfmc, est_mc, gpu_s = [], [], 0.0
+        for r in range(reps):
+            s0 = take(p["m"][-1])
+            lists = []
+            for j, i in enumerate(p["idx"]):
+                f, _ = mfmc.mfmc_solve_batch([models[i]] * p["m"][j], _seeds(s0, p["m"][j]))
+                lists.append(f)
+            est_mfmc.append(mfmc.mfmc_estimate(plan, lists))
+            m_mc = max(1, int(B // cost[0]))
+            s1 = take(m_mc)
+            f, _ = mfmc.mfmc_solve_batch([models[0]] * m_mc, _seeds(s1, m_mc))
+            est_mc.append(float(np.mean(f)))
+        mse_mfmc = float(np.mean((np.array(est_mfmc) - q_val) ** 2))
+        mse_mc = float(np.mean((np.array(est_mc) - q_val) ** 2))
+        sig1 = p["sigma_all"][0]
+        row = {"budget_gpu_s": B, "budget_over_C1": b, "subset": p["idx"], "m": p["m"],
+               "below_min_budget": p["below_min_budget"], "mse_mfmc": mse_mfmc, "mse_mc": mse_mc,
+               "mse_mfmc_theory": p["mse_theory"], "mse_mc_theory": sig1 ** 2 / max(1, int(B // cost[0])),
+               "mse_ratio_mc_over_mfmc": mse_mc / mse_mfmc if mse_mfmc > 0 else None}
+        if plain_cost:
+            row["mse_mc_plain_loop_theory"] = sig1 ** 2 / max(1e-9, B / plain_cost)
+        rows.append(row)
+    line = {"metric": "MFMC MSE per GPU-s (hierarchy)", "value": rows[2]["mse_mfmc"], "unit": "MSE at B = 100 C_1",
+            "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": "MFMC hierarchy delta=1/32: 512^2/R16, 256^2/R8, 128^2/R4, 64^2/R2, 1000 steps,"
+                                   " nuclei IC (Eq. ic), pilot 64, 10 replicates per budget",
+                       "algos": algos},
+            "cost_gpu_s_per_sample": cost, "samples_per_s_per_fidelity": [1.0 / c for c in cost],
+            "plain_loop_cost_gpu_s_per_hf_sample": plain_cost,
+            "pilot_rho": plan.as_dict()["rho_all"], "pilot_sigma": plan.as_dict()["sigma_all"],
+            "q_validation": q_val, "n_validation": n_val, "validation_s": t_val, "budgets": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serving(args):
+    """Poisson stream of solve requests of mixed fidelity (64^2 .. 1024^2 in 40/30/20/8/2 %,
+    delta = 1/32, 500-2000 steps each) through the continuous-batching server."""
+    import numpy as np
+    import torch
+    from paper_2310_10750_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2310_10750_gb300 import mfmc
+    rng = np.random.default_rng(20231016 + 1000003 * 3)
+    sizes = [64, 128, 256, 512, 1024]
+    probs = [0.40, 0.30, 0.20, 0.08, 0.02]
+    models = {n: mfmc.Model(n=n, delta=(n // 32) / n, eps=0.02, eps_lo=0.016, eps_hi=0.024, tau=1e-3,
+                            nsteps=1000, ic=mfmc.IC_SMOOTHED_GAUSS, ic_amp=0.05) for n in sizes}
+    for n, m in models.items():                           # tune each fidelity before serving
+        mfmc.mfmc_solve_batch([m] * 8, _seeds(1, 8))
+    total = args.requests
+    kinds = rng.choice(sizes, size=total, p=probs)
+    steps = rng.integers(500, 2001, size=total)
+
+    def run_stream(count, rate):
+        srv = mfmc.Server(120 << 30, 8192)
+        gaps = rng.exponential(1.0 / rate, size=count) if rate else np.zeros(count)
+        t0 = time.perf_counter()
+        t_next = t0
+        tickets = []
+        for i in range(count):
+            t_next += gaps[i]
+            while True:
+                now = time.perf_counter()
+                if now >= t_next:
+                    break
+                time.sleep(min(0.0005, t_next - now))
+            p = mfmc.make_params(1, nsteps=[int(steps[i])])
+            tickets.append(srv.submit(models[int(kinds[i])], 7 + i, params=p[0]))
+        srv.drain()
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        for t in tickets:
+            srv.poll(t)
+        srv.close()
+        return st, wall
+
+    cap_n = min(2000, total)
+    st_cap, wall_cap = run_stream(cap_n, 0.0)              # all at once: capacity
+    capacity = cap_n / wall_cap
+    st, wall = run_stream(total, 0.8 * capacity)
+    line = {"metric": "p50/p99 solve latency (serving)", "value": st["p99_latency_s"], "unit": "s (p99)",
+            "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": f"{total} requests, Poisson at 0.8 x measured capacity, n in 64..1024 "
+                                   "(40/30/20/8/2 %), R = n/32, 500-2000 steps, 120 GB budget"},
+            "p50_latency_s": st["p50_latency_s"], "p99_latency_s": st["p99_latency_s"],
+            "mean_latency_s": st["mean_latency_s"], "samples_per_s": st["samples_per_s"],
+            "capacity_samples_per_s": capacity, "arrival_rate": 0.8 * capacity, "wall_s": wall,
+            "completed": st["completed"], "peak_inflight": st["peak_inflight"], "peak_bytes": st["peak_bytes"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_large(args):
+    """1024^2, delta = 32h (3209-point disc), 2000 steps, 64 samples: throughput of the
+    autotuned algorithm and of the direct sum, and the FP32 vs compensated (Kahan) sums
+    against the FP64 oracle on samples 0-3 (oracle run for a bounded number of steps)."""
+    import numpy as np
+    import torch
+    from paper_2310_10750_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2310_10750_gb300 import mfmc
+    import oracle
+    n, R, steps, ns = 1024, 32, 2000, 64
+    base = 20231016 + 1000003 * 4
+    kw = dict(n=n, delta=R / n, eps=0.02, eps_lo=0.016, eps_hi=0.024, tau=1e-3, ic=mfmc.IC_SMOOTHED_GAUSS,
+              ic_amp=0.05)
+    model = mfmc.Model(nsteps=steps, **kw)
+    c = _batched_cost(mfmc, model, ns, base)
+    names = {1: "direct", 2: "prefix", 4: "resident", 6: "prefix-tma", 7: "row-stream"}
+    algo = names.get(model.info().algo, str(model.info().algo))
+    direct_c = None
+    if not args.no_plain:
+        md = mfmc.Model(nsteps=20, algo=mfmc.ALGO_DIRECT, **kw)
+        direct_c = _batched_cost(mfmc, md, ns, base) * steps / 20
+    k = args.oracle_steps
+    prec = []
+    seeds = _seeds(base, 4)
+    o = oracle.OracleModel(n=n, delta=R / n, eps=0.02, eps_lo=0.016, eps_hi=0.024, tau=1e-3, nsteps=k, ic=1,
+                           ic_amp=0.05)
+    for algo_id, label in ((mfmc.ALGO_PREFIX_TMA, "fp32"), (mfmc.ALGO_PREFIX_KAHAN, "fp32-kahan")):
+        g = mfmc.Model(nsteps=k, algo=algo_id, **kw)
+        if algo_id == mfmc.ALGO_PREFIX_TMA:
+            g.set_tile_variant(0)
+        u0 = torch.empty((4, n, n), dtype=torch.float32, device="cuda")
+        uT = torch.empty_like(u0)
+        ooi = torch.empty(4, dtype=torch.float64, device="cuda")
+        eps = torch.tensor(mfmc.mfmc_sample_eps(g, seeds), dtype=torch.float64, device="cuda")
+        mfmc.mfmc_init_fields(g, seeds, u0)
+        mfmc.mfmc_solve_fields(g, u0, 4, eps=eps, uT=uT, ooi=ooi)
+        torch.cuda.synchronize()
+        prec.append((label, ooi.cpu().numpy(), uT.cpu().numpy()))
+    errs = {}
+    for i, s in enumerate(seeds):
+        fr, _, ur, _ = o.solve_sample(int(s))
+        for label, f, u in prec:
+            e = errs.setdefault(label, {"max_rel_ooi_err": 0.0, "max_abs_field_err": 0.0})
+            e["max_rel_ooi_err"] = max(e["max_rel_ooi_err"], abs(f[i] - fr) / fr)
+            e["max_abs_field_err"] = max(e["max_abs_field_err"], float(np.abs(u[i] - ur).max()))
+    pts = ns * n * n * steps
+    line = {"metric": "grid-pt updates/s (large HF)", "value": pts / (c * ns), "unit": METRIC,
+            "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "1024^2, delta=32h (3209-pt disc), 2000 steps, 64 samples", "algo": algo},
+            "gpu_s_per_sample": c, "direct_sum_gpu_s_per_sample": direct_c,
+            "precision_vs_oracle": {"samples": 4, "oracle_steps": k, **errs}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="single", choices=["single", "hierarchy", "serving", "large"],
+                    help="single (the headline, default), or one of the other measured configurations")
+    ap.add_argument("--validation", type=int, default=2048, help="hierarchy: HF samples of the validation mean")
+    ap.add_argument("--requests", type=int, default=20000, help="serving: requests in the stream")
+    ap.add_argument("--oracle-steps", type=int, default=100, help="large: oracle steps of the precision sweep")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -341,6 +576,12 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "hierarchy":
+        return run_hierarchy(args)
+    if args.workload == "serving":
+        return run_serving(args)
+    if args.workload == "large":
+        return run_large(args)
     return run_ours(args)
 
 

@@ -46,6 +46,7 @@ struct Cohort {
     std::vector<int> slots;  // result slot of each request
     size_t bytes = 0;
     bool resident = false;
+    bool rows = false;       // the model was tuned to the row-streaming kernel
     int variant = 0;
     cudaStream_t st = nullptr;
     cudaEvent_t done = nullptr;
@@ -162,6 +163,11 @@ static mfmc_status launch_cohort(Cohort *c, double *res_dev) {
     if (s != MFMC_OK) return s;
     if (c->resident) {
         s = run_resident_steps(m, c->coef, c->u0, k, max_steps, c->steps, nullptr, c->out + k, c->out, c->st);
+    } else if (c->rows) {
+        s = rows_alloc_buffers(m, m.rows_bh, k, &c->tb, c->st);
+        if (s == MFMC_OK)
+            s = run_solve_rows_core(m, m.rows_bh, m.rows_rx, c->coef, c->u0, k, max_steps, c->steps, nullptr,
+                                    c->out + k, c->out, c->tb, c->st);
     } else {
         s = tma_alloc_buffers(m, c->variant, k, &c->tb, c->st);
         if (s == MFMC_OK)
@@ -197,6 +203,8 @@ static void server_loop(mfmc_server *S) {
                     c = new Cohort();
                     c->model = r.model;
                     c->resident = res;
+                    c->rows = !res && r.model->tuned && r.model->algo == MFMC_ALGO_ROWS &&
+                              rows_supported(*r.model, r.model->rows_rx);
                     c->variant = r.model->tma_variant;
                     fresh.push_back(c);
                 }
