@@ -123,7 +123,7 @@ typedef struct {
     double xi;             /* c_gamma - c_F, Eq. (xi_constant)                      */
     int algo;              /* mfmc_algo the solver uses for this model             */
     size_t field_bytes;    /* n * n * 4                                             */
-    int tile_variant;      /* tile shape of the TMA kernel (0..4) the solver uses  */
+    int tile_variant;      /* tile shape of the TMA kernel (0..7) the solver uses  */
     int band_height;       /* band height of the row-streaming kernel              */
     int columns_per_thread;/* columns per thread of the row-streaming kernel       */
 } mfmc_model_info;
@@ -149,7 +149,7 @@ void mfmc_model_destroy(mfmc_model *model);
 /* Derived constants of a model. */
 mfmc_status mfmc_model_query(const mfmc_model *model, mfmc_model_info *out);
 
-/* Pin the tile shape (0..4) of the TMA kernel instead of letting the autotuner choose
+/* Pin the tile shape (0..7) of the TMA kernel instead of letting the autotuner choose
  * (for measurements and tests).  MFMC_EINVAL for an unknown variant. */
 mfmc_status mfmc_model_set_tile_variant(mfmc_model *model, int variant);
 

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "mfmc_internal.h"
+#include "tma_step.cuh"
 
 namespace mfmc {
 
@@ -37,7 +38,7 @@ mfmc_status autotune(Model &m, cudaStream_t st) {
     for (int a : {MFMC_ALGO_RESIDENT, MFMC_ALGO_ROWS, MFMC_ALGO_PREFIX_TMA, MFMC_ALGO_PREFIX, MFMC_ALGO_DIRECT}) {
         if (!algo_supported(m, a)) continue;
         if (a == MFMC_ALGO_PREFIX_TMA) {
-            for (int v = 0; v < 5; ++v) cands.push_back({a, v});
+            for (int v = 0; v < kTmaVariants; ++v) cands.push_back({a, v});
         } else if (a == MFMC_ALGO_ROWS) {
             // second: band height * 8 + columns per thread
             for (int rx : {2, 4})

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "mfmc_internal.h"
+#include "tma_step.cuh"
 
 namespace mfmc {
 
@@ -208,7 +209,7 @@ mfmc_status mfmc_model_query(const mfmc_model *m, mfmc_model_info *out) {
 }
 
 mfmc_status mfmc_model_set_tile_variant(mfmc_model *m, int variant) {
-    if (!m || variant < 0 || variant > 4) return fail(MFMC_EINVAL, "invalid tile variant");
+    if (!m || variant < 0 || variant >= kTmaVariants) return fail(MFMC_EINVAL, "invalid tile variant");
     std::lock_guard<std::mutex> lk(m->mu);
     m->tma_variant = variant;
     return MFMC_OK;

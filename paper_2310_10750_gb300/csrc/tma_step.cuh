@@ -88,9 +88,9 @@ constexpr long long kWaitLimit = 1ll << 24;
 // STAGES = 2: the next item's copy is issued before computing the current one;
 // STAGES = 1: it is issued after the current item is done (less shared memory per CTA,
 // so more CTAs per SM overlap their copies with each other's compute).
-template <int R, int RY, int TXT, int TYT, int ALGO, int STAGES = 2>
-__global__ void __launch_bounds__(TXT *TYT) step_tma_kernel(const __grid_constant__ CUtensorMap src_map,
-                                                            TmaArgs a) {
+template <int R, int RY, int TXT, int TYT, int ALGO, int STAGES = 2, int MINB = 1>
+__global__ void __launch_bounds__(TXT *TYT, MINB) step_tma_kernel(const __grid_constant__ CUtensorMap src_map,
+                                                                  TmaArgs a) {
     using C = TmaCfg<R, RY, TXT, TYT, STAGES>;
     constexpr int RX = 4, R4 = C::R4, SW = C::SW, NT = TXT * TYT, WIN = RX + 2 * R4;
     constexpr DiscRows<R> disc{};
@@ -247,29 +247,44 @@ __global__ void pad_fields_kernel(const float *u, float *dst, int n, int G, size
 //   variant 1: 4 x 8 outputs per thread,  64 x 128 tile, 256 threads
 //   variant 2: 4 x 8 outputs per thread,  64 x 64 tile,  128 threads
 //   variants 3, 4: shapes 0 and 1 with a single shared-memory stage
-constexpr int kTmaVariants = 5;
+//   variant 5: variant 4 with at most 64 registers per thread (4 CTAs per SM)
+//   variant 6: 4 x 16 outputs per thread, 64 x 256 tile, 256 threads, one stage, <= 128 registers
+//   variant 7: 4 x 16 outputs per thread, 64 x 128 tile, 128 threads, one stage, <= 168 registers
+constexpr int kTmaVariants = 8;
 
 template <int V>
 struct TmaShape;
 template <>
 struct TmaShape<0> {
-    static constexpr int RY = 16, TXT = 16, TYT = 8, STAGES = 2;
+    static constexpr int RY = 16, TXT = 16, TYT = 8, STAGES = 2, MINB = 1;
 };
 template <>
 struct TmaShape<1> {
-    static constexpr int RY = 8, TXT = 16, TYT = 16, STAGES = 2;
+    static constexpr int RY = 8, TXT = 16, TYT = 16, STAGES = 2, MINB = 1;
 };
 template <>
 struct TmaShape<2> {
-    static constexpr int RY = 8, TXT = 16, TYT = 8, STAGES = 2;
+    static constexpr int RY = 8, TXT = 16, TYT = 8, STAGES = 2, MINB = 1;
 };
 template <>
 struct TmaShape<3> {
-    static constexpr int RY = 16, TXT = 16, TYT = 8, STAGES = 1;
+    static constexpr int RY = 16, TXT = 16, TYT = 8, STAGES = 1, MINB = 1;
 };
 template <>
 struct TmaShape<4> {
-    static constexpr int RY = 8, TXT = 16, TYT = 16, STAGES = 1;
+    static constexpr int RY = 8, TXT = 16, TYT = 16, STAGES = 1, MINB = 1;
+};
+template <>
+struct TmaShape<5> {
+    static constexpr int RY = 8, TXT = 16, TYT = 16, STAGES = 1, MINB = 4;
+};
+template <>
+struct TmaShape<6> {
+    static constexpr int RY = 16, TXT = 16, TYT = 16, STAGES = 1, MINB = 2;
+};
+template <>
+struct TmaShape<7> {
+    static constexpr int RY = 16, TXT = 16, TYT = 8, STAGES = 1, MINB = 3;
 };
 
 typedef mfmc_status (*TmaFn)(const CUtensorMap &, const TmaArgs &, int grid, cudaStream_t);
@@ -289,7 +304,7 @@ template <int R, int V, int ALGO>
 mfmc_status launch_tma(const CUtensorMap &map, const TmaArgs &a, int grid, cudaStream_t st) {
     using T = TmaShape<V>;
     using C = TmaCfg<R, T::RY, T::TXT, T::TYT, T::STAGES>;
-    auto kern = step_tma_kernel<R, T::RY, T::TXT, T::TYT, ALGO, T::STAGES>;
+    auto kern = step_tma_kernel<R, T::RY, T::TXT, T::TYT, ALGO, T::STAGES, T::MINB>;
     static bool attr_done = false;
     if (!attr_done) {
         MFMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
@@ -304,7 +319,7 @@ template <int R, int V>
 int tma_blocks_per_sm() {
     using T = TmaShape<V>;
     using C = TmaCfg<R, T::RY, T::TXT, T::TYT, T::STAGES>;
-    auto k = step_tma_kernel<R, T::RY, T::TXT, T::TYT, 1, T::STAGES>;
+    auto k = step_tma_kernel<R, T::RY, T::TXT, T::TYT, 1, T::STAGES, T::MINB>;
     int per = 0;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, T::TXT * T::TYT, C::SMEM);
@@ -342,6 +357,9 @@ TmaLauncher make_tma_launcher() {
     L.v[2] = make_tma_variant<R, 2, false>();
     L.v[3] = make_tma_variant<R, 3, false>();
     L.v[4] = make_tma_variant<R, 4, false>();
+    L.v[5] = make_tma_variant<R, 5, false>();
+    L.v[6] = make_tma_variant<R, 6, false>();
+    L.v[7] = make_tma_variant<R, 7, false>();
     return L;
 }
 
