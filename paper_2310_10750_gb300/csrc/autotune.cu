@@ -76,23 +76,37 @@ mfmc_status autotune(Model &m, cudaStream_t st) {
         };
         for (auto a : cands) {
             if (s != MFMC_OK) break;
-            s = run(a);  // warm-up
+            // a candidate that cannot run this model (for example a tile taller than a TMA
+            // box allows) is skipped; a failing CUDA call that is not a launch refusal stops
+            mfmc_status cs = run(a);  // warm-up
+            if (cs != MFMC_OK) {
+                (void)cudaGetLastError();
+                if (cudaStreamSynchronize(st) != cudaSuccess) {
+                    s = cs;
+                    break;
+                }
+                continue;
+            }
             float ms_min = 1e30f;
-            for (int rep = 0; rep < 3 && s == MFMC_OK; ++rep) {
+            for (int rep = 0; rep < 3 && cs == MFMC_OK; ++rep) {
                 cudaEventRecord(e0, st);
-                s = run(a);
+                cs = run(a);
                 cudaEventRecord(e1, st);
                 e = cudaEventSynchronize(e1);
-                if (e != cudaSuccess) s = cuda_fail(e, "autotune timing");
+                if (e != cudaSuccess) {
+                    s = cuda_fail(e, "autotune timing");
+                    break;
+                }
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, e0, e1);
                 ms_min = std::min(ms_min, ms);
             }
-            if (s == MFMC_OK && ms_min < best_ms) {
+            if (s == MFMC_OK && cs == MFMC_OK && ms_min < best_ms) {
                 best_ms = ms_min;
                 best = a;
             }
         }
+        set_error("");
         cudaStreamSynchronize(st);
         cudaFree(u0);
         cudaFree(coef);

@@ -158,6 +158,10 @@ mfmc_status run_solve_tma_core(const Model &m, int kahan, int variant, const Ste
                                const TmaBuffers &b, cudaStream_t st);
 mfmc_status run_resident_steps(const Model &m, const StepCoef *coef, const float *u0, size_t ns, int nsteps,
                                const int *steps_ps, float *uT, double *ubar, double *ooi, cudaStream_t st);
+// OoI from per-tile partials (tile order), and copying fields into a ghost frame.
+mfmc_status launch_finalize(const double *partials, int tiles, size_t ns, int n, double *ubar, double *ooi,
+                            cudaStream_t st);
+mfmc_status launch_pad(const float *u0, float *padded, int n, int G, size_t ns, cudaStream_t st);
 // Row-streaming kernel: geometry, buffers and solve with band height bh.
 void rows_geometry(const Model &m, int *nbox, int *bw);
 mfmc_status rows_alloc_buffers(const Model &m, int bh, size_t ns, TmaBuffers *b, cudaStream_t alloc_st);

@@ -213,6 +213,25 @@ __global__ void finalize_ooi_kernel(const double *partials, int tiles, size_t ns
     if (ooi) ooi[i] = 0.5 * (1.0 + mean);
 }
 
+mfmc_status launch_finalize(const double *partials, int tiles, size_t ns, int n, double *ubar, double *ooi,
+                            cudaStream_t st) {
+    if (ns == 0) return MFMC_OK;
+    finalize_ooi_kernel<<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(partials, tiles, ns, 1.0 / ((double)n * n), ubar,
+                                                                       ooi);
+    MFMC_LAUNCHED("finalize");
+    return MFMC_OK;
+}
+
+mfmc_status launch_pad(const float *u0, float *padded, int n, int G, size_t ns, cudaStream_t st) {
+    const int P = n + 2 * G;
+    const size_t total = ns * (size_t)P * (P / 4);
+    const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 32);
+    if (total == 0) return MFMC_OK;
+    pad_fields_kernel<<<blocks, 256, 0, st>>>(u0, padded, n, G, ns);
+    MFMC_LAUNCHED("pad");
+    return MFMC_OK;
+}
+
 __global__ void reduce_fields_kernel(const float *u, int n, double *ubar, double *ooi) {
     __shared__ double red[256];
     const size_t nn = (size_t)n * n;

@@ -85,15 +85,112 @@ struct TmaCfg {
 
 constexpr long long kWaitLimit = 1ll << 24;
 
+// One tile item: disc sums from the staged tile `s` (tile + halo, row pitch SW), the
+// update and projection, stores of the outputs (and ghost images), and the FP64 partial
+// of the OoI when `last`.  Shared by the single-fidelity and the mixed-fidelity kernels.
+template <int R, int RY, int TXT, int TYT, int ALGO>
+__device__ __forceinline__ void tma_tile_compute(const float *s, const TmaArgs &a, int sample, int tile, int x0,
+                                                 int y0, bool last, double *red) {
+    constexpr int RX = 4, R4 = (R + 3) & ~3, SW = 4 * TXT + 2 * R4, NT = TXT * TYT, WIN = RX + 2 * R4;
+    constexpr DiscRows<R> disc{};
+    const int tid = threadIdx.x;
+    const int tx = tid % TXT, ty = tid / TXT, ox = tx * RX, oy = ty * RY;
+    const int n = a.n, G = R4;
+    float acc[RY][RX];
+    float cmp[ALGO == 2 ? RY : 1][RX];
+#pragma unroll
+    for (int j = 0; j < RY; ++j)
+#pragma unroll
+        for (int i = 0; i < RX; ++i) {
+            acc[j][i] = 0.f;
+            cmp[ALGO == 2 ? j : 0][i] = 0.f;
+        }
+#pragma unroll
+    for (int r = 0; r < RY + 2 * R; ++r) {
+        const float4 *rowp = reinterpret_cast<const float4 *>(s + (oy + r) * SW + ox);
+        float v[WIN];
+#pragma unroll
+        for (int q = 0; q < WIN / 4; ++q) {
+            const float4 t = rowp[q];
+            v[4 * q + 0] = t.x;
+            v[4 * q + 1] = t.y;
+            v[4 * q + 2] = t.z;
+            v[4 * q + 3] = t.w;
+        }
+        float p[RX + 2 * R + 1];
+        p[0] = 0.f;
+#pragma unroll
+        for (int q = 0; q < RX + 2 * R; ++q) p[q + 1] = p[q] + v[R4 - R + q];
+#pragma unroll
+        for (int j = 0; j < RY; ++j) {
+            const int dy = r - R - j;
+            if (dy >= -R && dy <= R) {
+                const int w = disc.w[dy < 0 ? -dy : dy];
+#pragma unroll
+                for (int i = 0; i < RX; ++i) {
+                    const float h = p[i + R + w + 1] - p[i + R - w];
+                    if (ALGO != 2) {
+                        acc[j][i] += h;
+                    } else {
+                        const float y = h - cmp[ALGO == 2 ? j : 0][i];
+                        const float t = acc[j][i] + y;
+                        cmp[ALGO == 2 ? j : 0][i] = (t - acc[j][i]) - y;
+                        acc[j][i] = t;
+                    }
+                }
+            }
+        }
+    }
+
+    const StepCoef cf = a.coef[sample];
+    double part = 0.0;
+    const size_t nn = (size_t)n * n, PP = (size_t)a.P * a.P;
+#pragma unroll
+    for (int j = 0; j < RY; ++j) {
+        const float4 c4v = *reinterpret_cast<const float4 *>(s + (oy + j + R) * SW + ox + R4);
+        const float uc[4] = {c4v.x, c4v.y, c4v.z, c4v.w};
+        float o[4];
+#pragma unroll
+        for (int i = 0; i < RX; ++i) {
+            const float sd = fmaf(-cf.c0, uc[i], acc[j][i]);
+            const float v = uc[i] + fmaf(cf.c1, sd, cf.c2 * uc[i]);
+            o[i] = fminf(1.f, fmaxf(-1.f, v));
+        }
+        const int y = y0 + oy + j, x = x0 + ox;
+        if (y < n && x < n) {
+            const float4 val = make_float4(o[0], o[1], o[2], o[3]);
+            if (a.dst_plain) {
+                *reinterpret_cast<float4 *>(a.dst_plain + sample * nn + (size_t)y * n + x) = val;
+            } else if (a.dst) {
+                float *d = a.dst + sample * PP;
+                const int rows[3] = {G + y, y < G ? G + y + n : -1, y >= n - G ? G + y - n : -1};
+                const int cols[3] = {G + x, x < G ? G + x + n : -1, x >= n - G ? G + x - n : -1};
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    if (rows[q] < 0) continue;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        if (cols[c] < 0) continue;
+                        *reinterpret_cast<float4 *>(d + (size_t)rows[q] * a.P + cols[c]) = val;
+                    }
+                }
+            }
+            if (last) part += ((double)o[0] + (double)o[1]) + ((double)o[2] + (double)o[3]);
+        }
+    }
+    if (last) {
+        const double t = block_sum_fixed<NT>(part, red);
+        if (tid == 0) a.partials[(size_t)sample * a.tiles + tile] = t;
+    }
+}
+
 // STAGES = 2: the next item's copy is issued before computing the current one;
 // STAGES = 1: it is issued after the current item is done (less shared memory per CTA,
 // so more CTAs per SM overlap their copies with each other's compute).
-template <int R, int RY, int TXT, int TYT, int ALGO, int STAGES = 2, int MINB = 1>
-__global__ void __launch_bounds__(TXT *TYT, MINB) step_tma_kernel(const __grid_constant__ CUtensorMap src_map,
-                                                                  TmaArgs a) {
+template <int R, int RY, int TXT, int TYT, int ALGO, int STAGES>
+__device__ __forceinline__ void tma_step_body(const CUtensorMap &src_map, const TmaArgs &a) {
     using C = TmaCfg<R, RY, TXT, TYT, STAGES>;
-    constexpr int RX = 4, R4 = C::R4, SW = C::SW, NT = TXT * TYT, WIN = RX + 2 * R4;
-    constexpr DiscRows<R> disc{};
+    constexpr int R4 = C::R4, NT = TXT * TYT;
     extern __shared__ unsigned char smem_raw[];
     float *base = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ __align__(8) uint64_t bars[2];
@@ -109,7 +206,6 @@ __global__ void __launch_bounds__(TXT *TYT, MINB) step_tma_kernel(const __grid_c
     }
     __syncthreads();
 
-    const int n = a.n, G = R4;
     auto issue = [&](int item, int stage) {
         const int sample = item / a.tiles, tile = item - sample * a.tiles;
         const int x0 = (tile % a.tiles_x) * C::TX, y0 = (tile / a.tiles_x) * C::TY;
@@ -118,7 +214,6 @@ __global__ void __launch_bounds__(TXT *TYT, MINB) step_tma_kernel(const __grid_c
         tma_load_3d(base + stage * C::STAGE_FLOATS, &src_map, &bars[stage], x0, y0 + R4 - R, sample);
     };
 
-    const int tx = tid % TXT, ty = tid / TXT, ox = tx * RX, oy = ty * RY;
     int k = 0;
     const int stride = gridDim.x;
     const int first = next_active(a, blockIdx.x, stride);
@@ -146,95 +241,32 @@ __global__ void __launch_bounds__(TXT *TYT, MINB) step_tma_kernel(const __grid_c
         const int x0 = (tile % a.tiles_x) * C::TX, y0 = (tile / a.tiles_x) * C::TY;
         const bool last = a.last || (a.steps_ps != nullptr && a.step == a.steps_ps[sample]);
 
-        float acc[RY][RX];
-        float cmp[ALGO == 2 ? RY : 1][RX];
-#pragma unroll
-        for (int j = 0; j < RY; ++j)
-#pragma unroll
-            for (int i = 0; i < RX; ++i) {
-                acc[j][i] = 0.f;
-                cmp[ALGO == 2 ? j : 0][i] = 0.f;
-            }
-#pragma unroll
-        for (int r = 0; r < RY + 2 * R; ++r) {
-            const float4 *rowp = reinterpret_cast<const float4 *>(s + (oy + r) * SW + ox);
-            float v[WIN];
-#pragma unroll
-            for (int q = 0; q < WIN / 4; ++q) {
-                const float4 t = rowp[q];
-                v[4 * q + 0] = t.x;
-                v[4 * q + 1] = t.y;
-                v[4 * q + 2] = t.z;
-                v[4 * q + 3] = t.w;
-            }
-            float p[RX + 2 * R + 1];
-            p[0] = 0.f;
-#pragma unroll
-            for (int q = 0; q < RX + 2 * R; ++q) p[q + 1] = p[q] + v[R4 - R + q];
-#pragma unroll
-            for (int j = 0; j < RY; ++j) {
-                const int dy = r - R - j;
-                if (dy >= -R && dy <= R) {
-                    const int w = disc.w[dy < 0 ? -dy : dy];
-#pragma unroll
-                    for (int i = 0; i < RX; ++i) {
-                        const float h = p[i + R + w + 1] - p[i + R - w];
-                        if (ALGO != 2) {
-                            acc[j][i] += h;
-                        } else {
-                            const float y = h - cmp[ALGO == 2 ? j : 0][i];
-                            const float t = acc[j][i] + y;
-                            cmp[ALGO == 2 ? j : 0][i] = (t - acc[j][i]) - y;
-                            acc[j][i] = t;
-                        }
-                    }
-                }
-            }
-        }
-
-        const StepCoef cf = a.coef[sample];
-        double part = 0.0;
-        const size_t nn = (size_t)n * n, PP = (size_t)a.P * a.P;
-#pragma unroll
-        for (int j = 0; j < RY; ++j) {
-            const float4 c4v = *reinterpret_cast<const float4 *>(s + (oy + j + R) * SW + ox + R4);
-            const float uc[4] = {c4v.x, c4v.y, c4v.z, c4v.w};
-            float o[4];
-#pragma unroll
-            for (int i = 0; i < RX; ++i) {
-                const float sd = fmaf(-cf.c0, uc[i], acc[j][i]);
-                const float v = uc[i] + fmaf(cf.c1, sd, cf.c2 * uc[i]);
-                o[i] = fminf(1.f, fmaxf(-1.f, v));
-            }
-            const int y = y0 + oy + j, x = x0 + ox;
-            if (y < n && x < n) {
-                const float4 val = make_float4(o[0], o[1], o[2], o[3]);
-                if (a.dst_plain) {
-                    *reinterpret_cast<float4 *>(a.dst_plain + sample * nn + (size_t)y * n + x) = val;
-                } else if (a.dst) {
-                    float *d = a.dst + sample * PP;
-                    const int rows[3] = {G + y, y < G ? G + y + n : -1, y >= n - G ? G + y - n : -1};
-                    const int cols[3] = {G + x, x < G ? G + x + n : -1, x >= n - G ? G + x - n : -1};
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        if (rows[q] < 0) continue;
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            if (cols[c] < 0) continue;
-                            *reinterpret_cast<float4 *>(d + (size_t)rows[q] * a.P + cols[c]) = val;
-                        }
-                    }
-                }
-                if (last) part += ((double)o[0] + (double)o[1]) + ((double)o[2] + (double)o[3]);
-            }
-        }
-        if (last) {
-            const double t = block_sum_fixed<NT>(part, red);
-            if (tid == 0) a.partials[(size_t)sample * a.tiles + tile] = t;
-        }
+        tma_tile_compute<R, RY, TXT, TYT, ALGO>(s, a, sample, tile, x0, y0, last, red);
         __syncthreads();  // every thread is done with this stage before it is refilled
         if (STAGES == 1 && tid == 0 && nxt < a.total) issue(nxt, 0);
     }
+}
+
+// The kernel, with the compiler's own register budget, and a variant whose register use
+// is capped so that MINB CTAs fit on an SM.
+template <int R, int RY, int TXT, int TYT, int ALGO, int STAGES = 2>
+__global__ void __launch_bounds__(TXT *TYT) step_tma_kernel(const __grid_constant__ CUtensorMap src_map,
+                                                            TmaArgs a) {
+    tma_step_body<R, RY, TXT, TYT, ALGO, STAGES>(src_map, a);
+}
+
+template <int R, int RY, int TXT, int TYT, int ALGO, int STAGES, int MINB>
+__global__ void __launch_bounds__(TXT *TYT, MINB) step_tma_kernel_capped(const __grid_constant__ CUtensorMap src_map,
+                                                                         TmaArgs a) {
+    tma_step_body<R, RY, TXT, TYT, ALGO, STAGES>(src_map, a);
+}
+
+template <int R, int RY, int TXT, int TYT, int ALGO, int STAGES, int MINB>
+constexpr auto tma_kernel_ptr() {
+    if constexpr (MINB <= 1)
+        return &step_tma_kernel<R, RY, TXT, TYT, ALGO, STAGES>;
+    else
+        return &step_tma_kernel_capped<R, RY, TXT, TYT, ALGO, STAGES, MINB>;
 }
 
 // Copy unpadded fields [ns][n][n] into padded scratch [ns][P][P] including the frame
@@ -248,7 +280,7 @@ __global__ void pad_fields_kernel(const float *u, float *dst, int n, int G, size
 //   variant 2: 4 x 8 outputs per thread,  64 x 64 tile,  128 threads
 //   variants 3, 4: shapes 0 and 1 with a single shared-memory stage
 //   variant 5: variant 4 with at most 64 registers per thread (4 CTAs per SM)
-//   variant 6: 4 x 16 outputs per thread, 64 x 256 tile, 256 threads, one stage, <= 128 registers
+//   variant 6: 4 x 16 outputs per thread, 128 x 128 tile, 256 threads, one stage, <= 128 registers
 //   variant 7: 4 x 16 outputs per thread, 64 x 128 tile, 128 threads, one stage, <= 168 registers
 constexpr int kTmaVariants = 8;
 
@@ -280,7 +312,7 @@ struct TmaShape<5> {
 };
 template <>
 struct TmaShape<6> {
-    static constexpr int RY = 16, TXT = 16, TYT = 16, STAGES = 1, MINB = 2;
+    static constexpr int RY = 16, TXT = 32, TYT = 8, STAGES = 1, MINB = 2;
 };
 template <>
 struct TmaShape<7> {
@@ -304,7 +336,7 @@ template <int R, int V, int ALGO>
 mfmc_status launch_tma(const CUtensorMap &map, const TmaArgs &a, int grid, cudaStream_t st) {
     using T = TmaShape<V>;
     using C = TmaCfg<R, T::RY, T::TXT, T::TYT, T::STAGES>;
-    auto kern = step_tma_kernel<R, T::RY, T::TXT, T::TYT, ALGO, T::STAGES, T::MINB>;
+    auto kern = tma_kernel_ptr<R, T::RY, T::TXT, T::TYT, ALGO, T::STAGES, T::MINB>();
     static bool attr_done = false;
     if (!attr_done) {
         MFMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
@@ -319,7 +351,7 @@ template <int R, int V>
 int tma_blocks_per_sm() {
     using T = TmaShape<V>;
     using C = TmaCfg<R, T::RY, T::TXT, T::TYT, T::STAGES>;
-    auto k = step_tma_kernel<R, T::RY, T::TXT, T::TYT, 1, T::STAGES, T::MINB>;
+    auto k = tma_kernel_ptr<R, T::RY, T::TXT, T::TYT, 1, T::STAGES, T::MINB>();
     int per = 0;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, T::TXT * T::TYT, C::SMEM);

@@ -100,6 +100,7 @@ _sig("mfmc_init_fields", _st, [_vp, _vp, _vp, ctypes.c_size_t, _vp, _vp])
 _sig("mfmc_solve_fields", _st, [_vp, _vp, _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp])
 _sig("mfmc_solve_fields_algo", _st, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp])
 _sig("mfmc_solve_batch", _st, [_vp, _vp, _vp, ctypes.c_size_t, _vp, _vp])
+_sig("mfmc_solve_batch_mixed", _st, [_vp, _vp, _vp, ctypes.c_size_t, _vp, _vp])
 _sig("mfmc_pilot_stats", _st, [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp])
 _sig("mfmc_plan", _st, [ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_double, ctypes.c_int, _vp, ctypes.c_int,
                         ctypes.POINTER(mfmc_plan_t)])
@@ -255,6 +256,19 @@ def mfmc_solve_batch(models: Sequence[Model], seeds, params=None):
     ubar = np.zeros(ns)
     _check(_L.mfmc_solve_batch(ctypes.addressof(handles), ctypes.addressof(params) if params is not None else None,
                                s.ctypes.data, ns, ooi.ctypes.data, ubar.ctypes.data))
+    return ooi, ubar
+
+
+def mfmc_solve_batch_mixed(models: Sequence[Model], seeds, params=None):
+    """mfmc_solve_batch with one mixed-fidelity launch per step -> (ooi, ubar) host arrays."""
+    s = _seeds(seeds)
+    ns = len(s)
+    handles = (_vp * ns)(*[m.handle for m in models])
+    ooi = np.zeros(ns)
+    ubar = np.zeros(ns)
+    _check(_L.mfmc_solve_batch_mixed(ctypes.addressof(handles),
+                                     ctypes.addressof(params) if params is not None else None,
+                                     s.ctypes.data, ns, ooi.ctypes.data, ubar.ctypes.data))
     return ooi, ubar
 
 

@@ -1,0 +1,117 @@
+"""The one-launch-per-step hierarchy solve (mfmc_solve_batch_mixed) against the FP64 oracle
+and against the per-model solves.
+
+Tolerances as in the single-fidelity parity tests: a k-step solve agrees with the oracle to
+|f_gpu - f_orc| <= 1e-5 f_orc.  Against the per-model TMA solve the fields are the same
+FP32 values (each output is formed by the same sequence of operations whatever the tile
+shape), so the OoI differs only by the FP64 summation order of the tile partials.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+COMMON = dict(eps=0.03, eps_lo=0.024, eps_hi=0.036, tau=5e-3, ic=2, ic_amp=0.05)
+# (n, R): every R the mixed kernel serves, ragged tiles at 96 (64 x 64 tiles) and 160
+# (128 x 64 tiles for R = 16), a field smaller than one R = 8 tile (64 x 128) at 64.
+HIERARCHY = [(160, 16), (64, 8), (96, 4), (64, 2)]
+
+
+def models(mf, steps=40, algo=None):
+    out = []
+    for n, R in HIERARCHY:
+        g = mf.Model(n=n, delta=R / n, nsteps=steps, algo=algo if algo is not None else mf.ALGO_AUTO, **COMMON)
+        out.append(g)
+    return out
+
+
+def oracle_model(n, R, steps):
+    return O.OracleModel(n=n, delta=R / n, nsteps=steps, **COMMON)
+
+
+def test_mixed_batch_matches_oracle(gpu_lib):
+    mf = gpu_lib
+    gs = models(mf)
+    pick = [0, 1, 2, 3, 3, 2, 1, 0, 2, 3]
+    seeds = np.arange(len(pick), dtype=np.uint64) + 777
+    f, ubar = mf.mfmc_solve_batch_mixed([gs[k] for k in pick], seeds)
+    for i, k in enumerate(pick):
+        n, R = HIERARCHY[k]
+        fr, mean, _, _ = oracle_model(n, R, 40).solve_sample(int(seeds[i]))
+        assert abs(f[i] - fr) <= 1e-5 * fr, (i, n, R, f[i], fr)
+        assert abs(ubar[i] - mean) <= 2e-5 * fr
+
+
+def test_mixed_batch_matches_per_model_tma(gpu_lib):
+    mf = gpu_lib
+    gs = models(mf, steps=30)
+    ref = models(mf, steps=30, algo=mf.ALGO_PREFIX_TMA)
+    pick = [k for k in range(4) for _ in range(5)]
+    seeds = np.arange(len(pick), dtype=np.uint64) + 4242
+    f, ubar = mf.mfmc_solve_batch_mixed([gs[k] for k in pick], seeds)
+    fr, ur = mf.mfmc_solve_batch([ref[k] for k in pick], seeds)
+    np.testing.assert_allclose(f, fr, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(ubar, ur, rtol=0, atol=2e-13)
+
+
+def test_mixed_per_sample_steps(gpu_lib):
+    mf = gpu_lib
+    gs = models(mf, steps=12)
+    pick = [0, 1, 2, 3, 0, 3]
+    steps = [12, 3, 1, 7, 5, 12]
+    seeds = np.arange(len(pick), dtype=np.uint64) + 99
+    p = mf.make_params(len(pick), nsteps=steps)
+    f, _ = mf.mfmc_solve_batch_mixed([gs[k] for k in pick], seeds, params=p)
+    for i, k in enumerate(pick):
+        n, R = HIERARCHY[k]
+        fr, _, _, _ = oracle_model(n, R, steps[i]).solve_sample(int(seeds[i]))
+        assert abs(f[i] - fr) <= 1e-5 * fr, (i, steps[i])
+
+
+def test_mixed_graph_replay_and_repeat(gpu_lib):
+    # the second call of a shape replays the captured step loop with new inputs
+    mf = gpu_lib
+    gs = models(mf, steps=20)
+    pick = [3, 2, 1, 0]
+    s1 = np.arange(4, dtype=np.uint64) + 1
+    s2 = np.arange(4, dtype=np.uint64) + 1001
+    a1, _ = mf.mfmc_solve_batch_mixed([gs[k] for k in pick], s1)
+    a2, _ = mf.mfmc_solve_batch_mixed([gs[k] for k in pick], s2)
+    b1, _ = mf.mfmc_solve_batch_mixed([gs[k] for k in pick], s1)
+    assert np.array_equal(a1, b1)
+    assert not np.array_equal(a1, a2)
+    for i, k in enumerate(pick):
+        n, R = HIERARCHY[k]
+        fr, _, _, _ = oracle_model(n, R, 20).solve_sample(int(s2[i]))
+        assert abs(a2[i] - fr) <= 1e-5 * fr
+
+
+def test_mixed_single_model_single_sample(gpu_lib):
+    mf = gpu_lib
+    g = mf.Model(n=64, delta=4 / 64, nsteps=5, **COMMON)
+    f, _ = mf.mfmc_solve_batch_mixed([g], [31337])
+    fr, _, _, _ = oracle_model(64, 4, 5).solve_sample(31337)
+    assert abs(f[0] - fr) <= 1e-5 * fr
+
+
+def test_mixed_rejects_unsupported(gpu_lib):
+    mf = gpu_lib
+    gs = models(mf, steps=4)
+    extra = mf.Model(n=128, delta=8 / 128, nsteps=4, **COMMON)
+    with pytest.raises(mf.MfmcError):   # five distinct models
+        mf.mfmc_solve_batch_mixed(gs + [extra], np.arange(5, dtype=np.uint64))
+    r3 = mf.Model(n=64, delta=3 / 64, nsteps=4, **COMMON)
+    with pytest.raises(mf.MfmcError):   # R outside {2, 4, 8, 16}
+        mf.mfmc_solve_batch_mixed([r3], [1])
+    gauss = mf.Model(n=64, delta=8 / 64, kernel=1, delta_hf=0.25, nsteps=4, **COMMON)
+    with pytest.raises(mf.MfmcError):   # Gaussian kernel
+        mf.mfmc_solve_batch_mixed([gauss], [1])
+    zero = mf.Model(n=64, delta=4 / 64, nsteps=0, **COMMON)
+    with pytest.raises(mf.MfmcError):   # no step to take
+        mf.mfmc_solve_batch_mixed([zero], [1])
+    # the library stays usable after the rejections
+    f, _ = mf.mfmc_solve_batch_mixed([gs[3]], [5])
+    fr, _, _, _ = oracle_model(64, 2, 4).solve_sample(5)
+    assert abs(f[0] - fr) <= 1e-5 * fr
