@@ -553,13 +553,70 @@ def run_large(args):
     return 0
 
 
+def run_mixed(args):
+    """One MFMC replicate's samples of the delta = 1/32 hierarchy (512^2/R16, 256^2/R8,
+    128^2/R4, 64^2/R2, 1000 steps, nuclei IC), solved three ways: one mfmc_solve_batch
+    call per model in turn; one mfmc_solve_batch call over all samples (per-model streams);
+    one mfmc_solve_batch_mixed call (one launch per time step over every model's tiles).
+    Allocations: the MFMC plans measured at B = 100 C_1 and 300 C_1, and a small allocation
+    in which no level fills the GPU alone.  Wall time of the synchronous calls, best of 3
+    after a warm-up call (autotuning, graph capture)."""
+    import numpy as np
+    from paper_2310_10750_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2310_10750_gb300 import mfmc
+    base = 20231016 + 1000003 * 4
+    levels = [(512, 16), (256, 8), (128, 4), (64, 2)]
+    common = dict(eps=0.02, eps_lo=0.016, eps_hi=0.024, tau=1e-3, nsteps=1000, ic=mfmc.IC_NUCLEI)
+    models = [mfmc.Model(n=n, delta=R / n, **common) for n, R in levels]
+    allocations = {"plan B=100 C_1": [1, 3, 91, 47259], "plan B=300 C_1": [4, 11, 273, 141778],
+                   "small levels": [2, 8, 32, 128]}
+
+    def timed(fn):
+        fn()
+        best, out = 1e30, None
+        for _ in range(3):
+            t = time.perf_counter()
+            out = fn()
+            best = min(best, time.perf_counter() - t)
+        return best, out
+
+    rows = []
+    for name, m in allocations.items():
+        seeds = [_seeds(base, k, 10 ** 7 * j) for j, k in enumerate(m)]
+        flat_models = [models[j] for j, k in enumerate(m) for _ in range(k)]
+        flat_seeds = np.concatenate(seeds)
+
+        def per_model():
+            return np.concatenate([mfmc.mfmc_solve_batch([models[j]] * k, seeds[j])[0] for j, k in enumerate(m)])
+
+        t_seq, f_seq = timed(per_model)
+        t_batch, (f_batch, _) = timed(lambda: mfmc.mfmc_solve_batch(flat_models, flat_seeds))
+        t_mixed, (f_mixed, _) = timed(lambda: mfmc.mfmc_solve_batch_mixed(flat_models, flat_seeds))
+        pts = sum(k * n * n for k, (n, _) in zip(m, levels)) * 1000
+        rows.append({"allocation": name, "m": m, "grid_pt_updates": pts,
+                     "per_model_calls_s": t_seq, "one_batch_call_s": t_batch, "mixed_one_launch_per_step_s": t_mixed,
+                     "mixed_speedup_vs_batch_call": t_batch / t_mixed,
+                     "max_rel_ooi_diff_mixed_vs_batch": float(np.max(np.abs(f_mixed - f_batch) / f_batch)),
+                     "max_rel_ooi_diff_batch_vs_per_model": float(np.max(np.abs(f_batch - f_seq) / f_seq))})
+    algos = {1: "direct", 2: "prefix", 4: "resident", 6: "prefix-tma", 7: "row-stream"}
+    line = {"metric": "hierarchy replicate wall time", "value": rows[2]["mixed_one_launch_per_step_s"], "unit": "s",
+            "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": "MFMC replicate of the delta=1/32 hierarchy (512^2/R16, 256^2/R8, 128^2/R4, "
+                                   "64^2/R2), 1000 steps, nuclei IC; value = small-levels allocation, mixed call",
+                       "per_model_algos": [algos.get(g.info().algo, str(g.info().algo)) for g in models]},
+            "allocations": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="single", choices=["single", "hierarchy", "serving", "large"],
+    ap.add_argument("--workload", default="single", choices=["single", "hierarchy", "serving", "large", "mixed"],
                     help="single (the headline, default), or one of the other measured configurations")
     ap.add_argument("--validation", type=int, default=2048, help="hierarchy: HF samples of the validation mean")
     ap.add_argument("--requests", type=int, default=20000, help="serving: requests in the stream")
@@ -582,6 +639,8 @@ def main():
         return run_serving(args)
     if args.workload == "large":
         return run_large(args)
+    if args.workload == "mixed":
+        return run_mixed(args)
     return run_ours(args)
 
 

@@ -217,15 +217,20 @@ mfmc_status mfmc_solve_batch(mfmc_model *const *models, const mfmc_sample_params
                              double *ubar_out);
 
 /* The same batch call for a model hierarchy (Section 3: samples of f_1 ... f_K at
- * shared parameters), with every model's samples advanced by ONE kernel launch per time
- * step: the (model, sample, tile) items of all models form one work queue, fine model
- * first, that persistent CTAs drain through an atomic ticket counter.  Same arguments and
- * results as mfmc_solve_batch, and bit-identical OoI to the TMA prefix kernel's per-model
- * solve of the same samples.  Limits: at most 4 distinct models, each with the constant
- * kernel and R = delta/h in {2, 4, 8, 16}; every sample runs >= 1 step.  Other inputs
- * return MFMC_EINVAL.  The step loop is captured in a CUDA graph on the first call of a
- * shape and replayed by later calls of the same shape.  Calls are serialised by a lock;
- * the library keeps the batch buffers until exit.  Synchronous. */
+ * shared parameters), with the samples of every model that streams through HBM advanced by
+ * ONE kernel launch per time step: the (model, sample, tile) items of those models form one
+ * work queue, fine model first, that persistent CTAs drain through an atomic ticket
+ * counter.  Models whose whole field fits in shared memory (the resident kernel, n <= 128)
+ * instead run all their steps in one resident launch each, on a second stream concurrent
+ * with the step launches.  Same arguments and results as mfmc_solve_batch; the fields of the
+ * queued models are bit-identical to those of the TMA prefix kernel with 4 columns per
+ * thread, their OoI differs from that solve's only by the FP64 summation order of the tile
+ * partials, and resident models give the resident kernel's results.  Limits: at most 4
+ * distinct models, each with the constant kernel and R = delta/h in {2, 4, 8, 16}; every
+ * sample runs >= 1 step.  Other inputs return MFMC_EINVAL.  The step loop is captured in a
+ * CUDA graph on the first call of a shape and replayed by later calls of the same shape.
+ * Calls are serialised by a lock; the library keeps the batch buffers until exit.
+ * Synchronous. */
 mfmc_status mfmc_solve_batch_mixed(mfmc_model *const *models, const mfmc_sample_params *params,
                                    const uint64_t *seeds, size_t ns, double *ooi_out,
                                    double *ubar_out);

@@ -7,6 +7,10 @@
 // one TMA box (tile + halo) of that model's ghost-framed field, then the same register-tiled
 // prefix-sum computation and fused update as the single-fidelity TMA kernel.  The step loop
 // of a batch is captured in a CUDA graph and replayed for repeated batches of the same shape.
+// Models whose whole field fits in shared memory (the resident kernel: n <= 128) do not go
+// through the queue: each runs all its steps in one resident launch on a second stream,
+// concurrently with the step launches, since streaming their tiles through HBM every step
+// would cost more than keeping them on chip.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -144,6 +148,7 @@ static bool mix_geom(int R, MixGeom *g) {
 struct MixGroupBufs {
     size_t cap = 0;
     int n = 0, R = 0;
+    bool padded = false;  // ghost-framed buffers and tile partials allocated (step-queue groups)
     float *u0 = nullptr;
     StepCoef *coef = nullptr;
     double *eps = nullptr, *out = nullptr, *theta = nullptr;
@@ -155,6 +160,8 @@ struct MixGroupBufs {
 struct MixWorkspace {
     std::mutex mu;
     cudaStream_t st = nullptr;
+    cudaStream_t st_res = nullptr;   // resident-kernel groups, concurrent with the step launches
+    cudaEvent_t ev_init = nullptr, ev_res = nullptr;
     MixGroupBufs g[kMixGroups];
     int *counters = nullptr;
     size_t counters_cap = 0;
@@ -169,10 +176,11 @@ static MixWorkspace &mix_ws() {
     return *w;
 }
 
-static mfmc_status ensure_group(MixGroupBufs &b, const Model &m, size_t k, cudaStream_t st, uint64_t *generation) {
+static mfmc_status ensure_group(MixGroupBufs &b, const Model &m, size_t k, bool padded, cudaStream_t st,
+                                uint64_t *generation) {
     MixGeom geo;
     mix_geom(m.R, &geo);
-    if (b.cap >= k && b.n == m.d.n && b.R == m.R) return MFMC_OK;
+    if (b.cap >= k && b.n == m.d.n && b.R == m.R && (b.padded || !padded)) return MFMC_OK;
     ++*generation;
     MFMC_CUDA(cudaStreamSynchronize(st));
     for (void *p : {(void *)b.u0, (void *)b.coef, (void *)b.eps, (void *)b.out, (void *)b.theta, (void *)b.seeds,
@@ -189,12 +197,14 @@ static mfmc_status ensure_group(MixGroupBufs &b, const Model &m, size_t k, cudaS
     MFMC_CUDA(cudaMalloc((void **)&b.theta, 12 * k * sizeof(double)));
     MFMC_CUDA(cudaMalloc((void **)&b.seeds, k * sizeof(uint64_t)));
     MFMC_CUDA(cudaMalloc((void **)&b.steps, k * sizeof(int)));
-    MFMC_CUDA(cudaMalloc((void **)&b.tb.padA, k * (size_t)P * P * sizeof(float)));
-    MFMC_CUDA(cudaMalloc((void **)&b.tb.padB, k * (size_t)P * P * sizeof(float)));
-    MFMC_CUDA(cudaMalloc((void **)&b.tb.partials, k * (size_t)tiles * sizeof(double)));
     b.cap = k;
     b.n = m.d.n;
     b.R = m.R;
+    if (!padded) return MFMC_OK;
+    MFMC_CUDA(cudaMalloc((void **)&b.tb.padA, k * (size_t)P * P * sizeof(float)));
+    MFMC_CUDA(cudaMalloc((void **)&b.tb.padB, k * (size_t)P * P * sizeof(float)));
+    MFMC_CUDA(cudaMalloc((void **)&b.tb.partials, k * (size_t)tiles * sizeof(double)));
+    b.padded = true;
     mfmc_status s = encode_map(&b.tb.mapA, b.tb.padA, P, k, geo.sw, geo.sh);
     if (s == MFMC_OK) s = encode_map(&b.tb.mapB, b.tb.padB, P, k, geo.sw, geo.sh);
     return s;
@@ -227,24 +237,38 @@ extern "C" mfmc_status mfmc_solve_batch_mixed(mfmc_model *const *models, const m
     });
     MixWorkspace &W = mix_ws();
     std::lock_guard<std::mutex> lk(W.mu);
-    if (!W.st) MFMC_CUDA(cudaStreamCreateWithFlags(&W.st, cudaStreamNonBlocking));
+    if (!W.st) {
+        MFMC_CUDA(cudaStreamCreateWithFlags(&W.st, cudaStreamNonBlocking));
+        MFMC_CUDA(cudaStreamCreateWithFlags(&W.st_res, cudaStreamNonBlocking));
+        MFMC_CUDA(cudaEventCreateWithFlags(&W.ev_init, cudaEventDisableTiming));
+        MFMC_CUDA(cudaEventCreateWithFlags(&W.ev_res, cudaEventDisableTiming));
+    }
     cudaStream_t st = W.st;
     const int ng = (int)order.size();
-    int max_steps = 0;
+    // Models whose whole field fits the shared-memory resident kernel run all their steps
+    // there, on a second stream; the others form the step queue of the mixed launches.
+    std::vector<char> resident(ng);
+    std::vector<int> queue;  // group indices in the step queue, heaviest first
+    int max_steps = 0;       // of the queue groups
+    std::vector<int> group_steps(ng, 0);
     std::vector<std::vector<int>> steps(ng);
     for (int g = 0; g < ng; ++g) {
         mfmc_model *m = order[g];
         const auto &idx = groups[m];
-        mfmc_status s = ensure_group(W.g[g], *m, idx.size(), st, &W.generation);
+        resident[g] = algo_supported(*m, MFMC_ALGO_RESIDENT) ? 1 : 0;
+        if (!resident[g]) queue.push_back(g);
+        mfmc_status s = ensure_group(W.g[g], *m, idx.size(), !resident[g], st, &W.generation);
         if (s != MFMC_OK) return s;
         steps[g].resize(idx.size());
         for (size_t q = 0; q < idx.size(); ++q) {
             const mfmc_sample_params *p = params ? &params[idx[q]] : nullptr;
             steps[g][q] = (p && p->nsteps > 0) ? p->nsteps : m->d.nsteps;
             if (steps[g][q] < 1) return fail(MFMC_EINVAL, "the mixed batch needs at least one step per sample");
-            max_steps = std::max(max_steps, steps[g][q]);
+            group_steps[g] = std::max(group_steps[g], steps[g][q]);
         }
+        if (!resident[g]) max_steps = std::max(max_steps, group_steps[g]);
     }
+    const int nq = (int)queue.size();
     if ((size_t)max_steps > W.counters_cap) {
         MFMC_CUDA(cudaStreamSynchronize(st));
         ++W.generation;
@@ -277,84 +301,106 @@ extern "C" mfmc_status mfmc_solve_batch_mixed(mfmc_model *const *models, const m
         MFMC_CUDA(cudaMemcpyAsync(b.steps, steps[g].data(), k * sizeof(int), cudaMemcpyHostToDevice, st));
         mfmc_status s = launch_init_fields(*m, b.seeds, b.theta, k, b.u0, st);
         if (s == MFMC_OK) s = launch_coefficients(*m, b.eps, k, b.coef, st);
-        if (s == MFMC_OK) s = launch_pad(b.u0, b.tb.padB, m->d.n, (m->R + 3) & ~3, k, st);
+        if (s == MFMC_OK && !resident[g]) s = launch_pad(b.u0, b.tb.padB, m->d.n, (m->R + 3) & ~3, k, st);
         if (s != MFMC_OK) return s;
     }
-    // the step loop: one mixed launch per step, captured once per shape and replayed
-    std::vector<uintptr_t> key{(uintptr_t)max_steps, (uintptr_t)ng, (uintptr_t)W.generation};
-    for (int g = 0; g < ng; ++g) {
-        key.push_back((uintptr_t)order[g]);
-        key.push_back(groups[order[g]].size());
-        key.push_back((uintptr_t)W.g[g].tb.padA);
-    }
-    key.push_back((uintptr_t)W.counters);
-    if (!(W.gexec && W.gkey == key)) {
-        if (W.gexec) cudaGraphExecDestroy(W.gexec);
-        W.gexec = nullptr;
-        static bool attr = false;
-        if (!attr) {
-            MFMC_CUDA(cudaFuncSetAttribute(mixed_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMixSmem));
-            attr = true;
-        }
-        int dev = 0, sms = 0, per = 0;
-        MFMC_CUDA(cudaGetDevice(&dev));
-        MFMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        MFMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mixed_step_kernel, 256, kMixSmem));
-        MixedArgs a;
-        MixedMaps mp;
-        int total = 0;
+    // resident groups: one launch each on the second stream, after the inputs are built
+    const bool any_resident = nq < ng;
+    if (any_resident) {
+        MFMC_CUDA(cudaEventRecord(W.ev_init, st));
+        MFMC_CUDA(cudaStreamWaitEvent(W.st_res, W.ev_init, 0));
         for (int g = 0; g < ng; ++g) {
-            MixGeom geo;
-            mix_geom(order[g]->R, &geo);
-            const int n = order[g]->d.n;
-            TmaArgs &t = a.g[g];
-            t.dst_plain = nullptr;
-            t.coef = W.g[g].coef;
-            t.partials = W.g[g].tb.partials;
-            t.status = W.status;
-            t.steps_ps = W.g[g].steps;
-            t.n = n;
-            t.P = n + 2 * ((order[g]->R + 3) & ~3);
-            t.tiles_x = (n + geo.tx - 1) / geo.tx;
-            t.tiles = t.tiles_x * ((n + geo.ty - 1) / geo.ty);
-            t.total = (int)groups[order[g]].size() * t.tiles;
-            t.last = 0;
-            a.R[g] = order[g]->R;
-            a.begin[g] = total;
-            total += t.total;
-        }
-        a.begin[ng] = total;
-        a.ngroups = ng;
-        a.total = total;
-        a.status = W.status;
-        const int grid = std::max(1, std::min(total, sms * std::max(1, per)));
-        cudaGraph_t graph = nullptr;
-        MFMC_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
-        cudaError_t e = cudaMemsetAsync(W.counters, 0, max_steps * sizeof(int), st);
-        for (int k = 1; k <= max_steps && e == cudaSuccess; ++k) {
-            for (int g = 0; g < ng; ++g) {
-                a.g[g].step = k;
-                a.g[g].dst = (k & 1) ? W.g[g].tb.padA : W.g[g].tb.padB;
-                mp.m[g] = (k & 1) ? W.g[g].tb.mapB : W.g[g].tb.mapA;
-            }
-            a.counter = W.counters + (k - 1);
-            mixed_step_kernel<<<grid, 256, kMixSmem, st>>>(mp, a);
-            e = cudaGetLastError();
-        }
-        for (int g = 0; g < ng && e == cudaSuccess; ++g) {
+            if (!resident[g]) continue;
+            MixGroupBufs &b = W.g[g];
             const size_t k = groups[order[g]].size();
-            if (launch_finalize(W.g[g].tb.partials, a.g[g].tiles, k, order[g]->d.n, W.g[g].out + k, W.g[g].out, st) !=
-                MFMC_OK)
-                e = cudaErrorUnknown;
+            mfmc_status s = run_resident_steps(*order[g], b.coef, b.u0, k, group_steps[g], b.steps, nullptr, b.out + k,
+                                               b.out, W.st_res);
+            if (s != MFMC_OK) return s;
         }
-        cudaError_t e2 = cudaStreamEndCapture(st, &graph);
-        if (e == cudaSuccess) e = e2;
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&W.gexec, graph, 0);
-        if (graph) cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return cuda_fail(e, "mixed step graph");
-        W.gkey = key;
+        MFMC_CUDA(cudaEventRecord(W.ev_res, W.st_res));
     }
-    MFMC_CUDA(cudaGraphLaunch(W.gexec, st));
+    // the step queue: one mixed launch per step, captured once per shape and replayed
+    if (nq > 0) {
+        std::vector<uintptr_t> key{(uintptr_t)max_steps, (uintptr_t)nq, (uintptr_t)W.generation};
+        for (int g : queue) {
+            key.push_back((uintptr_t)order[g]);
+            key.push_back(groups[order[g]].size());
+            key.push_back((uintptr_t)W.g[g].tb.padA);
+        }
+        key.push_back((uintptr_t)W.counters);
+        if (!(W.gexec && W.gkey == key)) {
+            if (W.gexec) cudaGraphExecDestroy(W.gexec);
+            W.gexec = nullptr;
+            static bool attr = false;
+            if (!attr) {
+                MFMC_CUDA(cudaFuncSetAttribute(mixed_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)kMixSmem));
+                attr = true;
+            }
+            int dev = 0, sms = 0, per = 0;
+            MFMC_CUDA(cudaGetDevice(&dev));
+            MFMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            MFMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mixed_step_kernel, 256, kMixSmem));
+            MixedArgs a;
+            MixedMaps mp;
+            int total = 0;
+            for (int qi = 0; qi < nq; ++qi) {
+                const int g = queue[qi];
+                MixGeom geo;
+                mix_geom(order[g]->R, &geo);
+                const int n = order[g]->d.n;
+                TmaArgs &t = a.g[qi];
+                t.dst_plain = nullptr;
+                t.coef = W.g[g].coef;
+                t.partials = W.g[g].tb.partials;
+                t.status = W.status;
+                t.steps_ps = W.g[g].steps;
+                t.n = n;
+                t.P = n + 2 * ((order[g]->R + 3) & ~3);
+                t.tiles_x = (n + geo.tx - 1) / geo.tx;
+                t.tiles = t.tiles_x * ((n + geo.ty - 1) / geo.ty);
+                t.total = (int)groups[order[g]].size() * t.tiles;
+                t.last = 0;
+                a.R[qi] = order[g]->R;
+                a.begin[qi] = total;
+                total += t.total;
+            }
+            a.begin[nq] = total;
+            a.ngroups = nq;
+            a.total = total;
+            a.status = W.status;
+            const int grid = std::max(1, std::min(total, sms * std::max(1, per)));
+            cudaGraph_t graph = nullptr;
+            MFMC_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+            cudaError_t e = cudaMemsetAsync(W.counters, 0, max_steps * sizeof(int), st);
+            for (int k = 1; k <= max_steps && e == cudaSuccess; ++k) {
+                for (int qi = 0; qi < nq; ++qi) {
+                    const int g = queue[qi];
+                    a.g[qi].step = k;
+                    a.g[qi].dst = (k & 1) ? W.g[g].tb.padA : W.g[g].tb.padB;
+                    mp.m[qi] = (k & 1) ? W.g[g].tb.mapB : W.g[g].tb.mapA;
+                }
+                a.counter = W.counters + (k - 1);
+                mixed_step_kernel<<<grid, 256, kMixSmem, st>>>(mp, a);
+                e = cudaGetLastError();
+            }
+            for (int qi = 0; qi < nq && e == cudaSuccess; ++qi) {
+                const int g = queue[qi];
+                const size_t k = groups[order[g]].size();
+                if (launch_finalize(W.g[g].tb.partials, a.g[qi].tiles, k, order[g]->d.n, W.g[g].out + k, W.g[g].out,
+                                    st) != MFMC_OK)
+                    e = cudaErrorUnknown;
+            }
+            cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+            if (e == cudaSuccess) e = e2;
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&W.gexec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(e, "mixed step graph");
+            W.gkey = key;
+        }
+        MFMC_CUDA(cudaGraphLaunch(W.gexec, st));
+    }
+    if (any_resident) MFMC_CUDA(cudaStreamWaitEvent(st, W.ev_res, 0));
     std::vector<std::vector<double>> host(ng);
     for (int g = 0; g < ng; ++g) {
         host[g].resize(2 * groups[order[g]].size());

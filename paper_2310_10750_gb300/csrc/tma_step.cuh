@@ -85,6 +85,12 @@ struct TmaCfg {
 
 constexpr long long kWaitLimit = 1ll << 24;
 
+// Store one float4 at padded (row, col) of a field with row pitch P when both are >= 0
+// (a ghost image that exists).
+__device__ __forceinline__ void put_ghost(float *d, int P, int row, int col, float4 val) {
+    if (row >= 0 && col >= 0) *reinterpret_cast<float4 *>(d + (size_t)row * P + col) = val;
+}
+
 // One tile item: disc sums from the staged tile `s` (tile + halo, row pitch SW), the
 // update and projection, stores of the outputs (and ghost images), and the FP64 partial
 // of the OoI when `last`.  Shared by the single-fidelity and the mixed-fidelity kernels.
@@ -96,6 +102,7 @@ __device__ __forceinline__ void tma_tile_compute(const float *s, const TmaArgs &
     const int tid = threadIdx.x;
     const int tx = tid % TXT, ty = tid / TXT, ox = tx * RX, oy = ty * RY;
     const int n = a.n, G = R4;
+    const StepCoef cf = a.coef[sample];  // issued before the row loop, which hides its latency
     float acc[RY][RX];
     float cmp[ALGO == 2 ? RY : 1][RX];
 #pragma unroll
@@ -142,9 +149,10 @@ __device__ __forceinline__ void tma_tile_compute(const float *s, const TmaArgs &
         }
     }
 
-    const StepCoef cf = a.coef[sample];
     double part = 0.0;
     const size_t nn = (size_t)n * n, PP = (size_t)a.P * a.P;
+    // whether this thread's block has ghost images (touches the frame); uniform per thread
+    const bool framed = x0 + ox < G || x0 + ox + RX > n - G || y0 + oy < G || y0 + oy + RY > n - G;
 #pragma unroll
     for (int j = 0; j < RY; ++j) {
         const float4 c4v = *reinterpret_cast<const float4 *>(s + (oy + j + R) * SW + ox + R4);
@@ -163,16 +171,19 @@ __device__ __forceinline__ void tma_tile_compute(const float *s, const TmaArgs &
                 *reinterpret_cast<float4 *>(a.dst_plain + sample * nn + (size_t)y * n + x) = val;
             } else if (a.dst) {
                 float *d = a.dst + sample * PP;
-                const int rows[3] = {G + y, y < G ? G + y + n : -1, y >= n - G ? G + y - n : -1};
-                const int cols[3] = {G + x, x < G ? G + x + n : -1, x >= n - G ? G + x - n : -1};
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    if (rows[q] < 0) continue;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        if (cols[c] < 0) continue;
-                        *reinterpret_cast<float4 *>(d + (size_t)rows[q] * a.P + cols[c]) = val;
-                    }
+                *reinterpret_cast<float4 *>(d + (size_t)(G + y) * a.P + G + x) = val;
+                if (framed) {
+                    // ghost images at rows G + y +- n and columns G + x +- n inside the frame
+                    const int ra = y < G ? G + y + n : -1, rb = y >= n - G ? G + y - n : -1;
+                    const int ca = x < G ? G + x + n : -1, cb = x >= n - G ? G + x - n : -1;
+                    put_ghost(d, a.P, G + y, ca, val);
+                    put_ghost(d, a.P, G + y, cb, val);
+                    put_ghost(d, a.P, ra, G + x, val);
+                    put_ghost(d, a.P, ra, ca, val);
+                    put_ghost(d, a.P, ra, cb, val);
+                    put_ghost(d, a.P, rb, G + x, val);
+                    put_ghost(d, a.P, rb, ca, val);
+                    put_ghost(d, a.P, rb, cb, val);
                 }
             }
             if (last) part += ((double)o[0] + (double)o[1]) + ((double)o[2] + (double)o[3]);

@@ -2,9 +2,11 @@
 and against the per-model solves.
 
 Tolerances as in the single-fidelity parity tests: a k-step solve agrees with the oracle to
-|f_gpu - f_orc| <= 1e-5 f_orc.  Against the per-model TMA solve the fields are the same
-FP32 values (each output is formed by the same sequence of operations whatever the tile
-shape), so the OoI differs only by the FP64 summation order of the tile partials.
+|f_gpu - f_orc| <= 1e-5 f_orc.  Against the per-model solves with the same kernels (the TMA
+prefix kernel for the queued models, the resident kernel for models that fit in shared
+memory) the fields are the same FP32 values (each output is formed by the same sequence of
+operations whatever the tile shape), so the OoI differs only by the FP64 summation order of
+the tile partials.
 """
 import numpy as np
 import pytest
@@ -44,16 +46,49 @@ def test_mixed_batch_matches_oracle(gpu_lib):
         assert abs(ubar[i] - mean) <= 2e-5 * fr
 
 
-def test_mixed_batch_matches_per_model_tma(gpu_lib):
+def reference_models(mf, steps):
+    """Per-model solves with the algorithm the mixed call uses for that model: the resident
+    kernel where it fits, else the TMA prefix kernel (4 columns per thread)."""
+    out = []
+    for n, R in HIERARCHY:
+        try:
+            g = mf.Model(n=n, delta=R / n, nsteps=steps, algo=mf.ALGO_RESIDENT, **COMMON)
+        except mf.MfmcError:
+            g = mf.Model(n=n, delta=R / n, nsteps=steps, algo=mf.ALGO_PREFIX_TMA, **COMMON)
+        out.append(g)
+    return out
+
+
+def test_mixed_batch_matches_per_model_solves(gpu_lib):
     mf = gpu_lib
     gs = models(mf, steps=30)
-    ref = models(mf, steps=30, algo=mf.ALGO_PREFIX_TMA)
+    ref = reference_models(mf, 30)
+    kinds = {g.info().algo for g in ref}
+    assert mf.ALGO_PREFIX_TMA in kinds and mf.ALGO_RESIDENT in kinds
     pick = [k for k in range(4) for _ in range(5)]
     seeds = np.arange(len(pick), dtype=np.uint64) + 4242
     f, ubar = mf.mfmc_solve_batch_mixed([gs[k] for k in pick], seeds)
     fr, ur = mf.mfmc_solve_batch([ref[k] for k in pick], seeds)
     np.testing.assert_allclose(f, fr, rtol=0, atol=1e-13)
     np.testing.assert_allclose(ubar, ur, rtol=0, atol=2e-13)
+
+
+def test_mixed_queue_of_four_streamed_models(gpu_lib):
+    # four models too large for the resident kernel: all of them share the step queue
+    # (ragged tiles for every shape: 64 x 64, 64 x 128 and 128 x 64 tiles on n = 132..160)
+    mf = gpu_lib
+    shapes = [(160, 16), (136, 8), (132, 4), (140, 2)]
+    gs = [mf.Model(n=n, delta=R / n, nsteps=12, **COMMON) for n, R in shapes]
+    tma = [mf.Model(n=n, delta=R / n, nsteps=12, algo=mf.ALGO_PREFIX_TMA, **COMMON) for n, R in shapes]
+    pick = [3, 2, 1, 0, 0, 1, 2, 3, 1]
+    seeds = np.arange(len(pick), dtype=np.uint64) + 555
+    f, _ = mf.mfmc_solve_batch_mixed([gs[k] for k in pick], seeds)
+    fr, _ = mf.mfmc_solve_batch([tma[k] for k in pick], seeds)
+    np.testing.assert_allclose(f, fr, rtol=0, atol=1e-13)
+    for i in (0, 3, 5):
+        n, R = shapes[pick[i]]
+        fo, _, _, _ = oracle_model(n, R, 12).solve_sample(int(seeds[i]))
+        assert abs(f[i] - fo) <= 1e-5 * fo
 
 
 def test_mixed_per_sample_steps(gpu_lib):
