@@ -2,7 +2,7 @@
 
 A plain, slow FP64 CPU reference of what the GPU library computes, written from the
 paper: ``nlch_oracle.c`` holds the model, its time step and the output of interest
-(Section 2 and Section 4, beta2 = 0); ``mfmc_oracle.py`` holds the multifidelity
+(Section 2 and Section 4, beta2 = 0; periodic lattice or a collar holding fixed data); ``mfmc_oracle.py`` holds the multifidelity
 Monte Carlo statistics, model selection, allocation and estimator (Section 3).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
@@ -75,6 +75,17 @@ def lib():
         L.orc_solve.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _ip, _ip, _dp, ctypes.c_int,
                                 ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                 ctypes.c_double]
+        for name in ("orc_convolve_collar", "orc_apply_L_collar"):
+            getattr(L, name).restype = None
+            getattr(L, name).argtypes = [ctypes.c_int, _dp, _ip, _ip, _dp, ctypes.c_int, ctypes.c_double, _dp]
+        L.orc_step_collar.restype = None
+        L.orc_step_collar.argtypes = [ctypes.c_int, _dp, _dp, _ip, _ip, _dp, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double]
+        L.orc_solve_collar.restype = ctypes.c_double
+        L.orc_solve_collar.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _ip, _ip, _dp, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double]
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_set_threads.restype = None
         L.orc_set_threads.argtypes = [ctypes.c_int]
@@ -136,6 +147,8 @@ class OracleModel:
     ic: int = 0                # 0 uniform, 1 smoothed Gaussian noise, 2 four nuclei
     ic_amp: float = 0.05
     ic_base_n: int = 0         # noise ICs: base lattice of the shared random field (0 = n)
+    bc: int = 0                # 0 periodic lattice, 1 collar Omega_I holding the fixed value bc_value
+    bc_value: float = -1.0
     _disc: Optional[tuple] = field(default=None, repr=False)
 
     @property
@@ -188,7 +201,10 @@ class OracleModel:
         w, _ = self.weights(eps)
         u = np.ascontiguousarray(u, dtype=np.float64)
         out = np.empty_like(u)
-        lib().orc_convolve(self.n, _d(u), _i(dx), _i(dy), _d(w), len(dx), _d(out))
+        if self.bc == 1:
+            lib().orc_convolve_collar(self.n, _d(u), _i(dx), _i(dy), _d(w), len(dx), self.bc_value, _d(out))
+        else:
+            lib().orc_convolve(self.n, _d(u), _i(dx), _i(dy), _d(w), len(dx), _d(out))
         return out
 
     def apply_L(self, u: np.ndarray, eps: float) -> np.ndarray:
@@ -196,7 +212,10 @@ class OracleModel:
         w, _ = self.weights(eps)
         u = np.ascontiguousarray(u, dtype=np.float64)
         out = np.empty_like(u)
-        lib().orc_apply_L(self.n, _d(u), _i(dx), _i(dy), _d(w), len(dx), _d(out))
+        if self.bc == 1:
+            lib().orc_apply_L_collar(self.n, _d(u), _i(dx), _i(dy), _d(w), len(dx), self.bc_value, _d(out))
+        else:
+            lib().orc_apply_L(self.n, _d(u), _i(dx), _i(dy), _d(w), len(dx), _d(out))
         return out
 
     def apply_L_open(self, u: np.ndarray, eps: float) -> np.ndarray:
@@ -224,8 +243,12 @@ class OracleModel:
         w, cg = self.weights(eps)
         u = np.ascontiguousarray(u, dtype=np.float64)
         out = np.empty_like(u)
-        lib().orc_step(self.n, _d(u), _d(out), _i(dx), _i(dy), _d(w), len(dx), cg, self.c_F,
-                       self.tau, self.beta1)
+        if self.bc == 1:
+            lib().orc_step_collar(self.n, _d(u), _d(out), _i(dx), _i(dy), _d(w), len(dx), cg, self.c_F,
+                                  self.tau, self.beta1, self.bc_value)
+        else:
+            lib().orc_step(self.n, _d(u), _d(out), _i(dx), _i(dy), _d(w), len(dx), cg, self.c_F,
+                           self.tau, self.beta1)
         return out
 
     def solve(self, u0: np.ndarray, eps: float, nsteps: Optional[int] = None):
@@ -234,8 +257,12 @@ class OracleModel:
         w, cg = self.weights(eps)
         u = np.ascontiguousarray(u0, dtype=np.float64).copy()
         k = self.nsteps if nsteps is None else nsteps
-        mean = lib().orc_solve(self.n, _d(u), k, _i(dx), _i(dy), _d(w), len(dx), cg, self.c_F,
-                               self.tau, self.beta1)
+        if self.bc == 1:
+            mean = lib().orc_solve_collar(self.n, _d(u), k, _i(dx), _i(dy), _d(w), len(dx), cg, self.c_F,
+                                          self.tau, self.beta1, self.bc_value)
+        else:
+            mean = lib().orc_solve(self.n, _d(u), k, _i(dx), _i(dy), _d(w), len(dx), cg, self.c_F,
+                                   self.tau, self.beta1)
         return u, mean
 
     def solve_sample(self, seed: int, eps_override: float = 0.0, theta=None,

@@ -180,6 +180,61 @@ void orc_step(int n, const double *u, double *unew, const int *dx, const int *dy
         }
 }
 
+/* ------------------------------------------------------------------------- */
+/* Volume-constrained boundary (Section 2: the operator integrates over        */
+/* Omega together with the interaction collar Omega_I of width delta around it; */
+/* the paper leaves the data on Omega_I open).  Reading: Omega is the n x n     */
+/* lattice without wrap-around, every lattice point outside it within the      */
+/* horizon belongs to the collar and holds the fixed value uI, and the scheme  */
+/* is unchanged otherwise.  c_gamma stays the full-disc sum, so L vanishes on  */
+/* u = uI everywhere.  The collar value of a point is read by orc_collar_at.   */
+/* ------------------------------------------------------------------------- */
+static inline double orc_collar_at(int n, const double *u, int y, int x, double uI) {
+    if (y < 0 || y >= n || x < 0 || x >= n) return uI;
+    return u[y * n + x];
+}
+
+/* (gamma * u)_i with the collar: direct sum over the disc. */
+void orc_convolve_collar(int n, const double *u, const int *dx, const int *dy, const double *w,
+                         int count, double uI, double *out) {
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < n; ++y)
+        for (int x = 0; x < n; ++x) {
+            double s = 0.0;
+            for (int k = 0; k < count; ++k) s += w[k] * orc_collar_at(n, u, y + dy[k], x + dx[k], uI);
+            out[y * n + x] = s;
+        }
+}
+
+/* (L u)_i = sum_z w_z (u_i - u_{i+z}) with the collar. */
+void orc_apply_L_collar(int n, const double *u, const int *dx, const int *dy, const double *w,
+                        int count, double uI, double *out) {
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < n; ++y)
+        for (int x = 0; x < n; ++x) {
+            double ui = u[y * n + x], s = 0.0;
+            for (int k = 0; k < count; ++k) s += w[k] * (ui - orc_collar_at(n, u, y + dy[k], x + dx[k], uI));
+            out[y * n + x] = s;
+        }
+}
+
+/* One time step (beta2 = 0) with the collar: as orc_step, the convolution reads uI
+ * outside Omega. */
+void orc_step_collar(int n, const double *u, double *unew, const int *dx, const int *dy,
+                     const double *w, int count, double cgam, double cF, double tau, double beta1,
+                     double uI) {
+    double denom = 1.0 + tau * beta1 * cgam;
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < n; ++y)
+        for (int x = 0; x < n; ++x) {
+            double conv = 0.0;
+            for (int k = 0; k < count; ++k) conv += w[k] * orc_collar_at(n, u, y + dy[k], x + dx[k], uI);
+            double ui = u[y * n + x];
+            double v = (ui + tau * beta1 * (conv + cF * ui)) / denom;
+            unew[y * n + x] = v > 1.0 ? 1.0 : (v < -1.0 ? -1.0 : v);
+        }
+}
+
 /* Spatial mean of u: the lumped-mass integral (h^2 sum_i u_i) divided by |Omega| = 1. */
 double orc_mean(int n, const double *u) {
     double s = 0.0;
@@ -318,6 +373,20 @@ double orc_solve(int n, double *u, int nsteps, const int *dx, const int *dy, con
     double *a = u, *b = (double *)malloc(sizeof(double) * N);
     for (int k = 0; k < nsteps; ++k) {
         orc_step(n, a, b, dx, dy, w, count, cgam, cF, tau, beta1);
+        double *t = a; a = b; b = t;
+    }
+    if (a != u) { memcpy(u, a, sizeof(double) * N); b = a; }
+    free(b);
+    return orc_mean(n, u);
+}
+
+/* Full solve of one sample with the collar (see orc_step_collar). */
+double orc_solve_collar(int n, double *u, int nsteps, const int *dx, const int *dy, const double *w,
+                        int count, double cgam, double cF, double tau, double beta1, double uI) {
+    long N = (long)n * n;
+    double *a = u, *b = (double *)malloc(sizeof(double) * N);
+    for (int k = 0; k < nsteps; ++k) {
+        orc_step_collar(n, a, b, dx, dy, w, count, cgam, cF, tau, beta1, uI);
         double *t = a; a = b; b = t;
     }
     if (a != u) { memcpy(u, a, sizeof(double) * N); b = a; }

@@ -248,3 +248,76 @@ def test_uniform_ic_and_rounding_to_fp32():
     m2 = model(eps_lo=0.024, eps_hi=0.036)
     e2 = m2.sample_eps(1)
     assert 0.024 <= e2 <= 0.036 and e2 == 0.024 + 0.012 * O.uniform(1, 0, 0)
+
+
+# --------------------------------------------------------------------------- collar boundary
+def _outside_counts(n, R):
+    """For every node of an n x n lattice: how many points of the radius-R lattice disc
+    around it lie outside the lattice (counted by brute force over the disc)."""
+    pts = [(dx, dy) for dy in range(-R, R + 1) for dx in range(-R, R + 1) if dx * dx + dy * dy <= R * R]
+    cnt = np.zeros((n, n), dtype=np.int64)
+    for y in range(n):
+        for x in range(n):
+            cnt[y, x] = sum(1 for dx, dy in pts if not (0 <= y + dy < n and 0 <= x + dx < n))
+    return cnt
+
+
+@pytest.mark.parametrize("R,uI", [(3, -1.0), (4, 0.25)])
+def test_collar_L_on_constant_interior_counts_collar_points(R, uI):
+    # u = c on Omega, uI on the collar: every disc point in the collar contributes
+    # A h^2 (c - uI) and every interior one nothing, with A = 8 eps^2 / (pi delta^4)
+    n, eps, c = 24, 0.03, 0.3
+    m = model(n=n, delta=R / n, bc=1, bc_value=uI)
+    A = 8 * eps ** 2 / (math.pi * (R / n) ** 4)
+    got = m.apply_L(np.full((n, n), c), eps)
+    want = A / n ** 2 * (c - uI) * _outside_counts(n, R)
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-14)
+    assert np.all(got[R:n - R, R:n - R] == 0.0)
+
+
+def test_collar_one_step_closed_form():
+    # one step from u = c on Omega: (c (1 + tau beta1 (c_gamma + c_F)) - tau beta1 A h^2
+    # (c - uI) count) / (1 + tau beta1 c_gamma), clipped; c_gamma = A h^2 |D|
+    n, R, eps, c, uI, tau = 20, 3, 0.05, 0.6, -1.0, 0.02
+    m = model(n=n, delta=R / n, eps=eps, tau=tau, bc=1, bc_value=uI)
+    Ah2 = 8 * eps ** 2 / (math.pi * (R / n) ** 4) / n ** 2
+    D = sum(1 for dy in range(-R, R + 1) for dx in range(-R, R + 1) if dx * dx + dy * dy <= R * R)
+    cg = Ah2 * D
+    v = (c * (1 + tau * (cg + 1.0)) - tau * Ah2 * (c - uI) * _outside_counts(n, R)) / (1 + tau * cg)
+    want = np.clip(v, -1.0, 1.0)
+    got = m.step(np.full((n, n), c), eps)
+    assert np.allclose(got, want, rtol=0, atol=1e-14)
+    assert got[n // 2, n // 2] == pytest.approx(c * (1 + tau * (cg + 1)) / (1 + tau * cg), abs=1e-15)
+
+
+def test_collar_agrees_with_periodic_away_from_the_edges():
+    n, R = 32, 4
+    rng = np.random.default_rng(3)
+    u = rng.uniform(-1, 1, (n, n))
+    per = model(n=n, delta=R / n).apply_L(u, 0.03)
+    col = model(n=n, delta=R / n, bc=1, bc_value=0.7).apply_L(u, 0.03)
+    assert np.array_equal(per[R:n - R, R:n - R], col[R:n - R, R:n - R])
+    assert not np.allclose(per[:R], col[:R])
+
+
+@pytest.mark.parametrize("uI", [-1.0, 0.0, 1.0])
+def test_collar_pure_phase_matching_the_collar_is_stationary(uI):
+    m = model(n=16, delta=3 / 16, tau=0.01, bc=1, bc_value=uI)
+    u = np.full((16, 16), uI)
+    for _ in range(3):
+        u = m.step(u, 0.03)
+    assert np.all(u == uI)
+
+
+def test_collar_keeps_reflection_symmetry_and_bounds():
+    # the collar is symmetric under x -> n-1-x, so a symmetric initial field stays symmetric
+    n, R = 24, 3
+    m = model(n=n, delta=R / n, tau=5e-3, bc=1, bc_value=-1.0, ic=2)
+    u0 = m.initial_field(11)
+    u0 = 0.5 * (u0 + u0[:, ::-1])
+    uT, _ = m.solve(u0, 0.03, nsteps=40)
+    assert np.abs(uT - uT[:, ::-1]).max() <= 1e-13
+    assert np.abs(uT).max() <= 1.0
+    # the -1 collar pulls the field down near the edges relative to the periodic solve
+    uP, _ = model(n=n, delta=R / n, tau=5e-3, ic=2).solve(u0, 0.03, nsteps=40)
+    assert uT.mean() < uP.mean()
