@@ -48,7 +48,14 @@ typedef enum { MFMC_KERNEL_CONSTANT = 0, MFMC_KERNEL_GAUSSIAN = 1 } mfmc_kernel;
 
 /* Boundary: the periodic unit torus (the interaction collar of Section 2 is not
  * modelled). */
-typedef enum { MFMC_BC_PERIODIC = 0 } mfmc_boundary;
+/* Boundary of the lattice Omega.  PERIODIC: the unit torus.  COLLAR: the volume-constrained
+ * form of Section 2 -- the operator of Eq. (nonl_operator) integrates over Omega together
+ * with the interaction collar Omega_I of width delta around it, and the collar holds the
+ * fixed value bc_value (the paper leaves the collar data open; a constant is this library's
+ * reading).  COLLAR runs on the TMA prefix kernels and the generic kernel (plain / direct
+ * forms); the resident, row-streaming and staged-tile kernels, the mixed-fidelity call and
+ * the allocation-free solve are periodic only. */
+typedef enum { MFMC_BC_PERIODIC = 0, MFMC_BC_COLLAR = 1 } mfmc_boundary;
 
 /* Initial field built on the device from a 64-bit seed (SplitMix64, one counter per
  * draw: draw i of stream k is output number k*2^32 + i + 1 of the sequence started at
@@ -101,6 +108,7 @@ typedef struct {
                               the b x b block of base-lattice IC values, so models
                               of different n share one random input per seed.     */
     mfmc_algo algo;
+    double bc_value;       /* COLLAR: the fixed value of u on the collar, in [-1, 1] */
 } mfmc_model_desc;
 
 /* Per-sample parameters (all optional).  eps <= 0 means "from the model" (the nominal

@@ -120,7 +120,9 @@ static mfmc_status validate_desc(const mfmc_model_desc &d, int *R_out) {
     if (d.nsteps < 0) return fail(MFMC_EINVAL, "nsteps must be >= 0");
     if (d.kernel != MFMC_KERNEL_CONSTANT && d.kernel != MFMC_KERNEL_GAUSSIAN) return fail(MFMC_EINVAL, "unknown kernel");
     if (d.kernel == MFMC_KERNEL_GAUSSIAN && !(d.delta_hf > 0)) return fail(MFMC_EINVAL, "delta_hf must be > 0");
-    if (d.bc != MFMC_BC_PERIODIC) return fail(MFMC_EINVAL, "unknown boundary");
+    if (d.bc != MFMC_BC_PERIODIC && d.bc != MFMC_BC_COLLAR) return fail(MFMC_EINVAL, "unknown boundary");
+    if (d.bc == MFMC_BC_COLLAR && !(d.bc_value >= -1.0 && d.bc_value <= 1.0))
+        return fail(MFMC_EINVAL, "the collar value must lie in [-1, 1]");
     if (d.ic != MFMC_IC_UNIFORM && d.ic != MFMC_IC_SMOOTHED_GAUSS && d.ic != MFMC_IC_NUCLEI) return fail(MFMC_EINVAL, "unknown ic");
     if (!(d.ic_amp >= 0)) return fail(MFMC_EINVAL, "ic_amp must be >= 0");
     if (d.ic_base_n < 0 || (d.ic_base_n > 0 && (d.ic_base_n % d.n != 0 || d.ic_base_n > 16384)))

@@ -225,8 +225,9 @@ extern "C" mfmc_status mfmc_solve_batch_mixed(mfmc_model *const *models, const m
         mfmc_model *m = models[i];
         if (!m) return fail(MFMC_EINVAL, "NULL model at sample %zu", i);
         MixGeom geo;
-        if (m->d.kernel != MFMC_KERNEL_CONSTANT || !mix_geom(m->R, &geo))
-            return fail(MFMC_EINVAL, "the one-launch mixed batch runs constant-kernel models with R in {2, 4, 8, 16}");
+        if (m->d.kernel != MFMC_KERNEL_CONSTANT || m->d.bc != MFMC_BC_PERIODIC || !mix_geom(m->R, &geo))
+            return fail(MFMC_EINVAL, "the one-launch mixed batch runs periodic constant-kernel models with R in "
+                                     "{2, 4, 8, 16}");
         if (!groups.count(m)) order.push_back(m);
         groups[m].push_back(i);
     }
@@ -361,6 +362,7 @@ extern "C" mfmc_status mfmc_solve_batch_mixed(mfmc_model *const *models, const m
                 t.tiles = t.tiles_x * ((n + geo.ty - 1) / geo.ty);
                 t.total = (int)groups[order[g]].size() * t.tiles;
                 t.last = 0;
+                t.periodic = 1;
                 a.R[qi] = order[g]->R;
                 a.begin[qi] = total;
                 total += t.total;

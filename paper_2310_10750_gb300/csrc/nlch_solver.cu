@@ -134,6 +134,8 @@ struct GenericArgs {
     double *partials;
     const float *wtab;  // NULL: unit weights
     int n, R, tiles_x, tiles, sample0, last;
+    int collar;         // 1: points outside the lattice read uI (volume constraint), 0: periodic
+    float uI;
 };
 
 constexpr int GEN_TX = 32, GEN_TY = 8, GEN_NT = GEN_TX * GEN_TY;
@@ -154,7 +156,12 @@ __global__ void __launch_bounds__(GEN_NT) step_generic_kernel(GenericArgs a) {
     const float *__restrict__ src = a.src + (size_t)sample * nn;
     for (int idx = threadIdx.x; idx < SH * SW4; idx += GEN_NT) {
         const int r = idx / SW4, c4 = idx - r * SW4;
-        const int gy = wrap_idx(y0 - R + r, n), gx = wrap_idx(x0 - R4 + 4 * c4, n);
+        const int py = y0 - R + r, px = x0 - R4 + 4 * c4;  // px, n: multiples of 4
+        if (a.collar && (py < 0 || py >= n || px < 0 || px >= n)) {
+            smem4[idx] = make_float4(a.uI, a.uI, a.uI, a.uI);
+            continue;
+        }
+        const int gy = wrap_idx(py, n), gx = wrap_idx(px, n);
         smem4[idx] = __ldg(reinterpret_cast<const float4 *>(src + (size_t)gy * n + gx));
     }
     if (threadIdx.x <= R) {
@@ -227,7 +234,7 @@ mfmc_status launch_pad(const float *u0, float *padded, int n, int G, size_t ns, 
     const size_t total = ns * (size_t)P * (P / 4);
     const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 32);
     if (total == 0) return MFMC_OK;
-    pad_fields_kernel<<<blocks, 256, 0, st>>>(u0, padded, n, G, ns);
+    pad_fields_kernel<<<blocks, 256, 0, st>>>(u0, padded, n, G, ns, 0, 0.f);
     MFMC_LAUNCHED("pad");
     return MFMC_OK;
 }
@@ -251,6 +258,16 @@ __global__ void reduce_fields_kernel(const float *u, int n, double *ubar, double
 
 bool algo_supported(const Model &m, int algo) {
     const bool constant = m.d.kernel == MFMC_KERNEL_CONSTANT;
+    if (m.d.bc == MFMC_BC_COLLAR) {
+        // the collar lives in the TMA kernels' ghost frame and in the generic kernel's loads
+        switch (algo) {
+            case MFMC_ALGO_PLAIN:
+            case MFMC_ALGO_DIRECT: return true;
+            case MFMC_ALGO_PREFIX_KAHAN:
+            case MFMC_ALGO_PREFIX_TMA: return constant && tma_launcher(m.R) != nullptr;
+            default: return false;
+        }
+    }
     switch (algo) {
         case MFMC_ALGO_PLAIN: return true;
         case MFMC_ALGO_DIRECT: return true;  // tile kernel (R <= 8) or the generic kernel
@@ -272,7 +289,7 @@ static int tiles_for(const Model &m, int algo, int *tiles_x) {
     int tx = GEN_TX, ty = GEN_TY;
     const TileLauncher *L = tile_launcher(m.R);
     const bool constant = m.d.kernel == MFMC_KERNEL_CONSTANT;
-    const bool tiled = constant && L &&
+    const bool tiled = constant && L && m.d.bc == MFMC_BC_PERIODIC &&
                        ((algo == MFMC_ALGO_DIRECT && L->fn[0]) || algo == MFMC_ALGO_PREFIX);
     if (tiled) {
         tx = L->tx;
@@ -303,7 +320,7 @@ static mfmc_status launch_generic(const Model &m, const GenericArgs &base, size_
 
 // ----------------------------------------------------------------------------- TMA path
 // Copy unpadded fields [ns][n][n] into padded scratch [ns][P][P] including the frame.
-__global__ void pad_fields_kernel(const float *u, float *dst, int n, int G, size_t ns) {
+__global__ void pad_fields_kernel(const float *u, float *dst, int n, int G, size_t ns, int collar, float uI) {
     const int P = n + 2 * G, P4 = P / 4;
     const size_t total = ns * (size_t)P * P4;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
@@ -311,8 +328,13 @@ __global__ void pad_fields_kernel(const float *u, float *dst, int n, int G, size
         const size_t smp = idx / ((size_t)P * P4);
         const int rem = (int)(idx - smp * (size_t)P * P4);
         const int py = rem / P4, px = (rem - (rem / P4) * P4) * 4;
-        const int y = wrap_idx(py - G, n), x = wrap_idx(px - G, n);
-        const float4 v = __ldg(reinterpret_cast<const float4 *>(u + smp * (size_t)n * n + (size_t)y * n + x));
+        float4 v;
+        if (collar && (py < G || py >= G + n || px < G || px >= G + n)) {  // px, G, n: multiples of 4
+            v = make_float4(uI, uI, uI, uI);
+        } else {
+            const int y = wrap_idx(py - G, n), x = wrap_idx(px - G, n);
+            v = __ldg(reinterpret_cast<const float4 *>(u + smp * (size_t)n * n + (size_t)y * n + x));
+        }
         *reinterpret_cast<float4 *>(dst + smp * (size_t)P * P + (size_t)py * P + px) = v;
     }
 }
@@ -425,7 +447,11 @@ mfmc_status run_solve_tma_core(const Model &m, int kahan, int variant, const Ste
     {
         const size_t total = ns * (size_t)P * (P / 4);
         const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 32);
-        pad_fields_kernel<<<blocks, 256, 0, st>>>(u0, b.padB, n, G, ns);
+        const int collar = m.d.bc == MFMC_BC_COLLAR;
+        pad_fields_kernel<<<blocks, 256, 0, st>>>(u0, b.padB, n, G, ns, collar, (float)m.d.bc_value);
+        // with a collar the steps store interior points only, so the frame of the other
+        // buffer must hold the collar too (its interior is overwritten by step 1)
+        if (collar) pad_fields_kernel<<<blocks, 256, 0, st>>>(u0, b.padA, n, G, ns, collar, (float)m.d.bc_value);
         MFMC_LAUNCHED("nlch_solver launch 4");
     }
     int dev = 0, sms = 0;
@@ -452,6 +478,7 @@ mfmc_status run_solve_tma_core(const Model &m, int kahan, int variant, const Ste
         a.tiles = tiles;
         a.total = (int)total;
         a.last = (last && !steps_ps) ? 1 : 0;
+        a.periodic = m.d.bc == MFMC_BC_PERIODIC;
         mfmc_status s = L->fn[kahan ? 2 : 1](*src, a, grid, st);
         if (s != MFMC_OK) return s;
         src = (dstbuf == b.padA) ? &b.mapA : &b.mapB;
@@ -532,7 +559,7 @@ mfmc_status run_solve_rows_core(const Model &m, int bh, int rx, const StepCoef *
     {
         const size_t total = ns * (size_t)P * (P / 4);
         const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 32);
-        pad_fields_kernel<<<blocks, 256, 0, st>>>(u0, b.padB, n, G, ns);
+        pad_fields_kernel<<<blocks, 256, 0, st>>>(u0, b.padB, n, G, ns, 0, 0.f);
         MFMC_LAUNCHED("nlch_solver launch 6");
     }
     const int ri = rx == 4 ? 0 : 1;
@@ -647,7 +674,7 @@ mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0,
     const bool constant = m.d.kernel == MFMC_KERNEL_CONSTANT;
     const TileLauncher *L = tile_launcher(m.R);
     const int ai = algo == MFMC_ALGO_DIRECT ? 0 : 1;
-    const bool tiled = algo != MFMC_ALGO_PLAIN && constant && L && L->fn[ai];
+    const bool tiled = algo != MFMC_ALGO_PLAIN && constant && L && L->fn[ai] && m.d.bc == MFMC_BC_PERIODIC;
 
     if (algo == MFMC_ALGO_PLAIN) {
         // reference form: one sample per launch, one launch per step
@@ -667,6 +694,8 @@ mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0,
                 g.tiles = tiles;
                 g.sample0 = 0;
                 g.last = k == nsteps;
+                g.collar = m.d.bc == MFMC_BC_COLLAR;
+                g.uI = (float)m.d.bc_value;
                 s = launch_generic(m, g, smp, 1, st);
                 if (s != MFMC_OK) return s;
                 src = dst;
@@ -701,6 +730,8 @@ mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0,
                 g.tiles = tiles;
                 g.sample0 = 0;
                 g.last = k == nsteps;
+                g.collar = m.d.bc == MFMC_BC_COLLAR;
+                g.uI = (float)m.d.bc_value;
                 s = launch_generic(m, g, 0, ns, st);
             }
             if (s != MFMC_OK) return s;

@@ -27,6 +27,8 @@ struct TmaArgs {
     const int *steps_ps;   // per-sample step counts (serving), or nullptr: every sample runs `step`
     int step;              // 1-based index of this step
     int n, P, tiles_x, tiles, total, last;
+    int periodic;          // 1: periodic frame (outputs also stored as ghost images); 0: the frame
+                           // is a fixed collar and only interior outputs are stored
 };
 
 // A sample takes part in step `a.step` while a.step <= its own step count.
@@ -152,7 +154,8 @@ __device__ __forceinline__ void tma_tile_compute(const float *s, const TmaArgs &
     double part = 0.0;
     const size_t nn = (size_t)n * n, PP = (size_t)a.P * a.P;
     // whether this thread's block has ghost images (touches the frame); uniform per thread
-    const bool framed = x0 + ox < G || x0 + ox + RX > n - G || y0 + oy < G || y0 + oy + RY > n - G;
+    const bool framed =
+        a.periodic && (x0 + ox < G || x0 + ox + RX > n - G || y0 + oy < G || y0 + oy + RY > n - G);
 #pragma unroll
     for (int j = 0; j < RY; ++j) {
         const float4 c4v = *reinterpret_cast<const float4 *>(s + (oy + j + R) * SW + ox + R4);
@@ -280,9 +283,9 @@ constexpr auto tma_kernel_ptr() {
         return &step_tma_kernel_capped<R, RY, TXT, TYT, ALGO, STAGES, MINB>;
 }
 
-// Copy unpadded fields [ns][n][n] into padded scratch [ns][P][P] including the frame
-// (defined in nlch_solver.cu).
-__global__ void pad_fields_kernel(const float *u, float *dst, int n, int G, size_t ns);
+// Copy unpadded fields [ns][n][n] into padded scratch [ns][P][P] including the frame: the
+// periodic images, or the collar value uI when `collar` (defined in nlch_solver.cu).
+__global__ void pad_fields_kernel(const float *u, float *dst, int n, int G, size_t ns, int collar, float uI);
 
 // --------------------------------------------------------------------------- host side
 // Tile shapes (rows per thread RY, threads along x TXT, threads along y TYT):

@@ -24,6 +24,7 @@ _L = ctypes.CDLL(LIB_PATH)
 MFMC_OK, MFMC_EINVAL, MFMC_ENOMEM, MFMC_ECUDA, MFMC_ETIMEOUT, MFMC_EBUDGET, MFMC_EBUSY, MFMC_ENOTFOUND = range(8)
 KERNEL_CONSTANT, KERNEL_GAUSSIAN = 0, 1
 BC_PERIODIC = 0
+BC_COLLAR = 1
 IC_UNIFORM, IC_SMOOTHED_GAUSS, IC_NUCLEI = 0, 1, 2
 ALGO_AUTO, ALGO_DIRECT, ALGO_PREFIX, ALGO_PREFIX_KAHAN, ALGO_RESIDENT, ALGO_PLAIN, ALGO_PREFIX_TMA, ALGO_ROWS = range(8)
 MAX_MODELS = 16
@@ -41,7 +42,7 @@ class mfmc_model_desc(ctypes.Structure):
                 ("eps_hi", ctypes.c_double), ("c_F", ctypes.c_double), ("beta1", ctypes.c_double),
                 ("beta2", ctypes.c_double), ("tau", ctypes.c_double), ("nsteps", ctypes.c_int),
                 ("bc", ctypes.c_int), ("ic", ctypes.c_int), ("ic_amp", ctypes.c_double),
-                ("ic_base_n", ctypes.c_int), ("algo", ctypes.c_int)]
+                ("ic_base_n", ctypes.c_int), ("algo", ctypes.c_int), ("bc_value", ctypes.c_double)]
 
 
 class mfmc_sample_params(ctypes.Structure):
@@ -165,9 +166,9 @@ class Model:
 
     def __init__(self, n, delta, kernel=KERNEL_CONSTANT, delta_hf=0.0, eps=0.03, eps_lo=0.0, eps_hi=0.0,
                  c_F=1.0, beta1=1.0, beta2=0.0, tau=1e-3, nsteps=200, ic=IC_UNIFORM, ic_amp=0.05, ic_base_n=0,
-                 algo=ALGO_AUTO):
+                 algo=ALGO_AUTO, bc=BC_PERIODIC, bc_value=-1.0):
         self.desc = mfmc_model_desc(n, delta, kernel, delta_hf, eps, eps_lo, eps_hi, c_F, beta1, beta2, tau,
-                                    nsteps, BC_PERIODIC, ic, ic_amp, ic_base_n, algo)
+                                    nsteps, bc, ic, ic_amp, ic_base_n, algo, bc_value)
         h = _vp()
         _check(_L.mfmc_model_create(ctypes.byref(self.desc), ctypes.byref(h)))
         self.handle = h.value
