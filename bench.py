@@ -35,12 +35,19 @@ METRIC = "grid-pt updates/s"
 WORKLOAD = "single fidelity 256x256, delta=8h (197-pt disc), constant kernel, 1000 steps, 512 samples/GPU"
 
 
+BC = 0            # 0 periodic (the headline), 1 collar holding BC_VALUE (--bc collar)
+BC_VALUE = -1.0
+
+
 def config(algo=None):
     c = {"workload": WORKLOAD if (NSTEPS, NSAMPLES) == (1000, 512) else "profiling case: " + WORKLOAD,
          "n": N_LATTICE, "R": R_CELLS, "disc_points": 197, "nsteps": NSTEPS, "samples_per_gpu": NSAMPLES, "tau": TAU, "eps": "0.02*U[0.8,1.2]", "ic": "smoothed Gaussian sigma=0.05",
          "l2": "inputs larger than L2 (2 x 128 MiB field buffers per solve, L2 129 MB)"}
     if algo is not None:
         c["algo"] = algo
+    if BC == 1:
+        c["workload"] += f", collar boundary (fixed value {BC_VALUE:g} on the interaction collar)"
+        c["boundary"] = {"kind": "collar", "value": BC_VALUE}
     return c
 
 
@@ -126,7 +133,7 @@ def cpu_baseline(seconds=12.0):
     import numpy as np
     import oracle
     o = oracle.OracleModel(n=N_LATTICE, delta=R_CELLS / N_LATTICE, eps=EPS, eps_lo=EPS_LO, eps_hi=EPS_HI,
-                           tau=TAU, nsteps=NSTEPS, ic=1, ic_amp=SIGMA)
+                           tau=TAU, nsteps=NSTEPS, ic=1, ic_amp=SIGMA, bc=BC, bc_value=BC_VALUE)
     seed = SEED_BASE
     eps = o.sample_eps(seed)
     u0 = o.initial_field(seed)
@@ -175,9 +182,11 @@ def run_reference(args):
 def run_ours(args):
     import numpy as np
     import torch
-    global NSTEPS, NSAMPLES
+    global NSTEPS, NSAMPLES, BC, BC_VALUE
     NSTEPS = args.nsteps or NSTEPS
     NSAMPLES = args.samples or NSAMPLES
+    BC = 1 if args.bc == "collar" else 0
+    BC_VALUE = args.bc_value
     ws, rank, local = dist_env()
     from paper_2310_10750_gb300 import build as pkg_build
     if rank == 0:
@@ -196,7 +205,8 @@ def run_ours(args):
     algo_req = {"auto": mfmc.ALGO_AUTO, "prefix": mfmc.ALGO_PREFIX, "direct": mfmc.ALGO_DIRECT,
                 "kahan": mfmc.ALGO_PREFIX_KAHAN, "tma": mfmc.ALGO_PREFIX_TMA, "rows": mfmc.ALGO_ROWS}[args.algo]
     model = mfmc.Model(n=N_LATTICE, delta=R_CELLS / N_LATTICE, eps=EPS, eps_lo=EPS_LO, eps_hi=EPS_HI, tau=TAU,
-                       nsteps=NSTEPS, ic=mfmc.IC_SMOOTHED_GAUSS, ic_amp=SIGMA, algo=algo_req)
+                       nsteps=NSTEPS, ic=mfmc.IC_SMOOTHED_GAUSS, ic_amp=SIGMA, algo=algo_req, bc=BC,
+                       bc_value=BC_VALUE)
     if args.tile_variant >= 0:
         model.set_tile_variant(args.tile_variant)
     if args.band_height > 0:
@@ -284,7 +294,7 @@ def run_ours(args):
     if os.path.exists(tpath):
         try:
             tr = json.load(open(tpath))
-            key = f"{N_LATTICE}_{R_CELLS}_{algo}"
+            key = f"{N_LATTICE}_{R_CELLS}_{algo}" + ("_collar" if BC == 1 else "")
             if key in tr:
                 traffic = tr[key]
         except Exception:
@@ -630,6 +640,9 @@ def main():
     ap.add_argument("--band-height", type=int, default=0, help="profiling: pin the row-streaming band height")
     ap.add_argument("--columns", type=int, default=2, help="profiling: row-streaming columns per thread")
     ap.add_argument("--tile-variant", type=int, default=-1, help="profiling: pin the TMA tile shape")
+    ap.add_argument("--bc", default="periodic", choices=["periodic", "collar"],
+                    help="boundary of the single-fidelity workload (collar: volume constraint)")
+    ap.add_argument("--bc-value", type=float, default=-1.0, help="collar value for --bc collar")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

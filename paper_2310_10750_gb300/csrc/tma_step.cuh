@@ -156,6 +156,11 @@ __device__ __forceinline__ void tma_tile_compute(const float *s, const TmaArgs &
     // whether this thread's block has ghost images (touches the frame); uniform per thread
     const bool framed =
         a.periodic && (x0 + ox < G || x0 + ox + RX > n - G || y0 + oy < G || y0 + oy + RY > n - G);
+    // n >= 2G: a column (row) has at most one ghost image, so the thread's ghost column is
+    // fixed for the item; smaller fields take the general scatter
+    const bool one_image = n >= 2 * G;
+    const int xg = x0 + ox;
+    const int cxg = xg < G ? G + xg + n : (xg >= n - G ? G + xg - n : -1);
 #pragma unroll
     for (int j = 0; j < RY; ++j) {
         const float4 c4v = *reinterpret_cast<const float4 *>(s + (oy + j + R) * SW + ox + R4);
@@ -175,7 +180,14 @@ __device__ __forceinline__ void tma_tile_compute(const float *s, const TmaArgs &
             } else if (a.dst) {
                 float *d = a.dst + sample * PP;
                 *reinterpret_cast<float4 *>(d + (size_t)(G + y) * a.P + G + x) = val;
-                if (framed) {
+                if (framed && one_image) {
+                    const int ry = y < G ? G + y + n : (y >= n - G ? G + y - n : -1);
+                    put_ghost(d, a.P, G + y, cxg, val);
+                    if (ry >= 0) {
+                        *reinterpret_cast<float4 *>(d + (size_t)ry * a.P + G + x) = val;
+                        put_ghost(d, a.P, ry, cxg, val);
+                    }
+                } else if (framed) {
                     // ghost images at rows G + y +- n and columns G + x +- n inside the frame
                     const int ra = y < G ? G + y + n : -1, rb = y >= n - G ? G + y - n : -1;
                     const int ca = x < G ? G + x + n : -1, cb = x >= n - G ? G + x - n : -1;

@@ -168,3 +168,25 @@ def test_collar_rejections(gpu_lib):
     g = mf.Model(n=128, delta=4 / 128, nsteps=4, bc=mf.BC_COLLAR, bc_value=-1.0)
     with pytest.raises(mf.MfmcError):       # the mixed-fidelity call is periodic only
         mf.mfmc_solve_batch_mixed([g], [1])
+
+
+def test_collar_full_size_sampled(gpu_lib):
+    # the benchmark's collar line: 256 x 256, delta = 8h, 1000 steps, 512 samples in one
+    # launch configuration; the oracle checks samples 0 and 511 element by element
+    import torch
+    mf = gpu_lib
+    n, R, steps, ns = 256, 8, 1000, 512
+    kw = dict(n=n, delta=R / n, eps=0.02, eps_lo=0.016, eps_hi=0.024, tau=1e-3, nsteps=steps, ic=1, ic_amp=0.05)
+    g = mf.Model(bc=mf.BC_COLLAR, bc_value=-1.0, **kw)
+    o = O.OracleModel(bc=1, bc_value=-1.0, **kw)
+    seeds = seeds_of(ns, 20231016 + 1000003)
+    u0, uT, f, _ = gpu_solve(mf, g, seeds)
+    assert np.abs(uT).max() <= 1.0
+    # the -1 collar lowers the mean near the edges: every sample's mean drops below its start
+    assert np.all(uT.mean(axis=(1, 2)) < u0.mean(axis=(1, 2)))
+    tol = steps * 4e-6 * math.e
+    for i in (0, ns - 1):
+        fr, _, ur, _ = o.solve_sample(int(seeds[i]))
+        assert abs(f[i] - fr) <= 1e-5 * fr
+        assert np.abs(uT[i] - ur).max() <= tol
+    del torch
