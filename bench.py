@@ -620,13 +620,70 @@ def run_mixed(args):
     return 0
 
 
+def run_paper(args):
+    """The paper's own nine models (Section 4, Table 1): truncated Gaussian kernel,
+    delta_hf = 0.25, eps^2 = 0.00178, tau = 0.01, T = 1 (100 steps), the four-nuclei initial
+    condition whose theta is the shared random input, h in {1/128, 1/88, 1/64} x delta in
+    {0.25, 0.1875, 0.125}, on the periodic lattice with beta2 = 0 (the paper's beta2 = 0.05
+    step is not built).  50 pilot samples on shared seeds give rho_{1,k} and sigma_k; the cost
+    of a model is GPU seconds per sample of a batched solve; the MFMC plan (policy 0) is printed
+    for budgets of 10 .. 1000 C_1 together with the number of feasible subsets."""
+    import numpy as np
+    from paper_2310_10750_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2310_10750_gb300 import mfmc
+    base = 20231016 + 1000003 * 5
+    levels = [(128, 0.25), (128, 0.1875), (88, 0.1875), (88, 0.25), (128, 0.125), (88, 0.125),
+              (64, 0.1875), (64, 0.25), (64, 0.125)]
+    common = dict(kernel=mfmc.KERNEL_GAUSSIAN, delta_hf=0.25, eps=math.sqrt(0.00178), tau=0.01, nsteps=100,
+                  ic=mfmc.IC_NUCLEI)
+    models = [mfmc.Model(n=n, delta=d, **common) for n, d in levels]
+    n_pilot = 50
+    t = time.perf_counter()
+    pilot = np.stack([mfmc.mfmc_solve_batch([m] * n_pilot, _seeds(base, n_pilot))[0] for m in models])
+    t_pilot = time.perf_counter() - t
+    cost = [_batched_cost(mfmc, m, 256, base + 10 ** 7) for m in models]
+    paper = {}
+    gpath = os.path.join(ROOT, "tests", "golden", "table1_pilot_statistics.txt")
+    if os.path.exists(gpath):
+        for line in open(gpath):
+            if line.strip() and not line.startswith("#"):
+                f = line.split()
+                paper[int(f[0])] = {"rho": float(f[3]), "cost_ratio": float(f[4]), "sigma": float(f[5])}
+    plans = []
+    for b in (10.0, 100.0, 1000.0):
+        p = mfmc.mfmc_plan(pilot, cost, b * cost[0], 0).as_dict()
+        plans.append({"budget_over_C1": b, "subset": [i + 1 for i in p["idx"]], "m": p["m"], "V": p["V"],
+                      "Bmin_over_C1": p["Bmin"] / cost[0], "below_min_budget": p["below_min_budget"],
+                      "n_feasible_subsets": p["n_feasible"]})
+    p0 = mfmc.mfmc_plan(pilot, cost, 100 * cost[0], 0).as_dict()
+    table = []
+    for k, ((n, d), m) in enumerate(zip(levels, models)):
+        row = {"model": k + 1, "h": f"1/{n}", "delta": d, "delta_over_h": d * n, "disc_points": m.info().disc_points,
+               "rho_1k": p0["rho_all"][k], "cost_ratio": cost[k] / cost[0], "sigma": p0["sigma_all"][k],
+               "gpu_s_per_sample": cost[k]}
+        if k + 1 in paper:
+            row["paper"] = paper[k + 1]
+        table.append(row)
+    line = {"metric": "HF samples/s (paper's nine models)", "value": 1.0 / cost[0], "unit": "samples/s",
+            "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "Section 4 models: Gaussian kernel delta_hf=0.25, eps^2=0.00178, tau=0.01, "
+                                   "100 steps, nuclei IC, h in {1/128,1/88,1/64} x delta in {0.25,0.1875,0.125}, "
+                                   "periodic lattice, beta2 = 0; pilot 50 shared seeds",
+                       "algo": "generic weighted disc sum (the Gaussian kernel's only path)"},
+            "pilot_wall_s": t_pilot, "table1": table, "plans": plans,
+            "paper_C1_s": 63.089}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="single", choices=["single", "hierarchy", "serving", "large", "mixed"],
+    ap.add_argument("--workload", default="single", choices=["single", "hierarchy", "serving", "large", "mixed", "paper"],
                     help="single (the headline, default), or one of the other measured configurations")
     ap.add_argument("--validation", type=int, default=2048, help="hierarchy: HF samples of the validation mean")
     ap.add_argument("--requests", type=int, default=20000, help="serving: requests in the stream")
@@ -654,6 +711,8 @@ def main():
         return run_large(args)
     if args.workload == "mixed":
         return run_mixed(args)
+    if args.workload == "paper":
+        return run_paper(args)
     return run_ours(args)
 
 

@@ -85,8 +85,10 @@ typedef enum {
 } mfmc_algo;
 
 /* One fidelity of the model (Section 2, Section 4).  The lattice is n x n on the unit
- * torus, h = 1/n.  delta/h must be an integer R within 1e-9 (1 <= R <= 32) and
- * n % 4 == 0 and n >= 8.  beta2 must be 0 (the nonlocal Allen-Cahn limit of
+ * torus, h = 1/n; the disc of the nodal quadrature is D = { z : |z| <= delta/h }.
+ * R = floor(delta/h) must satisfy 1 <= R <= 32 and 2R + 1 <= n; n % 4 == 0 and n >= 8.
+ * A non-integer delta/h (the paper's h = 1/88, delta = 0.1875 gives 16.5) is served by the
+ * generic kernel only (MFMC_ALGO_PLAIN / DIRECT, which AUTO then picks).  beta2 must be 0 (the nonlocal Allen-Cahn limit of
  * Eq. (nonl_CH_nm) whose step is the pointwise projection onto [-1, 1]). */
 typedef struct {
     int n;                 /* lattice points per side                              */

@@ -1,6 +1,6 @@
 // Autotuner: for a model whose algorithm is AUTO, time every candidate disc-sum
 // algorithm on a batch large enough to fill the GPU and keep the fastest.  Results are
-// cached per (n, R, kernel) for the life of the process.
+// cached per (n, R, kernel, boundary, disc) for the life of the process.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -15,10 +15,10 @@
 namespace mfmc {
 
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune_cache;
+static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
 
 mfmc_status autotune(Model &m, cudaStream_t st) {
-    const auto key = std::make_tuple(m.d.n, m.R, (int)m.d.kernel);
+    const auto key = std::make_tuple(m.d.n, m.R, (int)m.d.kernel, (int)m.d.bc, m.r2max);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);

@@ -107,8 +107,9 @@ static mfmc_status validate_desc(const mfmc_model_desc &d, int *R_out) {
     if (!(d.delta > 0)) return fail(MFMC_EINVAL, "delta must be > 0");
     const double Rf = d.delta * d.n;
     const double Rr = std::round(Rf);
-    if (std::fabs(Rf - Rr) > 1e-9 * std::max(1.0, Rr)) return fail(MFMC_EINVAL, "delta/h = %.12g is not an integer", Rf);
-    const int R = (int)Rr;
+    // a non-integer delta/h is allowed; the disc is { z : |z| <= delta/h } and only the
+    // generic kernel (plain and direct forms) serves it
+    const int R = std::fabs(Rf - Rr) <= 1e-9 * std::max(1.0, Rr) ? (int)Rr : (int)std::floor(Rf);
     if (R < 1 || R > kMaxR) return fail(MFMC_EINVAL, "delta/h = %d outside [1, %d]", R, kMaxR);
     if (2 * R + 1 > d.n) return fail(MFMC_EINVAL, "the horizon disc (2R+1 = %d) must fit in one period n = %d", 2 * R + 1, d.n);
     if (!(d.tau > 0)) return fail(MFMC_EINVAL, "tau must be > 0");
@@ -152,10 +153,15 @@ mfmc_status mfmc_model_create(const mfmc_model_desc *desc, mfmc_model **out) {
     if (!m) return fail(MFMC_ENOMEM, "host allocation failed");
     m->d = *desc;
     m->R = R;
+    {
+        const double Rf = desc->delta * desc->n;
+        m->integer_R = std::fabs(Rf - R) <= 1e-9 * std::max(1.0, (double)R) ? 1 : 0;
+        m->r2max = m->integer_R ? R * R : (int)std::floor(Rf * Rf * (1.0 + 1e-12));
+    }
     int count = 0;
     for (int d = 0; d <= R; ++d) {
         int w = 0;
-        while ((w + 1) * (w + 1) <= R * R - d * d) ++w;
+        while ((w + 1) * (w + 1) <= m->r2max - d * d) ++w;
         m->widths[d] = w;
         count += (2 * w + 1) * (d == 0 ? 1 : 2);
     }
@@ -170,9 +176,9 @@ mfmc_status mfmc_model_create(const mfmc_model_desc *desc, mfmc_model **out) {
         const double sg = desc->delta_hf / 3.0;
         const double pref = h * h * 4.0 / (M_PI * std::pow(sg, 4));
         m->ahat = 1.0;
-        m->wtab.assign(R * R + 1, 0.f);
-        std::vector<double> wd(R * R + 1, 0.0);
-        for (int r2 = 0; r2 <= R * R; ++r2) {
+        m->wtab.assign(m->r2max + 1, 0.f);
+        std::vector<double> wd(m->r2max + 1, 0.0);
+        for (int r2 = 0; r2 <= m->r2max; ++r2) {
             wd[r2] = pref * std::exp(-(double)r2 * h * h / (sg * sg));
             m->wtab[r2] = (float)wd[r2];
         }

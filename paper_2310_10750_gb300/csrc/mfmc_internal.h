@@ -30,7 +30,9 @@ struct StepCoef {
 // A validated model: descriptor plus derived constants.
 struct Model {
     mfmc_model_desc d;
-    int R;                    // delta / h
+    int R;                    // floor(delta / h): the disc's extent in lattice points
+    int r2max;                // floor((delta / h)^2): the disc is { z : |z|^2 <= r2max }
+    int integer_R;            // 1 when delta / h is an integer (every kernel); 0: generic kernel only
     int disc;                 // |D_R|
     int widths[kMaxR + 1];    // w(|dy|) = floor(sqrt(R^2 - dy^2))
     double ahat;              // gamma h^2 / eps^2 at r = 0 for the constant kernel, 1 for Gaussian

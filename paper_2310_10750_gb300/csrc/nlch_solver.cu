@@ -136,6 +136,7 @@ struct GenericArgs {
     int n, R, tiles_x, tiles, sample0, last;
     int collar;         // 1: points outside the lattice read uI (volume constraint), 0: periodic
     float uI;
+    int r2max;          // the disc is { z : |z|^2 <= r2max } (R^2 for an integer delta / h)
 };
 
 constexpr int GEN_TX = 32, GEN_TY = 8, GEN_NT = GEN_TX * GEN_TY;
@@ -167,11 +168,11 @@ __global__ void __launch_bounds__(GEN_NT) step_generic_kernel(GenericArgs a) {
     if (threadIdx.x <= R) {
         const int d = threadIdx.x;
         int w = 0;
-        while ((w + 1) * (w + 1) <= R * R - d * d) ++w;
+        while ((w + 1) * (w + 1) <= a.r2max - d * d) ++w;
         widths[d] = w;
     }
     if (a.wtab)
-        for (int i = threadIdx.x; i <= R * R; i += GEN_NT) wt[i] = a.wtab[i];
+        for (int i = threadIdx.x; i <= a.r2max; i += GEN_NT) wt[i] = a.wtab[i];
     __syncthreads();
 
     const int lx = threadIdx.x % GEN_TX, ly = threadIdx.x / GEN_TX;
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(GEN_NT) step_generic_kernel(GenericArgs a) {
 static size_t generic_smem(int R) {
     const int R4 = (R + 3) & ~3;
     return (size_t)(GEN_TY + 2 * R) * (GEN_TX + 2 * R4) * sizeof(float) + (R + 1) * sizeof(int) +
-           (R * R + 1) * sizeof(float);
+           (size_t)(R + 1) * (R + 1) * sizeof(float);  // weight table: r2max < (R + 1)^2
 }
 
 // ----------------------------------------------------------------------------- OoI
@@ -258,6 +259,8 @@ __global__ void reduce_fields_kernel(const float *u, int n, double *ubar, double
 
 bool algo_supported(const Model &m, int algo) {
     const bool constant = m.d.kernel == MFMC_KERNEL_CONSTANT;
+    // a non-integer delta / h: only the generic kernel, whose disc is set at run time
+    if (!m.integer_R) return algo == MFMC_ALGO_PLAIN || algo == MFMC_ALGO_DIRECT;
     if (m.d.bc == MFMC_BC_COLLAR) {
         // the collar lives in the TMA kernels' ghost frame and in the generic kernel's loads
         switch (algo) {
@@ -289,7 +292,7 @@ static int tiles_for(const Model &m, int algo, int *tiles_x) {
     int tx = GEN_TX, ty = GEN_TY;
     const TileLauncher *L = tile_launcher(m.R);
     const bool constant = m.d.kernel == MFMC_KERNEL_CONSTANT;
-    const bool tiled = constant && L && m.d.bc == MFMC_BC_PERIODIC &&
+    const bool tiled = constant && L && m.d.bc == MFMC_BC_PERIODIC && m.integer_R &&
                        ((algo == MFMC_ALGO_DIRECT && L->fn[0]) || algo == MFMC_ALGO_PREFIX);
     if (tiled) {
         tx = L->tx;
@@ -674,7 +677,8 @@ mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0,
     const bool constant = m.d.kernel == MFMC_KERNEL_CONSTANT;
     const TileLauncher *L = tile_launcher(m.R);
     const int ai = algo == MFMC_ALGO_DIRECT ? 0 : 1;
-    const bool tiled = algo != MFMC_ALGO_PLAIN && constant && L && L->fn[ai] && m.d.bc == MFMC_BC_PERIODIC;
+    const bool tiled =
+        algo != MFMC_ALGO_PLAIN && constant && L && L->fn[ai] && m.d.bc == MFMC_BC_PERIODIC && m.integer_R;
 
     if (algo == MFMC_ALGO_PLAIN) {
         // reference form: one sample per launch, one launch per step
@@ -696,6 +700,7 @@ mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0,
                 g.last = k == nsteps;
                 g.collar = m.d.bc == MFMC_BC_COLLAR;
                 g.uI = (float)m.d.bc_value;
+                g.r2max = m.r2max;
                 s = launch_generic(m, g, smp, 1, st);
                 if (s != MFMC_OK) return s;
                 src = dst;
@@ -732,6 +737,7 @@ mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0,
                 g.last = k == nsteps;
                 g.collar = m.d.bc == MFMC_BC_COLLAR;
                 g.uI = (float)m.d.bc_value;
+                g.r2max = m.r2max;
                 s = launch_generic(m, g, 0, ns, st);
             }
             if (s != MFMC_OK) return s;
