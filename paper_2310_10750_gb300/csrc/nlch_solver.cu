@@ -85,6 +85,54 @@ __global__ void init_fields_kernel(int n, int ic, double amp, int base_n, const 
     }
 }
 
+// The smoothed Gaussian IC, tiled: one CTA builds an output tile of TO x TO nodes of one
+// sample.  It evaluates amp * normal once for every base-lattice node of the tile's b x b
+// blocks plus a one-node halo (the untiled kernel evaluates each normal five times, in
+// FP64, which dominates the cost of building the fields), then the 5-point average of each
+// base node and the b x b block means with the same operations in the same order, so the
+// values are those of init_fields_kernel.
+constexpr int IC_SPAN = 32;   // base nodes per tile edge (b * TO <= IC_SPAN)
+constexpr int IC_NT = 256;
+
+__global__ void __launch_bounds__(IC_NT) smoothed_ic_kernel(int n, double amp, int B, int b, int TO,
+                                                            const uint64_t *seeds, size_t s0, float *u0) {
+    __shared__ double zz[(IC_SPAN + 2) * (IC_SPAN + 2)];  // amp * normal, tile + halo
+    __shared__ double nb[IC_SPAN * IC_SPAN];              // 5-point averages, clipped
+    const int tiles_x = (n + TO - 1) / TO;
+    const int ty0 = (blockIdx.x / tiles_x) * TO, tx0 = (blockIdx.x % tiles_x) * TO;
+    const size_t smp = s0 + blockIdx.y;
+    const uint64_t seed = seeds[smp];
+    const int span = b * TO, zw = span + 2;
+    const int Y0 = b * ty0 - b / 2 - 1, X0 = b * tx0 - b / 2 - 1;  // halo corner on the base lattice
+    for (int i = threadIdx.x; i < zw * zw; i += IC_NT) {
+        const int r = i / zw, c = i - r * zw;
+        int Y = (Y0 + r) % B, X = (X0 + c) % B;
+        Y = Y < 0 ? Y + B : Y;
+        X = X < 0 ? X + B : X;
+        zz[i] = __dmul_rn(amp, ic_normal(seed, (uint32_t)(Y * B + X)));
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < span * span; i += IC_NT) {
+        const int r = i / span + 1, c = i - (i / span) * span + 1;
+        double v = zz[r * zw + c];
+        v = __dadd_rn(v, zz[r * zw + c - 1]);
+        v = __dadd_rn(v, zz[r * zw + c + 1]);
+        v = __dadd_rn(v, zz[(r - 1) * zw + c]);
+        v = __dadd_rn(v, zz[(r + 1) * zw + c]);
+        nb[i] = clip1(__ddiv_rn(v, 5.0));
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < TO * TO; i += IC_NT) {
+        const int oy = i / TO, ox = i - oy * TO;
+        const int y = ty0 + oy, x = tx0 + ox;
+        if (y >= n || x >= n) continue;
+        double sacc = 0.0;
+        for (int a = 0; a < b; ++a)
+            for (int c = 0; c < b; ++c) sacc = __dadd_rn(sacc, nb[(oy * b + a) * span + ox * b + c]);
+        u0[smp * (size_t)n * n + (size_t)y * n + x] = (float)__ddiv_rn(sacc, __dmul_rn((double)b, (double)b));
+    }
+}
+
 mfmc_status launch_init_fields(const Model &m, const uint64_t *seeds_dev, const double *theta_dev,
                                size_t ns, float *u0, cudaStream_t st) {
     if (ns == 0) return MFMC_OK;
@@ -92,6 +140,17 @@ mfmc_status launch_init_fields(const Model &m, const uint64_t *seeds_dev, const 
     const int block = 256;
     const size_t blocks = std::min<size_t>((total + block - 1) / block, 152 * 64);
     const int base_n = m.d.ic_base_n > 0 ? m.d.ic_base_n : m.d.n;
+    const int b = base_n / m.d.n;
+    if (m.d.ic == MFMC_IC_SMOOTHED_GAUSS && b <= IC_SPAN) {
+        const int TO = IC_SPAN / b, tiles_x = (m.d.n + TO - 1) / TO;
+        for (size_t o = 0; o < ns; o += 65535) {
+            const unsigned gy = (unsigned)std::min<size_t>(65535, ns - o);
+            smoothed_ic_kernel<<<dim3(tiles_x * tiles_x, gy), IC_NT, 0, st>>>(m.d.n, m.d.ic_amp, base_n, b, TO,
+                                                                             seeds_dev, o, u0);
+        }
+        MFMC_LAUNCHED("nlch_solver launch 1 (tiled)");
+        return MFMC_OK;
+    }
     init_fields_kernel<<<(unsigned)blocks, block, 0, st>>>(m.d.n, (int)m.d.ic, m.d.ic_amp, base_n, seeds_dev,
                                                            theta_dev, ns, u0);
     MFMC_LAUNCHED("nlch_solver launch 1");
