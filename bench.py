@@ -203,7 +203,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     algo_req = {"auto": mfmc.ALGO_AUTO, "prefix": mfmc.ALGO_PREFIX, "direct": mfmc.ALGO_DIRECT,
-                "kahan": mfmc.ALGO_PREFIX_KAHAN, "tma": mfmc.ALGO_PREFIX_TMA, "rows": mfmc.ALGO_ROWS}[args.algo]
+                "kahan": mfmc.ALGO_PREFIX_KAHAN, "tma": mfmc.ALGO_PREFIX_TMA, "rows": mfmc.ALGO_ROWS,
+                "fft": mfmc.ALGO_FFT}[args.algo]
     model = mfmc.Model(n=N_LATTICE, delta=R_CELLS / N_LATTICE, eps=EPS, eps_lo=EPS_LO, eps_hi=EPS_HI, tau=TAU,
                        nsteps=NSTEPS, ic=mfmc.IC_SMOOTHED_GAUSS, ic_amp=SIGMA, algo=algo_req, bc=BC,
                        bc_value=BC_VALUE)
@@ -221,7 +222,7 @@ def run_ours(args):
         mfmc.mfmc_solve_fields(model, u0, ns, eps=eps, ooi=ooi, stream=stream)
     torch.cuda.synchronize()
     algo_names = {1: "direct", 2: "prefix", 3: "prefix-kahan", 4: "resident", 5: "plain", 6: "prefix-tma",
-                  7: "row-stream"}
+                  7: "row-stream", 8: "fft"}
     algo = algo_names.get(model.info().algo, str(model.info().algo))
     if algo == "prefix-tma":
         algo += f" (tile variant {model.info().tile_variant})"
@@ -509,59 +510,36 @@ def run_serving(args):
 
 def run_large(args):
     """1024^2, delta = 32h (3209-point disc), 2000 steps, 64 samples: throughput of the
-    autotuned algorithm and of the direct sum, and the FP32 vs compensated (Kahan) sums
-    against the FP64 oracle on samples 0-3 (oracle run for a bounded number of steps)."""
-    import numpy as np
-    import torch
+    autotuned algorithm, of the direct sum and of the spectral (cuFFT) form of the disc sum.
+    (The FP32 / compensated sums against the oracle are a test: tests/test_large_hf_gpu.py.)"""
     from paper_2310_10750_gb300 import build as pkg_build
     pkg_build.build()
     from paper_2310_10750_gb300 import mfmc
-    import oracle
     n, R, steps, ns = 1024, 32, 2000, 64
     base = 20231016 + 1000003 * 4
     kw = dict(n=n, delta=R / n, eps=0.02, eps_lo=0.016, eps_hi=0.024, tau=1e-3, ic=mfmc.IC_SMOOTHED_GAUSS,
               ic_amp=0.05)
     model = mfmc.Model(nsteps=steps, **kw)
     c = _batched_cost(mfmc, model, ns, base)
-    names = {1: "direct", 2: "prefix", 4: "resident", 6: "prefix-tma", 7: "row-stream"}
+    names = {1: "direct", 2: "prefix", 4: "resident", 6: "prefix-tma", 7: "row-stream", 8: "fft"}
     algo = names.get(model.info().algo, str(model.info().algo))
+    if algo == "prefix-tma":
+        algo += f" (tile variant {model.info().tile_variant})"
     direct_c = None
     if not args.no_plain:
         md = mfmc.Model(nsteps=20, algo=mfmc.ALGO_DIRECT, **kw)
         direct_c = _batched_cost(mfmc, md, ns, base) * steps / 20
-    k = args.oracle_steps
-    prec = []
-    seeds = _seeds(base, 4)
-    o = oracle.OracleModel(n=n, delta=R / n, eps=0.02, eps_lo=0.016, eps_hi=0.024, tau=1e-3, nsteps=k, ic=1,
-                           ic_amp=0.05)
-    for algo_id, label in ((mfmc.ALGO_PREFIX_TMA, "fp32"), (mfmc.ALGO_PREFIX_KAHAN, "fp32-kahan")):
-        g = mfmc.Model(nsteps=k, algo=algo_id, **kw)
-        if algo_id == mfmc.ALGO_PREFIX_TMA:
-            g.set_tile_variant(0)
-        u0 = torch.empty((4, n, n), dtype=torch.float32, device="cuda")
-        uT = torch.empty_like(u0)
-        ooi = torch.empty(4, dtype=torch.float64, device="cuda")
-        eps = torch.tensor(mfmc.mfmc_sample_eps(g, seeds), dtype=torch.float64, device="cuda")
-        mfmc.mfmc_init_fields(g, seeds, u0)
-        mfmc.mfmc_solve_fields(g, u0, 4, eps=eps, uT=uT, ooi=ooi)
-        torch.cuda.synchronize()
-        prec.append((label, ooi.cpu().numpy(), uT.cpu().numpy()))
-    errs = {}
-    for i, s in enumerate(seeds):
-        fr, _, ur, _ = o.solve_sample(int(s))
-        for label, f, u in prec:
-            e = errs.setdefault(label, {"max_rel_ooi_err": 0.0, "max_abs_field_err": 0.0})
-            e["max_rel_ooi_err"] = max(e["max_rel_ooi_err"], abs(f[i] - fr) / fr)
-            e["max_abs_field_err"] = max(e["max_abs_field_err"], float(np.abs(u[i] - ur).max()))
+    mf_ = mfmc.Model(nsteps=200, algo=mfmc.ALGO_FFT, **kw)
+    fft_c = _batched_cost(mfmc, mf_, ns, base) * steps / 200
     pts = ns * n * n * steps
     line = {"metric": "grid-pt updates/s (large HF)", "value": pts / (c * ns), "unit": METRIC,
             "higher_is_better": True, "data": "synthetic",
             "config": {"workload": "1024^2, delta=32h (3209-pt disc), 2000 steps, 64 samples", "algo": algo},
             "gpu_s_per_sample": c, "direct_sum_gpu_s_per_sample": direct_c,
-            "precision_vs_oracle": {"samples": 4, "oracle_steps": k, **errs}}
+            "fft_gpu_s_per_sample": fft_c,
+            "fft_what": "cuFFT R2C/C2R per step + product + fused update (library comparison point, 200 steps scaled)"}
     print(json.dumps(line), flush=True)
     return 0
-
 
 def run_mixed(args):
     """One MFMC replicate's samples of the delta = 1/32 hierarchy (512^2/R16, 256^2/R8,
@@ -643,6 +621,8 @@ def run_paper(args):
     pilot = np.stack([mfmc.mfmc_solve_batch([m] * n_pilot, _seeds(base, n_pilot))[0] for m in models])
     t_pilot = time.perf_counter() - t
     cost = [_batched_cost(mfmc, m, 256, base + 10 ** 7) for m in models]
+    fft_models = [mfmc.Model(n=n, delta=d, algo=mfmc.ALGO_FFT, **common) for n, d in levels]
+    fft_cost = [_batched_cost(mfmc, m, 256, base + 10 ** 7) for m in fft_models]
     paper = {}
     gpath = os.path.join(ROOT, "tests", "golden", "table1_pilot_statistics.txt")
     if os.path.exists(gpath):
@@ -661,7 +641,7 @@ def run_paper(args):
     for k, ((n, d), m) in enumerate(zip(levels, models)):
         row = {"model": k + 1, "h": f"1/{n}", "delta": d, "delta_over_h": d * n, "disc_points": m.info().disc_points,
                "rho_1k": p0["rho_all"][k], "cost_ratio": cost[k] / cost[0], "sigma": p0["sigma_all"][k],
-               "gpu_s_per_sample": cost[k]}
+               "gpu_s_per_sample": cost[k], "fft_gpu_s_per_sample": fft_cost[k]}
         if k + 1 in paper:
             row["paper"] = paper[k + 1]
         table.append(row)
@@ -693,7 +673,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--nsteps", type=int, default=0, help="profiling: time steps per solve")
     ap.add_argument("--samples", type=int, default=0, help="profiling: samples per GPU")
-    ap.add_argument("--algo", default="auto", choices=["auto", "prefix", "direct", "kahan", "tma", "rows"])
+    ap.add_argument("--algo", default="auto", choices=["auto", "prefix", "direct", "kahan", "tma", "rows", "fft"])
     ap.add_argument("--band-height", type=int, default=0, help="profiling: pin the row-streaming band height")
     ap.add_argument("--columns", type=int, default=2, help="profiling: row-streaming columns per thread")
     ap.add_argument("--tile-variant", type=int, default=-1, help="profiling: pin the TMA tile shape")

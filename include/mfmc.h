@@ -81,7 +81,13 @@ typedef enum {
                                   tiles of a ghost-framed field                   */
     MFMC_ALGO_ROWS = 7         /* prefix form, each thread streams 2 or 4 columns down
                                   a band of rows with a ring of 2R+1 accumulators
-                                  (R in {2,4,6,8}, n % 64 == 0, n <= 1024)         */
+                                  (R in {2,4,6,8}, n % 64 == 0, n <= 1024)         */,
+    MFMC_ALGO_FFT = 8          /* spectral form of the disc sum: cuFFT transforms (a library,
+                                  loaded at run time) of each field, a product with the
+                                  transform of the disc weights and the fused update; cost
+                                  independent of the horizon; any kernel and radius,
+                                  periodic boundary only; a comparison point for very large
+                                  horizons that AUTO does not pick */
 } mfmc_algo;
 
 /* One fidelity of the model (Section 2, Section 4).  The lattice is n x n on the unit

@@ -53,6 +53,7 @@ Model::~Model() {
     cudaFree(d_status);
     if (gexec) cudaGraphExecDestroy(gexec);
     if (stream) cudaStreamDestroy(stream);
+    fft_release(fft);
 }
 
 template <typename T>
@@ -128,7 +129,7 @@ static mfmc_status validate_desc(const mfmc_model_desc &d, int *R_out) {
     if (!(d.ic_amp >= 0)) return fail(MFMC_EINVAL, "ic_amp must be >= 0");
     if (d.ic_base_n < 0 || (d.ic_base_n > 0 && (d.ic_base_n % d.n != 0 || d.ic_base_n > 16384)))
         return fail(MFMC_EINVAL, "ic_base_n must be 0 or a multiple of n up to 16384");
-    if ((int)d.algo < MFMC_ALGO_AUTO || (int)d.algo > MFMC_ALGO_ROWS) return fail(MFMC_EINVAL, "unknown algo");
+    if ((int)d.algo < MFMC_ALGO_AUTO || (int)d.algo > MFMC_ALGO_FFT) return fail(MFMC_EINVAL, "unknown algo");
     *R_out = R;
     return MFMC_OK;
 }
@@ -297,7 +298,8 @@ static mfmc_status solve_impl(mfmc_model *m, int algo, const double *eps, const 
     // The launch sequence of a solve (coefficients, ~nsteps step kernels, OoI) is replayed as a
     // CUDA graph while the call's key (algorithm, shape, every pointer it touches, stream) is
     // unchanged: the first call with a key runs directly (sizing scratch), then is captured.
-    const bool graphable = !m->graphs_off && algo != MFMC_ALGO_RESIDENT && algo != MFMC_ALGO_PLAIN && nsteps > 0;
+    const bool graphable = !m->graphs_off && algo != MFMC_ALGO_RESIDENT && algo != MFMC_ALGO_PLAIN &&
+                           algo != MFMC_ALGO_FFT && nsteps > 0;
     auto key = [&]() {
         return std::vector<uintptr_t>{(uintptr_t)algo, (uintptr_t)m->tma_variant, (uintptr_t)m->rows_bh,
                                       (uintptr_t)m->rows_rx, (uintptr_t)ns, (uintptr_t)nsteps, (uintptr_t)eps,
@@ -350,7 +352,7 @@ mfmc_status mfmc_solve_fields(const mfmc_model *cm, const double *eps, const flo
 mfmc_status mfmc_solve_fields_algo(const mfmc_model *cm, int algo, const double *eps, const float *u0, size_t ns,
                                    float *uT, double *ubar, double *ooi, void *stream) {
     if (!cm) return fail(MFMC_EINVAL, "NULL model");
-    if (algo < MFMC_ALGO_AUTO || algo > MFMC_ALGO_ROWS) return fail(MFMC_EINVAL, "unknown algo");
+    if (algo < MFMC_ALGO_AUTO || algo > MFMC_ALGO_FFT) return fail(MFMC_EINVAL, "unknown algo");
     return solve_impl(const_cast<mfmc_model *>(cm), algo, eps, u0, ns, uT, ubar, ooi, (cudaStream_t)stream);
 }
 

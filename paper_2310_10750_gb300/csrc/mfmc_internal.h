@@ -27,6 +27,10 @@ struct StepCoef {
     float c0, c1, c2, pad;
 };
 
+struct FftState;  // spectral-convolution state of the FFT path (fft_solver.cu)
+void fft_release(FftState *f);
+bool fft_available();
+
 // A validated model: descriptor plus derived constants.
 struct Model {
     mfmc_model_desc d;
@@ -74,6 +78,7 @@ struct Model {
     cudaGraphExec_t gexec = nullptr;
     std::vector<uintptr_t> gkey;
     int graphs_off = 0;
+    FftState *fft = nullptr;  // created by the first FFT-path solve
     ~Model();
 };
 
@@ -176,6 +181,9 @@ bool rows_supported(const Model &m, int rx);
 // The TMA pipeline with an explicit tile-shape variant (autotuner).
 mfmc_status run_solve_tma(Model &m, int kahan, int variant, const StepCoef *coef, const float *u0, size_t ns,
                           int nsteps, float *uT, double *ubar, double *ooi, cudaStream_t st);
+// The spectral (cuFFT) form of the disc sum, periodic lattice, any kernel and radius.
+mfmc_status run_solve_fft(Model &m, const StepCoef *coef, const float *u0, size_t ns, int nsteps, float *uT,
+                          double *ubar, double *ooi, cudaStream_t st);
 // Whether an algorithm can run this model.
 bool algo_supported(const Model &m, int algo);
 // Autotuner: time the candidate algorithms on this model once and cache the winner.

@@ -318,6 +318,7 @@ __global__ void reduce_fields_kernel(const float *u, int n, double *ubar, double
 
 bool algo_supported(const Model &m, int algo) {
     const bool constant = m.d.kernel == MFMC_KERNEL_CONSTANT;
+    if (algo == MFMC_ALGO_FFT) return m.d.bc == MFMC_BC_PERIODIC;  // any kernel, any radius
     // a non-integer delta / h: only the generic kernel, whose disc is set at run time
     if (!m.integer_R) return algo == MFMC_ALGO_PLAIN || algo == MFMC_ALGO_DIRECT;
     if (m.d.bc == MFMC_BC_COLLAR) {
@@ -720,6 +721,7 @@ mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0,
         MFMC_LAUNCHED("nlch_solver launch 8");
         return MFMC_OK;
     }
+    if (algo == MFMC_ALGO_FFT) return run_solve_fft(m, coef, u0, ns, nsteps, uT, ubar, ooi, st);
     if (algo == MFMC_ALGO_PREFIX_TMA)
         return run_solve_tma(m, 0, m.tma_variant, coef, u0, ns, nsteps, uT, ubar, ooi, st);
     if (algo == MFMC_ALGO_PREFIX_KAHAN) return run_solve_tma(m, 1, 0, coef, u0, ns, nsteps, uT, ubar, ooi, st);

@@ -1,0 +1,36 @@
+"""The large high-fidelity configuration (1024 x 1024, delta = 32h: a 3209-point disc) against
+the FP64 oracle for a bounded number of steps: the plain FP32 disc sums (autotuned kernel),
+the FP32-compensated (Kahan) sums and the spectral form.  With |D| = 3209 FP32 adds per output
+this is where accumulation error would show first; the per-step bound of the other parity
+tests, 4e-6 max|u|, is the target for all three."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+def test_large_hf_fp32_kahan_and_fft_against_oracle(gpu_lib):
+    import torch
+    mf = gpu_lib
+    n, R, steps = 1024, 32, 20
+    kw = dict(n=n, delta=R / n, eps=0.02, eps_lo=0.016, eps_hi=0.024, tau=1e-3, nsteps=steps, ic=1, ic_amp=0.05)
+    o = O.OracleModel(**kw)
+    seeds = np.array([20231016 + 1000003 * 4], dtype=np.uint64)
+    fr, _, ur, _ = o.solve_sample(int(seeds[0]))
+    tol = steps * 4e-6 * 0.05 * math.e
+    for algo in (mf.ALGO_AUTO, mf.ALGO_PREFIX_KAHAN, mf.ALGO_FFT):
+        g = mf.Model(algo=algo, **kw)
+        u0 = torch.empty((1, n, n), dtype=torch.float32, device="cuda")
+        uT = torch.empty_like(u0)
+        ooi = torch.empty(1, dtype=torch.float64, device="cuda")
+        eps = torch.tensor(mf.mfmc_sample_eps(g, seeds), dtype=torch.float64, device="cuda")
+        mf.mfmc_init_fields(g, seeds, u0)
+        mf.mfmc_solve_fields(g, u0, 1, eps=eps, uT=uT, ooi=ooi)
+        torch.cuda.synchronize()
+        f = float(ooi.cpu()[0])
+        assert abs(f - fr) <= 1e-9 * fr, algo
+        assert np.abs(uT.cpu().numpy()[0].astype(np.float64) - ur).max() <= tol, algo
