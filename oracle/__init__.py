@@ -2,7 +2,8 @@
 
 A plain, slow FP64 CPU reference of what the GPU library computes, written from the
 paper: ``nlch_oracle.c`` holds the model, its time step and the output of interest
-(Section 2 and Section 4, beta2 = 0; periodic lattice or a collar holding fixed data); ``mfmc_oracle.py`` holds the multifidelity
+(Section 2 and Section 4, beta2 = 0; periodic lattice or a collar holding fixed data);
+``beta2_oracle.py`` holds the beta2 > 0 step (a semismooth Newton solve per step); ``mfmc_oracle.py`` holds the multifidelity
 Monte Carlo statistics, model selection, allocation and estimator (Section 3).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
