@@ -87,15 +87,22 @@ typedef enum {
                                   transform of the disc weights and the fused update; cost
                                   independent of the horizon; any kernel and radius,
                                   periodic boundary only; a comparison point for very large
-                                  horizons that AUTO does not pick */
+                                  horizons that AUTO does not pick */,
+    MFMC_ALGO_ACTIVE_SET = 9   /* the beta2 > 0 step: per step the explicit convolution, then
+                                  a semismooth Newton (primal-dual active-set) solve of the
+                                  resolvent equation with Jacobi-preconditioned CG, in FP64,
+                                  one CTA per sample; the only algorithm for beta2 > 0 (AUTO
+                                  picks it), periodic only */
 } mfmc_algo;
 
 /* One fidelity of the model (Section 2, Section 4).  The lattice is n x n on the unit
  * torus, h = 1/n; the disc of the nodal quadrature is D = { z : |z| <= delta/h }.
  * R = floor(delta/h) must satisfy 1 <= R <= 32 and 2R + 1 <= n; n % 4 == 0 and n >= 8.
  * A non-integer delta/h (the paper's h = 1/88, delta = 0.1875 gives 16.5) is served by the
- * generic kernel only (MFMC_ALGO_PLAIN / DIRECT, which AUTO then picks).  beta2 must be 0 (the nonlocal Allen-Cahn limit of
- * Eq. (nonl_CH_nm) whose step is the pointwise projection onto [-1, 1]). */
+ * generic kernel only (MFMC_ALGO_PLAIN / DIRECT, which AUTO then picks).  beta2 = 0 is the
+ * nonlocal Allen-Cahn limit of Eq. (nonl_CH_nm), whose step is the pointwise projection onto
+ * [-1, 1] (every kernel); beta2 > 0 (the paper's 0.05) couples the step through the 5-point
+ * Laplacian and is solved by MFMC_ALGO_ACTIVE_SET. */
 typedef struct {
     int n;                 /* lattice points per side                              */
     double delta;          /* horizon                                              */
@@ -105,7 +112,8 @@ typedef struct {
     double eps_lo, eps_hi; /* if eps_hi > eps_lo: per-sample eps ~ U[eps_lo,eps_hi]
                               drawn from stream 0 of the seed                     */
     double c_F;            /* obstacle potential constant, Eq. (potential_obstacle) */
-    double beta1, beta2;   /* Eq. (nonl_CH_nm); beta1 > 0, beta2 == 0              */
+    double beta1, beta2;   /* Eq. (nonl_CH_nm); beta1 > 0, beta2 >= 0 (beta2 > 0:
+                              MFMC_ALGO_ACTIVE_SET, periodic lattice only)          */
     double tau;            /* time step                                            */
     int nsteps;            /* number of steps, T = nsteps * tau                    */
     mfmc_boundary bc;

@@ -18,6 +18,11 @@ static std::mutex g_tune_mu;
 static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
 
 mfmc_status autotune(Model &m, cudaStream_t st) {
+    if (m.d.beta2 > 0.0) {  // one solver serves beta2 > 0
+        m.algo = MFMC_ALGO_ACTIVE_SET;
+        m.tuned = 1;
+        return MFMC_OK;
+    }
     const auto key = std::make_tuple(m.d.n, m.R, (int)m.d.kernel, (int)m.d.bc, m.r2max);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -51,6 +51,9 @@ Model::~Model() {
     cudaFree(padA);
     cudaFree(padB);
     cudaFree(d_status);
+    cudaFree(d_wtab64);
+    cudaFree(as_buf);
+    cudaFree(as_status);
     if (gexec) cudaGraphExecDestroy(gexec);
     if (stream) cudaStreamDestroy(stream);
     fft_release(fft);
@@ -115,7 +118,9 @@ static mfmc_status validate_desc(const mfmc_model_desc &d, int *R_out) {
     if (2 * R + 1 > d.n) return fail(MFMC_EINVAL, "the horizon disc (2R+1 = %d) must fit in one period n = %d", 2 * R + 1, d.n);
     if (!(d.tau > 0)) return fail(MFMC_EINVAL, "tau must be > 0");
     if (!(d.beta1 > 0)) return fail(MFMC_EINVAL, "beta1 must be > 0");
-    if (d.beta2 != 0.0) return fail(MFMC_EINVAL, "beta2 > 0 (active-set step) is not supported; beta2 must be 0");
+    if (!(d.beta2 >= 0.0)) return fail(MFMC_EINVAL, "beta2 must be >= 0");
+    if (d.beta2 > 0.0 && d.bc != MFMC_BC_PERIODIC)
+        return fail(MFMC_EINVAL, "beta2 > 0 (the active-set step) runs on the periodic lattice only");
     if (!(d.eps > 0) && !(d.eps_hi > d.eps_lo && d.eps_lo > 0)) return fail(MFMC_EINVAL, "eps must be > 0");
     if (d.eps_hi > d.eps_lo && !(d.eps_lo > 0)) return fail(MFMC_EINVAL, "eps range must be positive");
     if (!(d.c_F >= 0)) return fail(MFMC_EINVAL, "c_F must be >= 0");
@@ -129,7 +134,7 @@ static mfmc_status validate_desc(const mfmc_model_desc &d, int *R_out) {
     if (!(d.ic_amp >= 0)) return fail(MFMC_EINVAL, "ic_amp must be >= 0");
     if (d.ic_base_n < 0 || (d.ic_base_n > 0 && (d.ic_base_n % d.n != 0 || d.ic_base_n > 16384)))
         return fail(MFMC_EINVAL, "ic_base_n must be 0 or a multiple of n up to 16384");
-    if ((int)d.algo < MFMC_ALGO_AUTO || (int)d.algo > MFMC_ALGO_FFT) return fail(MFMC_EINVAL, "unknown algo");
+    if ((int)d.algo < MFMC_ALGO_AUTO || (int)d.algo > MFMC_ALGO_ACTIVE_SET) return fail(MFMC_EINVAL, "unknown algo");
     *R_out = R;
     return MFMC_OK;
 }
@@ -172,6 +177,7 @@ mfmc_status mfmc_model_create(const mfmc_model_desc *desc, mfmc_model **out) {
         // gamma = 8 eps^2 / (pi delta^4): h^2 gamma = eps^2 * ahat, unit weights
         m->ahat = 8.0 * h * h / (M_PI * std::pow(desc->delta, 4));
         m->chat = (double)count;
+        m->chat64 = (double)count;
     } else {
         // Gaussian weights / eps^2: h^2 4 / (pi s^4) exp(-r^2 / s^2), s = delta_hf / 3
         const double sg = desc->delta_hf / 3.0;
@@ -189,6 +195,13 @@ mfmc_status mfmc_model_create(const mfmc_model_desc *desc, mfmc_model **out) {
             for (int dx = -w; dx <= w; ++dx) c += (double)m->wtab[dx * dx + dy * dy];
         }
         m->chat = c;  // sum of the FP32 weights the kernel uses
+        m->wtab64 = wd;
+        double c64 = 0.0;
+        for (int dy = -R; dy <= R; ++dy) {
+            const int w = m->widths[dy < 0 ? -dy : dy];
+            for (int dx = -w; dx <= w; ++dx) c64 += wd[dx * dx + dy * dy];
+        }
+        m->chat64 = c64;
     }
     m->algo = desc->algo;
     m->tuned = 0;
@@ -289,6 +302,7 @@ static mfmc_status solve_impl(mfmc_model *m, int algo, const double *eps, const 
         algo = m->algo;
     }
     if (!algo_supported(*m, algo)) return fail(MFMC_EINVAL, "algorithm %d does not support this model", algo);
+    if (algo == MFMC_ALGO_ACTIVE_SET) return run_solve_active_set(*m, eps, u0, ns, nsteps, uT, ubar, ooi, st);
     mfmc_status s = grow(&m->coef, &m->coef_cap, ns);
     if (s != MFMC_OK) return s;
     if (m->d.kernel == MFMC_KERNEL_GAUSSIAN && !m->d_wtab) {
@@ -352,7 +366,7 @@ mfmc_status mfmc_solve_fields(const mfmc_model *cm, const double *eps, const flo
 mfmc_status mfmc_solve_fields_algo(const mfmc_model *cm, int algo, const double *eps, const float *u0, size_t ns,
                                    float *uT, double *ubar, double *ooi, void *stream) {
     if (!cm) return fail(MFMC_EINVAL, "NULL model");
-    if (algo < MFMC_ALGO_AUTO || algo > MFMC_ALGO_FFT) return fail(MFMC_EINVAL, "unknown algo");
+    if (algo < MFMC_ALGO_AUTO || algo > MFMC_ALGO_ACTIVE_SET) return fail(MFMC_EINVAL, "unknown algo");
     return solve_impl(const_cast<mfmc_model *>(cm), algo, eps, u0, ns, uT, ubar, ooi, (cudaStream_t)stream);
 }
 

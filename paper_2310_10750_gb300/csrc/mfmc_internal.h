@@ -42,6 +42,13 @@ struct Model {
     double ahat;              // gamma h^2 / eps^2 at r = 0 for the constant kernel, 1 for Gaussian
     std::vector<float> wtab;  // Gaussian: weight / eps^2 per r2 = dx^2 + dy^2 (0..R^2)
     double chat;              // sum_z what_z (FP64)
+    std::vector<double> wtab64; // Gaussian: FP64 weight / eps^2 per r2 (the beta2 > 0 solver)
+    double chat64 = 0.0;      // sum_z what_z of the FP64 weights
+    // scratch of the beta2 > 0 solver (active_set.cu)
+    double *d_wtab64 = nullptr;
+    double *as_buf = nullptr;
+    size_t as_cap = 0;        // doubles
+    int *as_status = nullptr;
     int algo;                 // resolved algorithm (never AUTO after the autotuner ran)
     int tuned;                // 1 once AUTO was resolved
     // library-owned scratch, reused across calls on this model
@@ -184,6 +191,10 @@ mfmc_status run_solve_tma(Model &m, int kahan, int variant, const StepCoef *coef
 // The spectral (cuFFT) form of the disc sum, periodic lattice, any kernel and radius.
 mfmc_status run_solve_fft(Model &m, const StepCoef *coef, const float *u0, size_t ns, int nsteps, float *uT,
                           double *ubar, double *ooi, cudaStream_t st);
+// The beta2 > 0 step (semismooth Newton with preconditioned CG per step, FP64, one CTA per
+// sample); eps_dev: per-sample eps (FP64) or nullptr for the nominal eps.
+mfmc_status run_solve_active_set(Model &m, const double *eps_dev, const float *u0, size_t ns, int nsteps,
+                                 float *uT, double *ubar, double *ooi, cudaStream_t st);
 // Whether an algorithm can run this model.
 bool algo_supported(const Model &m, int algo);
 // Autotuner: time the candidate algorithms on this model once and cache the winner.

@@ -225,10 +225,10 @@ extern "C" mfmc_status mfmc_solve_batch_mixed(mfmc_model *const *models, const m
         mfmc_model *m = models[i];
         if (!m) return fail(MFMC_EINVAL, "NULL model at sample %zu", i);
         MixGeom geo;
-        if (m->d.kernel != MFMC_KERNEL_CONSTANT || m->d.bc != MFMC_BC_PERIODIC || !m->integer_R ||
+        if (m->d.kernel != MFMC_KERNEL_CONSTANT || m->d.bc != MFMC_BC_PERIODIC || !m->integer_R || m->d.beta2 > 0.0 ||
             !mix_geom(m->R, &geo))
-            return fail(MFMC_EINVAL, "the one-launch mixed batch runs periodic constant-kernel models with R in "
-                                     "{2, 4, 8, 16}");
+            return fail(MFMC_EINVAL, "the one-launch mixed batch runs periodic constant-kernel beta2 = 0 models with "
+                                     "R in {2, 4, 8, 16}");
         if (!groups.count(m)) order.push_back(m);
         groups[m].push_back(i);
     }

@@ -318,6 +318,8 @@ __global__ void reduce_fields_kernel(const float *u, int n, double *ubar, double
 
 bool algo_supported(const Model &m, int algo) {
     const bool constant = m.d.kernel == MFMC_KERNEL_CONSTANT;
+    // beta2 > 0: only the active-set solver; it serves nothing else
+    if (m.d.beta2 > 0.0 || algo == MFMC_ALGO_ACTIVE_SET) return m.d.beta2 > 0.0 && algo == MFMC_ALGO_ACTIVE_SET;
     if (algo == MFMC_ALGO_FFT) return m.d.bc == MFMC_BC_PERIODIC;  // any kernel, any radius
     // a non-integer delta / h: only the generic kernel, whose disc is set at run time
     if (!m.integer_R) return algo == MFMC_ALGO_PLAIN || algo == MFMC_ALGO_DIRECT;

@@ -87,7 +87,7 @@ extern "C" mfmc_status mfmc_solve_fields_noalloc(const mfmc_model *cm, const dou
     if (uT && uT == u0) return fail(MFMC_EINVAL, "uT must not alias u0");
     const Model &m = *cm;
     const TileLauncher *L = tile_launcher(m.R);
-    if (m.d.kernel != MFMC_KERNEL_CONSTANT || m.d.bc != MFMC_BC_PERIODIC || !m.integer_R || !L)
+    if (m.d.kernel != MFMC_KERNEL_CONSTANT || m.d.bc != MFMC_BC_PERIODIC || !m.integer_R || m.d.beta2 > 0.0 || !L)
         return fail(MFMC_EINVAL, "the allocation-free solve supports the periodic constant kernel with R in "
                                  "{1,2,3,4,5,6,8,11,12,16,22,24,32}");
     const int n = m.d.n;

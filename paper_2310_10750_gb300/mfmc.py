@@ -26,8 +26,8 @@ KERNEL_CONSTANT, KERNEL_GAUSSIAN = 0, 1
 BC_PERIODIC = 0
 BC_COLLAR = 1
 IC_UNIFORM, IC_SMOOTHED_GAUSS, IC_NUCLEI = 0, 1, 2
-ALGO_AUTO, ALGO_DIRECT, ALGO_PREFIX, ALGO_PREFIX_KAHAN, ALGO_RESIDENT, ALGO_PLAIN, ALGO_PREFIX_TMA, ALGO_ROWS, ALGO_FFT = \
-    range(9)
+ALGO_AUTO, ALGO_DIRECT, ALGO_PREFIX, ALGO_PREFIX_KAHAN, ALGO_RESIDENT, ALGO_PLAIN, ALGO_PREFIX_TMA, ALGO_ROWS, ALGO_FFT, \
+    ALGO_ACTIVE_SET = range(10)
 MAX_MODELS = 16
 
 

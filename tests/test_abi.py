@@ -53,6 +53,9 @@ def test_model_validation_on_host(lib):
     # lattice c_gamma of the constant kernel: 8 eps^2/(pi delta^4) h^2 |D|
     assert info.c_gamma == pytest.approx(8 * 0.03 ** 2 / (3.141592653589793 * (4 / 64) ** 4) / 64 ** 2 * 49)
     assert info.c_gamma == pytest.approx(1.7968, abs=1e-4)
+    # beta2 > 0: the active-set solver, chosen by AUTO or named
+    mfmc.Model(n=64, delta=4 / 64, beta2=0.05)
+    mfmc.Model(n=64, delta=4 / 64, beta2=0.05, algo=mfmc.ALGO_ACTIVE_SET)
     # a non-integer delta/h: the disc is { |z| <= 4.5 } and only the generic kernel serves it
     g = mfmc.Model(n=64, delta=4.5 / 64, eps=0.03)
     assert g.info().R == 4
@@ -61,7 +64,8 @@ def test_model_validation_on_host(lib):
         with pytest.raises(mfmc.MfmcError):
             mfmc.Model(n=64, delta=4.5 / 64, algo=algo)
     for bad in (dict(n=62, delta=4 / 62), dict(n=64, delta=33 / 64),
-                dict(n=64, delta=4 / 64, tau=0.0), dict(n=64, delta=4 / 64, beta2=0.05),
+                dict(n=64, delta=4 / 64, tau=0.0), dict(n=64, delta=4 / 64, beta2=-0.05),
+                dict(n=64, delta=4 / 64, beta2=0.05, bc=1), dict(n=64, delta=4 / 64, beta2=0.05, algo=1),
                 dict(n=64, delta=4 / 64, beta1=0.0), dict(n=64, delta=4 / 64, nsteps=-1),
                 dict(n=64, delta=4 / 64, kernel=1, delta_hf=0.0), dict(n=8, delta=4 / 8),
                 dict(n=64, delta=4 / 64, ic_base_n=96), dict(n=64, delta=4 / 64, algo=9)):
