@@ -602,8 +602,8 @@ def run_paper(args):
     """The paper's own nine models (Section 4, Table 1): truncated Gaussian kernel,
     delta_hf = 0.25, eps^2 = 0.00178, tau = 0.01, T = 1 (100 steps), the four-nuclei initial
     condition whose theta is the shared random input, h in {1/128, 1/88, 1/64} x delta in
-    {0.25, 0.1875, 0.125}, on the periodic lattice with beta2 = 0 (the paper's beta2 = 0.05
-    step is not built).  50 pilot samples on shared seeds give rho_{1,k} and sigma_k; the cost
+    {0.25, 0.1875, 0.125}, on the periodic lattice with beta2 = 0 by default (the paper's beta2 = 0.05
+    step is the active-set solver, --beta2 0.05).  50 pilot samples on shared seeds give rho_{1,k} and sigma_k; the cost
     of a model is GPU seconds per sample of a batched solve; the MFMC plan (policy 0) is printed
     for budgets of 10 .. 1000 C_1 together with the number of feasible subsets."""
     import numpy as np
@@ -614,15 +614,18 @@ def run_paper(args):
     levels = [(128, 0.25), (128, 0.1875), (88, 0.1875), (88, 0.25), (128, 0.125), (88, 0.125),
               (64, 0.1875), (64, 0.25), (64, 0.125)]
     common = dict(kernel=mfmc.KERNEL_GAUSSIAN, delta_hf=0.25, eps=math.sqrt(0.00178), tau=0.01, nsteps=100,
-                  ic=mfmc.IC_NUCLEI)
+                  ic=mfmc.IC_NUCLEI, beta2=args.beta2)
     models = [mfmc.Model(n=n, delta=d, **common) for n, d in levels]
     n_pilot = 50
     t = time.perf_counter()
     pilot = np.stack([mfmc.mfmc_solve_batch([m] * n_pilot, _seeds(base, n_pilot))[0] for m in models])
     t_pilot = time.perf_counter() - t
-    cost = [_batched_cost(mfmc, m, 256, base + 10 ** 7) for m in models]
-    fft_models = [mfmc.Model(n=n, delta=d, algo=mfmc.ALGO_FFT, **common) for n, d in levels]
-    fft_cost = [_batched_cost(mfmc, m, 256, base + 10 ** 7) for m in fft_models]
+    cost = [_batched_cost(mfmc, m, 256 if args.beta2 == 0 else 152, base + 10 ** 7) for m in models]
+    if args.beta2 == 0:
+        fft_models = [mfmc.Model(n=n, delta=d, algo=mfmc.ALGO_FFT, **common) for n, d in levels]
+        fft_cost = [_batched_cost(mfmc, m, 256, base + 10 ** 7) for m in fft_models]
+    else:
+        fft_cost = [None] * len(models)
     paper = {}
     gpath = os.path.join(ROOT, "tests", "golden", "table1_pilot_statistics.txt")
     if os.path.exists(gpath):
@@ -642,6 +645,8 @@ def run_paper(args):
         row = {"model": k + 1, "h": f"1/{n}", "delta": d, "delta_over_h": d * n, "disc_points": m.info().disc_points,
                "rho_1k": p0["rho_all"][k], "cost_ratio": cost[k] / cost[0], "sigma": p0["sigma_all"][k],
                "gpu_s_per_sample": cost[k], "fft_gpu_s_per_sample": fft_cost[k]}
+        if args.beta2 > 0:
+            row["algo"] = "active-set (beta2 > 0)"
         if k + 1 in paper:
             row["paper"] = paper[k + 1]
         table.append(row)
@@ -649,8 +654,9 @@ def run_paper(args):
             "higher_is_better": True, "data": "synthetic",
             "config": {"workload": "Section 4 models: Gaussian kernel delta_hf=0.25, eps^2=0.00178, tau=0.01, "
                                    "100 steps, nuclei IC, h in {1/128,1/88,1/64} x delta in {0.25,0.1875,0.125}, "
-                                   "periodic lattice, beta2 = 0; pilot 50 shared seeds",
-                       "algo": "generic weighted disc sum (the Gaussian kernel's only path)"},
+                                   f"periodic lattice, beta1 = 1, beta2 = {args.beta2:g}; pilot 50 shared seeds",
+                       "algo": "generic weighted disc sum" if args.beta2 == 0 else
+                               "active-set Newton-CG step (FP64, one CTA per sample)"},
             "pilot_wall_s": t_pilot, "table1": table, "plans": plans,
             "paper_C1_s": 63.089}
     print(json.dumps(line), flush=True)
@@ -667,7 +673,7 @@ def main():
                     help="single (the headline, default), or one of the other measured configurations")
     ap.add_argument("--validation", type=int, default=2048, help="hierarchy: HF samples of the validation mean")
     ap.add_argument("--requests", type=int, default=20000, help="serving: requests in the stream")
-    ap.add_argument("--oracle-steps", type=int, default=100, help="large: oracle steps of the precision sweep")
+    ap.add_argument("--beta2", type=float, default=0.0, help="paper: beta2 of the nine models (the paper's 0.05)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
