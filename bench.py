@@ -642,11 +642,11 @@ def run_paper(args):
     p0 = mfmc.mfmc_plan(pilot, cost, 100 * cost[0], 0).as_dict()
     table = []
     for k, ((n, d), m) in enumerate(zip(levels, models)):
+        algo_names = {1: "direct (generic)", 5: "plain", 8: "fft", 9: "active-set", 10: "weighted-tma"}
         row = {"model": k + 1, "h": f"1/{n}", "delta": d, "delta_over_h": d * n, "disc_points": m.info().disc_points,
+               "algo": algo_names.get(m.info().algo, str(m.info().algo)),
                "rho_1k": p0["rho_all"][k], "cost_ratio": cost[k] / cost[0], "sigma": p0["sigma_all"][k],
                "gpu_s_per_sample": cost[k], "fft_gpu_s_per_sample": fft_cost[k]}
-        if args.beta2 > 0:
-            row["algo"] = "active-set (beta2 > 0)"
         if k + 1 in paper:
             row["paper"] = paper[k + 1]
         table.append(row)
@@ -655,7 +655,7 @@ def run_paper(args):
             "config": {"workload": "Section 4 models: Gaussian kernel delta_hf=0.25, eps^2=0.00178, tau=0.01, "
                                    "100 steps, nuclei IC, h in {1/128,1/88,1/64} x delta in {0.25,0.1875,0.125}, "
                                    f"periodic lattice, beta1 = 1, beta2 = {args.beta2:g}; pilot 50 shared seeds",
-                       "algo": "generic weighted disc sum" if args.beta2 == 0 else
+                       "algo": "autotuned per model (see table1[].algo)" if args.beta2 == 0 else
                                "active-set Newton-CG step (FP64, one CTA per sample)"},
             "pilot_wall_s": t_pilot, "table1": table, "plans": plans,
             "paper_C1_s": 63.089}

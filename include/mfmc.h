@@ -92,7 +92,11 @@ typedef enum {
                                   a semismooth Newton (primal-dual active-set) solve of the
                                   resolvent equation with Jacobi-preconditioned CG, in FP64,
                                   one CTA per sample; the only algorithm for beta2 > 0 (AUTO
-                                  picks it), periodic only */
+                                  picks it), periodic only */,
+    MFMC_ALGO_WEIGHTED = 10    /* register-tiled weighted disc sum over TMA tiles: any radial
+                                  kernel (the Gaussian's fastest own path), integer delta/h,
+                                  either boundary; |D| FMAs per point without the prefix
+                                  form's shortcut, so the constant kernel prefers PREFIX_TMA */
 } mfmc_algo;
 
 /* One fidelity of the model (Section 2, Section 4).  The lattice is n x n on the unit

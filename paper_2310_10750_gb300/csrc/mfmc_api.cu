@@ -52,6 +52,7 @@ Model::~Model() {
     cudaFree(padB);
     cudaFree(d_status);
     cudaFree(d_wtab64);
+    cudaFree(d_wsq);
     cudaFree(as_buf);
     cudaFree(as_status);
     if (gexec) cudaGraphExecDestroy(gexec);
@@ -134,7 +135,7 @@ static mfmc_status validate_desc(const mfmc_model_desc &d, int *R_out) {
     if (!(d.ic_amp >= 0)) return fail(MFMC_EINVAL, "ic_amp must be >= 0");
     if (d.ic_base_n < 0 || (d.ic_base_n > 0 && (d.ic_base_n % d.n != 0 || d.ic_base_n > 16384)))
         return fail(MFMC_EINVAL, "ic_base_n must be 0 or a multiple of n up to 16384");
-    if ((int)d.algo < MFMC_ALGO_AUTO || (int)d.algo > MFMC_ALGO_ACTIVE_SET) return fail(MFMC_EINVAL, "unknown algo");
+    if ((int)d.algo < MFMC_ALGO_AUTO || (int)d.algo > MFMC_ALGO_WEIGHTED) return fail(MFMC_EINVAL, "unknown algo");
     *R_out = R;
     return MFMC_OK;
 }
@@ -203,6 +204,11 @@ mfmc_status mfmc_model_create(const mfmc_model_desc *desc, mfmc_model **out) {
         }
         m->chat64 = c64;
     }
+    // the weighted TMA form's table: what(|dx|, |dy|) inside the disc, zero outside
+    m->wsq.assign((size_t)(R + 1) * (R + 1), 0.f);
+    for (int dy = 0; dy <= R; ++dy)
+        for (int dx = 0; dx <= m->widths[dy]; ++dx)
+            m->wsq[(size_t)dy * (R + 1) + dx] = desc->kernel == MFMC_KERNEL_CONSTANT ? 1.f : m->wtab[dx * dx + dy * dy];
     m->algo = desc->algo;
     m->tuned = 0;
     if (m->algo != MFMC_ALGO_AUTO && !algo_supported(*m, m->algo)) {
@@ -366,7 +372,7 @@ mfmc_status mfmc_solve_fields(const mfmc_model *cm, const double *eps, const flo
 mfmc_status mfmc_solve_fields_algo(const mfmc_model *cm, int algo, const double *eps, const float *u0, size_t ns,
                                    float *uT, double *ubar, double *ooi, void *stream) {
     if (!cm) return fail(MFMC_EINVAL, "NULL model");
-    if (algo < MFMC_ALGO_AUTO || algo > MFMC_ALGO_ACTIVE_SET) return fail(MFMC_EINVAL, "unknown algo");
+    if (algo < MFMC_ALGO_AUTO || algo > MFMC_ALGO_WEIGHTED) return fail(MFMC_EINVAL, "unknown algo");
     return solve_impl(const_cast<mfmc_model *>(cm), algo, eps, u0, ns, uT, ubar, ooi, (cudaStream_t)stream);
 }
 

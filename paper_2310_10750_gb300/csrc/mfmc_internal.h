@@ -46,6 +46,8 @@ struct Model {
     double chat64 = 0.0;      // sum_z what_z of the FP64 weights
     // scratch of the beta2 > 0 solver (active_set.cu)
     double *d_wtab64 = nullptr;
+    std::vector<float> wsq;   // weighted TMA form: weights by (|dy|, |dx|), zero outside the disc
+    float *d_wsq = nullptr;
     double *as_buf = nullptr;
     size_t as_cap = 0;        // doubles
     int *as_status = nullptr;

@@ -321,6 +321,8 @@ bool algo_supported(const Model &m, int algo) {
     // beta2 > 0: only the active-set solver; it serves nothing else
     if (m.d.beta2 > 0.0 || algo == MFMC_ALGO_ACTIVE_SET) return m.d.beta2 > 0.0 && algo == MFMC_ALGO_ACTIVE_SET;
     if (algo == MFMC_ALGO_FFT) return m.d.bc == MFMC_BC_PERIODIC;  // any kernel, any radius
+    if (algo == MFMC_ALGO_WEIGHTED)  // any radial kernel, integer delta / h, either boundary
+        return m.integer_R && tma_launcher(m.R) != nullptr && tma_launcher(m.R)->v[kTmaWeighted].fn[3] != nullptr;
     // a non-integer delta / h: only the generic kernel, whose disc is set at run time
     if (!m.integer_R) return algo == MFMC_ALGO_PLAIN || algo == MFMC_ALGO_DIRECT;
     if (m.d.bc == MFMC_BC_COLLAR) {
@@ -503,8 +505,10 @@ mfmc_status run_solve_tma_core(const Model &m, int kahan, int variant, const Ste
     const TmaLauncher *TL = tma_launcher(m.R);
     if (!TL) return fail(MFMC_EINVAL, "no TMA kernel for R = %d", m.R);
     if (kahan) variant = 0;
-    if (variant < 0 || variant >= kTmaVariants || !TL->v[variant].fn[kahan ? 2 : 1])
+    const int fsel = variant == kTmaWeighted ? 3 : (kahan ? 2 : 1);
+    if (variant < 0 || variant > kTmaWeighted || !TL->v[variant].fn[fsel])
         return fail(MFMC_EINVAL, "TMA variant %d unavailable", variant);
+    if (fsel == 3 && !m.d_wsq) return fail(MFMC_EINVAL, "the weighted form needs the model's weight table");
     const TmaVariant *L = &TL->v[variant];
     const int n = m.d.n, G = (m.R + 3) & ~3, P = n + 2 * G;
     int tiles_x = 0;
@@ -544,7 +548,8 @@ mfmc_status run_solve_tma_core(const Model &m, int kahan, int variant, const Ste
         a.total = (int)total;
         a.last = (last && !steps_ps) ? 1 : 0;
         a.periodic = m.d.bc == MFMC_BC_PERIODIC;
-        mfmc_status s = L->fn[kahan ? 2 : 1](*src, a, grid, st);
+        a.wsq = fsel == 3 ? m.d_wsq : nullptr;
+        mfmc_status s = L->fn[fsel](*src, a, grid, st);
         if (s != MFMC_OK) return s;
         src = (dstbuf == b.padA) ? &b.mapA : &b.mapB;
         dstbuf = (dstbuf == b.padA) ? b.padB : b.padA;
@@ -560,7 +565,15 @@ mfmc_status run_solve_tma(Model &m, int kahan, int variant, const StepCoef *coef
     const TmaLauncher *TL = tma_launcher(m.R);
     if (!TL) return fail(MFMC_EINVAL, "no TMA kernel for R = %d", m.R);
     if (kahan) variant = 0;
-    if (variant < 0 || variant >= kTmaVariants) return fail(MFMC_EINVAL, "TMA variant %d unavailable", variant);
+    if (variant == kTmaWeighted) {
+        if (!algo_supported(m, MFMC_ALGO_WEIGHTED)) return fail(MFMC_EINVAL, "no weighted TMA kernel for R = %d", m.R);
+        if (!m.d_wsq) {
+            MFMC_CUDA(cudaMalloc((void **)&m.d_wsq, m.wsq.size() * sizeof(float)));
+            MFMC_CUDA(cudaMemcpy(m.d_wsq, m.wsq.data(), m.wsq.size() * sizeof(float), cudaMemcpyHostToDevice));
+        }
+    } else if (variant < 0 || variant >= kTmaVariants) {
+        return fail(MFMC_EINVAL, "TMA variant %d unavailable", variant);
+    }
     int tiles_x = 0;
     const int tiles = tma_tiles(m, variant, &tiles_x);
     mfmc_status s = ensure_pad_scratch(m, ns, TL->v[variant].sw, TL->v[variant].sh);
@@ -724,6 +737,7 @@ mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0,
         return MFMC_OK;
     }
     if (algo == MFMC_ALGO_FFT) return run_solve_fft(m, coef, u0, ns, nsteps, uT, ubar, ooi, st);
+    if (algo == MFMC_ALGO_WEIGHTED) return run_solve_tma(m, 0, kTmaWeighted, coef, u0, ns, nsteps, uT, ubar, ooi, st);
     if (algo == MFMC_ALGO_PREFIX_TMA)
         return run_solve_tma(m, 0, m.tma_variant, coef, u0, ns, nsteps, uT, ubar, ooi, st);
     if (algo == MFMC_ALGO_PREFIX_KAHAN) return run_solve_tma(m, 1, 0, coef, u0, ns, nsteps, uT, ubar, ooi, st);

@@ -29,6 +29,8 @@ struct TmaArgs {
     int n, P, tiles_x, tiles, total, last;
     int periodic;          // 1: periodic frame (outputs also stored as ghost images); 0: the frame
                            // is a fixed collar and only interior outputs are stored
+    const float *wsq;      // weighted sums (ALGO 3): [(R + 1) * (R + 1)] weights by (|dy|, |dx|), zero
+                           // outside the disc; nullptr for the prefix forms
 };
 
 // A sample takes part in step `a.step` while a.step <= its own step count.
@@ -96,14 +98,18 @@ __device__ __forceinline__ void put_ghost(float *d, int P, int row, int col, flo
 // One tile item: disc sums from the staged tile `s` (tile + halo, row pitch SW), the
 // update and projection, stores of the outputs (and ghost images), and the FP64 partial
 // of the OoI when `last`.  Shared by the single-fidelity and the mixed-fidelity kernels.
+template <int R, int RY, int TXT, int TYT>
+__device__ __forceinline__ void tma_tile_epilogue(const float *s, const TmaArgs &a, int sample, int tile, int x0,
+                                                  int y0, bool last, double *red, const StepCoef &cf,
+                                                  const float (&acc)[RY][4]);
+
 template <int R, int RY, int TXT, int TYT, int ALGO>
 __device__ __forceinline__ void tma_tile_compute(const float *s, const TmaArgs &a, int sample, int tile, int x0,
                                                  int y0, bool last, double *red) {
-    constexpr int RX = 4, R4 = (R + 3) & ~3, SW = 4 * TXT + 2 * R4, NT = TXT * TYT, WIN = RX + 2 * R4;
+    constexpr int RX = 4, R4 = (R + 3) & ~3, SW = 4 * TXT + 2 * R4, WIN = RX + 2 * R4;
     constexpr DiscRows<R> disc{};
     const int tid = threadIdx.x;
     const int tx = tid % TXT, ty = tid / TXT, ox = tx * RX, oy = ty * RY;
-    const int n = a.n, G = R4;
     const StepCoef cf = a.coef[sample];  // issued before the row loop, which hides its latency
     float acc[RY][RX];
     float cmp[ALGO == 2 ? RY : 1][RX];
@@ -150,7 +156,20 @@ __device__ __forceinline__ void tma_tile_compute(const float *s, const TmaArgs &
             }
         }
     }
+    tma_tile_epilogue<R, RY, TXT, TYT>(s, a, sample, tile, x0, y0, last, red, cf, acc);
+}
 
+// The update and projection of a thread's RX x RY outputs from their disc sums acc, the stores
+// of the outputs (and, on the periodic lattice, of their ghost images), and the FP64 partial of
+// the OoI when `last`.
+template <int R, int RY, int TXT, int TYT>
+__device__ __forceinline__ void tma_tile_epilogue(const float *s, const TmaArgs &a, int sample, int tile, int x0,
+                                                  int y0, bool last, double *red, const StepCoef &cf,
+                                                  const float (&acc)[RY][4]) {
+    constexpr int RX = 4, R4 = (R + 3) & ~3, SW = 4 * TXT + 2 * R4, NT = TXT * TYT;
+    const int tid = threadIdx.x;
+    const int tx = tid % TXT, ty = tid / TXT, ox = tx * RX, oy = ty * RY;
+    const int n = a.n, G = R4;
     double part = 0.0;
     const size_t nn = (size_t)n * n, PP = (size_t)a.P * a.P;
     // whether this thread's block has ghost images (touches the frame); uniform per thread
@@ -210,6 +229,53 @@ __device__ __forceinline__ void tma_tile_compute(const float *s, const TmaArgs &
     }
 }
 
+// Weighted disc sums (ALGO 3), S_i = sum_z what(|z|) u_{i+z} for any radial kernel: per |dy|
+// the R + 1 weights of |dx| = 0..R (zero beyond the disc's half-width, so every row runs the
+// full window) come from the table `wsm` in shared memory; each thread keeps its window of a
+// staged row in registers and pairs the points +dx and -dx under one weight.  The dy loop is not
+// unrolled (the code stays one row long for any R); dx, the output rows and columns are.
+template <int R, int RY, int TXT, int TYT>
+__device__ __forceinline__ void tma_tile_weighted(const float *s, const float *wsm, const TmaArgs &a, int sample,
+                                                  int tile, int x0, int y0, bool last, double *red) {
+    constexpr int RX = 4, R4 = (R + 3) & ~3, SW = 4 * TXT + 2 * R4, WIN = RX + 2 * R4;
+    const int tid = threadIdx.x;
+    const int tx = tid % TXT, ty = tid / TXT, ox = tx * RX, oy = ty * RY;
+    const StepCoef cf = a.coef[sample];
+    float acc[RY][RX];
+#pragma unroll
+    for (int j = 0; j < RY; ++j)
+#pragma unroll
+        for (int i = 0; i < RX; ++i) acc[j][i] = 0.f;
+#pragma unroll 1
+    for (int dy = -R; dy <= R; ++dy) {
+        const float *wr = wsm + (dy < 0 ? -dy : dy) * (R + 1);
+        float wv[R + 1];
+#pragma unroll
+        for (int q = 0; q <= R; ++q) wv[q] = wr[q];
+#pragma unroll
+        for (int j = 0; j < RY; ++j) {
+            const float4 *rowp = reinterpret_cast<const float4 *>(s + (oy + j + R + dy) * SW + ox);
+            float v[WIN];
+#pragma unroll
+            for (int q = 0; q < WIN / 4; ++q) {
+                const float4 t = rowp[q];
+                v[4 * q + 0] = t.x;
+                v[4 * q + 1] = t.y;
+                v[4 * q + 2] = t.z;
+                v[4 * q + 3] = t.w;
+            }
+#pragma unroll
+            for (int i = 0; i < RX; ++i) {
+                float t = fmaf(wv[0], v[R4 + i], acc[j][i]);
+#pragma unroll
+                for (int d = 1; d <= R; ++d) t = fmaf(wv[d], v[R4 + i + d] + v[R4 + i - d], t);
+                acc[j][i] = t;
+            }
+        }
+    }
+    tma_tile_epilogue<R, RY, TXT, TYT>(s, a, sample, tile, x0, y0, last, red, cf, acc);
+}
+
 // STAGES = 2: the next item's copy is issued before computing the current one;
 // STAGES = 1: it is issued after the current item is done (less shared memory per CTA,
 // so more CTAs per SM overlap their copies with each other's compute).
@@ -230,6 +296,9 @@ __device__ __forceinline__ void tma_step_body(const CUtensorMap &src_map, const 
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_flag = 0;
     }
+    float *wsm = base + STAGES * C::STAGE_FLOATS;  // ALGO 3: the weight table after the stages
+    if constexpr (ALGO == 3)
+        for (int i = tid; i < (R + 1) * (R + 1); i += NT) wsm[i] = a.wsq[i];
     __syncthreads();
 
     auto issue = [&](int item, int stage) {
@@ -267,7 +336,10 @@ __device__ __forceinline__ void tma_step_body(const CUtensorMap &src_map, const 
         const int x0 = (tile % a.tiles_x) * C::TX, y0 = (tile / a.tiles_x) * C::TY;
         const bool last = a.last || (a.steps_ps != nullptr && a.step == a.steps_ps[sample]);
 
-        tma_tile_compute<R, RY, TXT, TYT, ALGO>(s, a, sample, tile, x0, y0, last, red);
+        if constexpr (ALGO == 3)
+            tma_tile_weighted<R, RY, TXT, TYT>(s, wsm, a, sample, tile, x0, y0, last, red);
+        else
+            tma_tile_compute<R, RY, TXT, TYT, ALGO>(s, a, sample, tile, x0, y0, last, red);
         __syncthreads();  // every thread is done with this stage before it is refilled
         if (STAGES == 1 && tid == 0 && nxt < a.total) issue(nxt, 0);
     }
@@ -309,6 +381,9 @@ __global__ void pad_fields_kernel(const float *u, float *dst, int n, int G, size
 //   variant 6: 4 x 16 outputs per thread, 128 x 128 tile, 256 threads, one stage, <= 128 registers
 //   variant 7: 4 x 16 outputs per thread, 64 x 128 tile, 128 threads, one stage, <= 168 registers
 constexpr int kTmaVariants = 8;
+// The weighted form (ALGO 3) runs one more shape: 4 x 4 outputs per thread, 64 x 64 tile,
+// 256 threads, one stage (its window and weight registers leave room for only 4 output rows).
+constexpr int kTmaWeighted = kTmaVariants;
 
 template <int V>
 struct TmaShape;
@@ -344,18 +419,22 @@ template <>
 struct TmaShape<7> {
     static constexpr int RY = 16, TXT = 16, TYT = 8, STAGES = 1, MINB = 3;
 };
+template <>
+struct TmaShape<kTmaWeighted> {
+    static constexpr int RY = 4, TXT = 16, TYT = 16, STAGES = 1, MINB = 1;
+};
 
 typedef mfmc_status (*TmaFn)(const CUtensorMap &, const TmaArgs &, int grid, cudaStream_t);
 
 struct TmaVariant {
     int tx, ty, sw, sh, threads;
     size_t smem;
-    TmaFn fn[3];  // [algo]: unused, prefix, prefix-Kahan
+    TmaFn fn[4];  // [algo]: unused, prefix, prefix-Kahan, weighted
     int (*blocks_per_sm)();
 };
 
 struct TmaLauncher {
-    TmaVariant v[kTmaVariants];
+    TmaVariant v[kTmaVariants + 1];  // [kTmaWeighted]: the weighted form (fn[3])
 };
 
 template <int R, int V, int ALGO>
@@ -363,12 +442,13 @@ mfmc_status launch_tma(const CUtensorMap &map, const TmaArgs &a, int grid, cudaS
     using T = TmaShape<V>;
     using C = TmaCfg<R, T::RY, T::TXT, T::TYT, T::STAGES>;
     auto kern = tma_kernel_ptr<R, T::RY, T::TXT, T::TYT, ALGO, T::STAGES, T::MINB>();
+    constexpr size_t smem = C::SMEM + (ALGO == 3 ? (size_t)(R + 1) * (R + 1) * sizeof(float) : 0);
     static bool attr_done = false;
     if (!attr_done) {
-        MFMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+        MFMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr_done = true;
     }
-    kern<<<grid, T::TXT * T::TYT, C::SMEM, st>>>(map, a);
+    kern<<<grid, T::TXT * T::TYT, smem, st>>>(map, a);
     MFMC_LAUNCHED("tma_step launch 1");
     return MFMC_OK;
 }
@@ -377,10 +457,12 @@ template <int R, int V>
 int tma_blocks_per_sm() {
     using T = TmaShape<V>;
     using C = TmaCfg<R, T::RY, T::TXT, T::TYT, T::STAGES>;
-    auto k = tma_kernel_ptr<R, T::RY, T::TXT, T::TYT, 1, T::STAGES, T::MINB>();
+    constexpr int ALGO = V == kTmaWeighted ? 3 : 1;
+    constexpr size_t smem = C::SMEM + (ALGO == 3 ? (size_t)(R + 1) * (R + 1) * sizeof(float) : 0);
+    auto k = tma_kernel_ptr<R, T::RY, T::TXT, T::TYT, ALGO, T::STAGES, T::MINB>();
     int per = 0;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, T::TXT * T::TYT, C::SMEM);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, T::TXT * T::TYT, smem);
     (void)cudaGetLastError();  // a failed query must not be reported by a later launch check
     return e == cudaSuccess && per > 0 ? per : 1;
 }
@@ -397,11 +479,17 @@ TmaVariant make_tma_variant() {
     L.threads = T::TXT * T::TYT;
     L.smem = C::SMEM;
     L.fn[0] = nullptr;
-    L.fn[1] = &launch_tma<R, V, 1>;
-    if constexpr (KAHAN) {
-        L.fn[2] = &launch_tma<R, V, 2>;
+    if constexpr (V == kTmaWeighted) {
+        L.fn[1] = L.fn[2] = nullptr;
+        L.fn[3] = &launch_tma<R, V, 3>;
     } else {
-        L.fn[2] = nullptr;
+        L.fn[1] = &launch_tma<R, V, 1>;
+        L.fn[3] = nullptr;
+        if constexpr (KAHAN) {
+            L.fn[2] = &launch_tma<R, V, 2>;
+        } else {
+            L.fn[2] = nullptr;
+        }
     }
     L.blocks_per_sm = &tma_blocks_per_sm<R, V>;
     return L;
@@ -418,6 +506,7 @@ TmaLauncher make_tma_launcher() {
     L.v[5] = make_tma_variant<R, 5, false>();
     L.v[6] = make_tma_variant<R, 6, false>();
     L.v[7] = make_tma_variant<R, 7, false>();
+    L.v[kTmaWeighted] = make_tma_variant<R, kTmaWeighted, false>();
     return L;
 }
 
