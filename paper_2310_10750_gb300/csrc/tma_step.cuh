@@ -230,10 +230,11 @@ __device__ __forceinline__ void tma_tile_epilogue(const float *s, const TmaArgs 
 }
 
 // Weighted disc sums (ALGO 3), S_i = sum_z what(|z|) u_{i+z} for any radial kernel: per |dy|
-// the R + 1 weights of |dx| = 0..R (zero beyond the disc's half-width, so every row runs the
-// full window) come from the table `wsm` in shared memory; each thread keeps its window of a
-// staged row in registers and pairs the points +dx and -dx under one weight.  The dy loop is not
-// unrolled (the code stays one row long for any R); dx, the output rows and columns are.
+// the R + 1 weights of |dx| = 0..R (zero beyond the disc's half-width) come from the table `wsm`
+// in shared memory, and the dx loop runs in groups of four up to the row's half-width; each
+// thread keeps its window of a staged row in registers and pairs the points +dx and -dx under
+// one weight.  The dy loop is not unrolled (the code stays one row long for any R); dx, the
+// output rows and columns are.
 template <int R, int RY, int TXT, int TYT>
 __device__ __forceinline__ void tma_tile_weighted(const float *s, const float *wsm, const TmaArgs &a, int sample,
                                                   int tile, int x0, int y0, bool last, double *red) {
@@ -248,10 +249,16 @@ __device__ __forceinline__ void tma_tile_weighted(const float *s, const float *w
         for (int i = 0; i < RX; ++i) acc[j][i] = 0.f;
 #pragma unroll 1
     for (int dy = -R; dy <= R; ++dy) {
-        const float *wr = wsm + (dy < 0 ? -dy : dy) * (R + 1);
+        const int ady = dy < 0 ? -dy : dy;
+        const float *wr = wsm + ady * (R + 1);
         float wv[R + 1];
 #pragma unroll
         for (int q = 0; q <= R; ++q) wv[q] = wr[q];
+        // half-width of the disc in this row: weights beyond it are zero, so the dx loop stops at
+        // the first group of four that lies wholly outside (uniform across the CTA)
+        int hw = (int)sqrtf((float)(R * R - ady * ady));
+        while (hw * hw > R * R - ady * ady) --hw;
+        while ((hw + 1) * (hw + 1) <= R * R - ady * ady) ++hw;
 #pragma unroll
         for (int j = 0; j < RY; ++j) {
             const float4 *rowp = reinterpret_cast<const float4 *>(s + (oy + j + R + dy) * SW + ox);
@@ -265,11 +272,17 @@ __device__ __forceinline__ void tma_tile_weighted(const float *s, const float *w
                 v[4 * q + 3] = t.w;
             }
 #pragma unroll
-            for (int i = 0; i < RX; ++i) {
-                float t = fmaf(wv[0], v[R4 + i], acc[j][i]);
+            for (int i = 0; i < RX; ++i) acc[j][i] = fmaf(wv[0], v[R4 + i], acc[j][i]);
 #pragma unroll
-                for (int d = 1; d <= R; ++d) t = fmaf(wv[d], v[R4 + i + d] + v[R4 + i - d], t);
-                acc[j][i] = t;
+            for (int d0 = 1; d0 <= R; d0 += 4) {
+                if (d0 > hw) break;
+#pragma unroll
+                for (int i = 0; i < RX; ++i) {
+                    float t = acc[j][i];
+#pragma unroll
+                    for (int d = d0; d < d0 + 4 && d <= R; ++d) t = fmaf(wv[d], v[R4 + i + d] + v[R4 + i - d], t);
+                    acc[j][i] = t;
+                }
             }
         }
     }
