@@ -88,11 +88,13 @@ typedef enum {
                                   independent of the horizon; any kernel and radius,
                                   periodic boundary only; a comparison point for very large
                                   horizons that AUTO does not pick */,
-    MFMC_ALGO_ACTIVE_SET = 9   /* the beta2 > 0 step: per step the explicit convolution, then
-                                  a semismooth Newton (primal-dual active-set) solve of the
-                                  resolvent equation with Jacobi-preconditioned CG, in FP64,
-                                  one CTA per sample; the only algorithm for beta2 > 0 (AUTO
-                                  picks it), periodic only */,
+    MFMC_ALGO_ACTIVE_SET = 9   /* the beta2 > 0 step: per step the explicit convolution (FP64;
+                                  direct below 100 disc points, else by cuFFT), then a
+                                  semismooth Newton (primal-dual active-set) solve of the
+                                  resolvent equation: FP64 fields and residual, each correction
+                                  by FP32 CG preconditioned with a multigrid V-cycle; one CTA
+                                  per sample; the only algorithm for beta2 > 0 (AUTO picks
+                                  it), periodic only */,
     MFMC_ALGO_WEIGHTED = 10    /* register-tiled weighted disc sum over TMA tiles: any radial
                                   kernel (the Gaussian's fastest own path), integer delta/h,
                                   either boundary; |D| FMAs per point without the prefix

@@ -7,14 +7,27 @@
 //     F(w) = tau (beta1 - beta2 Lap_h) w + P_[-1,1]((w + g) / c_gamma) - u^{k-1} = 0,
 // by a semismooth Newton iteration (primal-dual active set): with the inactive set
 // I = { |w + g| < c_gamma }, J = tau (beta1 - beta2 Lap_h) + diag(1_I) / c_gamma is symmetric
-// positive definite and each Newton system is solved by conjugate gradients preconditioned by
-// one geometric multigrid V-cycle (periodic levels, damped Jacobi smoothing, full weighting and
-// bilinear prolongation: a symmetric positive definite preconditioner).  The iteration starts from the beta2 = 0 step and stops when the active set
-// repeats and max |F| is at rounding level.
+// positive definite.  The iteration starts from the beta2 = 0 step and stops when the active
+// set repeats and max |F| <= 1e-11.
 //
-// One CTA per sample runs every step of its solve; its vectors live in global scratch (FP64)
-// and the CTA's reductions use a fixed order.  No CTA waits on another.  Every loop is bounded;
-// a Newton or CG iteration that does not converge within its bound sets the status flag.
+// Precision: u, g, w and the residual F are FP64.  Each Newton correction d solves
+// J d = -F / max|F| in FP32 to a max-norm residual of 1e-5 (inexact Newton): F is piecewise
+// linear in w, so while the active set holds one correction cuts max|F| by about that factor,
+// and the FP64 residual of the next iteration sets the accuracy reached.  FP64 arithmetic runs
+// at a small fraction of the FP32 rate on GB300, so only the explicit convolution and the
+// residual stay in FP64.  The FP32 solve is conjugate gradients preconditioned by one geometric
+// multigrid V-cycle (periodic levels, damped Jacobi smoothing, full weighting and bilinear
+// prolongation: a symmetric positive definite preconditioner).
+//
+// The explicit disc sum is FP64 too: a direct sum for small discs, else through cuFFT (D2Z, a
+// product with the real spectrum of the radial weights, Z2D) between per-step launches, which
+// costs O(n^2 log n) FP64 operations per field instead of O(n^2 |D|).
+//
+// One CTA per sample runs every step of its solve (every step of one launch with the direct
+// sum; one step per launch with the spectral sum, the state staying in global scratch between
+// launches); its vectors live in global scratch and the CTA's reductions use a fixed order.  No CTA waits on another.  Every loop is bounded; a
+// Newton iteration that does not converge within its bound sets the status flag (a CG solve
+// that reaches its bound hands its iterate to the next Newton iteration).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,12 +38,15 @@ namespace mfmc {
 
 constexpr int AS_NT = 512;
 constexpr int AS_MAX_NEWTON = 60;
-constexpr int AS_MAX_CG = 40000;
-constexpr int AS_VECS = 10;  // u, g, w, d, r, p, q, inactive mask, z, t
+constexpr int AS_MAX_CG = 500;        // FP32 CG iterations per Newton correction
+constexpr float AS_CG_RTOL = 1e-5f;   // max |J d + F| / max |F| that ends a correction
+constexpr int AS_VEC64 = 3;           // u, g, w
+constexpr int AS_VEC32 = 7;           // d, r, p, q, inactive mask, z, t
 constexpr int AS_MAX_LEVELS = 8;
-constexpr int AS_NU = 2;        // damped-Jacobi sweeps before and after each coarse correction
+constexpr int AS_NU = 2;              // damped-Jacobi sweeps before and after each coarse correction
 constexpr int AS_NU_COARSE = 16;
-constexpr double AS_OMEGA = 0.8;
+constexpr float AS_OMEGA = 0.8f;
+constexpr int AS_SPECTRAL_MIN_DISC = 100;  // disc points from which the disc sum runs through cuFFT
 
 // Multigrid levels of the CG preconditioner: n_0 = n, halved while even and >= 16 (the coarsest
 // has >= 8 points per side).  Returns the level count; sizes[l] = n_l.
@@ -44,13 +60,14 @@ __host__ __device__ inline int as_levels(int n, int *sizes) {
     return L;
 }
 
-// Doubles of scratch per sample: the fine-level vectors and, per coarser level, v, f, r and m.
+// Doubles of scratch per sample: the FP64 fine-level vectors, then (two floats per double) the
+// FP32 fine-level vectors and, per coarser level, v, f, r and m.
 __host__ __device__ inline size_t as_per_sample(int n) {
     int sz[AS_MAX_LEVELS];
     const int L = as_levels(n, sz);
-    size_t t = (size_t)AS_VECS * n * n;
-    for (int l = 1; l < L; ++l) t += (size_t)4 * sz[l] * sz[l];
-    return t;
+    size_t f = (size_t)AS_VEC32 * n * n;
+    for (int l = 1; l < L; ++l) f += (size_t)4 * sz[l] * sz[l];
+    return (size_t)AS_VEC64 * n * n + (f + 1) / 2;
 }
 
 struct ActiveSetArgs {
@@ -64,18 +81,30 @@ struct ActiveSetArgs {
     const double *wtab;  // Gaussian: FP64 weight / eps^2 by r^2; nullptr: constant kernel
     int widths[kMaxR + 1];
     int n, R, nsteps;
+    int load;     // read u0 into the FP64 field first
+    int g_given;  // the disc sums of u are in g already (spectral form): no direct sum
+    int finish;   // write uT, ubar and the OoI after the last step
     size_t s0;
     double ahat, chat, tau, beta1, beta2, cF;
 };
 
+// Visit every lattice point (y, x) of an n x n level: warps walk rows, lanes walk columns, so no
+// point index is divided and a warp's loads are contiguous.
+template <typename Fn>
+__device__ __forceinline__ void as_for(int n, Fn f) {
+    for (int y = threadIdx.x >> 5; y < n; y += AS_NT / 32)
+        for (int x = threadIdx.x & 31; x < n; x += 32) f(y, x, y * n + x);
+}
+
 // Block-wide sum and maximum in a fixed order (warp trees, then the warps in order).
-__device__ double as_block_sum(double v, double *red) {
+template <typename T>
+__device__ T as_block_sum(T v, T *red) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     __syncthreads();  // the previous result has been read
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
+        T t = 0;
         for (int i = 0; i < AS_NT / 32; ++i) t += red[i];
         red[AS_NT / 32] = t;
     }
@@ -83,14 +112,18 @@ __device__ double as_block_sum(double v, double *red) {
     return red[AS_NT / 32];
 }
 
-__device__ double as_block_max(double v, double *red) {
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+template <typename T>
+__device__ T as_block_max(T v, T *red) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const T u = __shfl_down_sync(0xffffffffu, v, o);
+        v = v > u ? v : u;
+    }
     __syncthreads();
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < AS_NT / 32; ++i) t = fmax(t, red[i]);
+        T t = 0;
+        for (int i = 0; i < AS_NT / 32; ++i) t = t > red[i] ? t : red[i];
         red[AS_NT / 32] = t;
     }
     __syncthreads();
@@ -100,99 +133,96 @@ __device__ double as_block_max(double v, double *red) {
 __device__ __forceinline__ double as_clip(double v) { return v > 1.0 ? 1.0 : (v < -1.0 ? -1.0 : v); }
 
 // Periodic 5-point Laplacian of v at (y, x), times h^2.
-__device__ __forceinline__ double as_lap_h2(const double *v, int n, int y, int x) {
+template <typename T>
+__device__ __forceinline__ T as_lap_h2(const T *v, int n, int y, int x) {
     const int ym = y == 0 ? n - 1 : y - 1, yp = y == n - 1 ? 0 : y + 1;
     const int xm = x == 0 ? n - 1 : x - 1, xp = x == n - 1 ? 0 : x + 1;
-    return ((v[y * n + xp] + v[y * n + xm]) + (v[yp * n + x] + v[ym * n + x])) - 4.0 * v[y * n + x];
+    return ((v[y * n + xp] + v[y * n + xm]) + (v[yp * n + x] + v[ym * n + x])) - T(4) * v[y * n + x];
 }
 
-// The Newton operator on level l (spacing 2^l h, inactive mask m averaged from the fine one):
+// The Newton operator on level l (spacing 2^l h, inactive mask m averaged from the fine one), FP32:
 // J v = tau beta1 v + (tau beta2 / h_l^2)(4 v - neighbours) + m v / c_gamma.
 struct AsLevel {
-    double *v, *f, *r;
-    const double *m;
+    float *v, *f, *r;
+    const float *m;
     int n;
-    double tb2h;  // tau beta2 / h_l^2
+    float tb2h;  // tau beta2 / h_l^2
 };
 
-__device__ __forceinline__ double as_apply(const AsLevel &L, const double *v, int i, double tb1, double cg) {
-    const int n = L.n, y = i / n, x = i - y * n;
-    return tb1 * v[i] - L.tb2h * as_lap_h2(v, n, y, x) + L.m[i] * v[i] / cg;
-}
-
-__device__ __forceinline__ double as_diag(const AsLevel &L, int i, double tb1, double cg) {
-    return tb1 + 4.0 * L.tb2h + L.m[i] / cg;
+__device__ __forceinline__ float as_apply(const AsLevel &L, const float *v, int y, int x, int i, float tb1,
+                                          float icg) {
+    return tb1 * v[i] - L.tb2h * as_lap_h2(v, L.n, y, x) + L.m[i] * icg * v[i];
 }
 
 // nu damped-Jacobi sweeps on level L (v <- v + omega D^-1 (f - J v)), r as the temporary
-__device__ void as_smooth(const AsLevel &L, int nu, double tb1, double cg) {
-    const int nn = L.n * L.n;
+__device__ void as_smooth(const AsLevel &L, int nu, float tb1, float icg) {
+    const float dconst = tb1 + 4.0f * L.tb2h;
     for (int k = 0; k < nu; ++k) {
-        for (int i = threadIdx.x; i < nn; i += AS_NT) L.r[i] = L.f[i] - as_apply(L, L.v, i, tb1, cg);
+        as_for(L.n, [&](int y, int x, int i) { L.r[i] = L.f[i] - as_apply(L, L.v, y, x, i, tb1, icg); });
         __syncthreads();
-        for (int i = threadIdx.x; i < nn; i += AS_NT) L.v[i] += AS_OMEGA * L.r[i] / as_diag(L, i, tb1, cg);
+        as_for(L.n, [&](int, int, int i) { L.v[i] += AS_OMEGA * L.r[i] / (dconst + L.m[i] * icg); });
         __syncthreads();
     }
 }
 
 // One V-cycle z = B r (symmetric: damped Jacobi before and after each correction, full-weighting
 // restriction = prolongation transpose / 4), levels[0].f = r and levels[0].v = z.
-__device__ void as_vcycle(const AsLevel *lv, int nl, double tb1, double cg) {
+__device__ void as_vcycle(const AsLevel *lv, int nl, float tb1, float icg) {
     for (int l = 0; l < nl; ++l) {
         const AsLevel &L = lv[l];
-        const int nn = L.n * L.n;
-        for (int i = threadIdx.x; i < nn; i += AS_NT) L.v[i] = 0.0;
+        as_for(L.n, [&](int, int, int i) { L.v[i] = 0.0f; });
         __syncthreads();
         if (l == nl - 1) {
-            as_smooth(L, AS_NU_COARSE, tb1, cg);
+            as_smooth(L, AS_NU_COARSE, tb1, icg);
             break;
         }
-        as_smooth(L, AS_NU, tb1, cg);
-        for (int i = threadIdx.x; i < nn; i += AS_NT) L.r[i] = L.f[i] - as_apply(L, L.v, i, tb1, cg);
+        as_smooth(L, AS_NU, tb1, icg);
+        as_for(L.n, [&](int y, int x, int i) { L.r[i] = L.f[i] - as_apply(L, L.v, y, x, i, tb1, icg); });
         __syncthreads();
         const AsLevel &C = lv[l + 1];
-        const int nc = C.n, n = L.n;
-        for (int i = threadIdx.x; i < nc * nc; i += AS_NT) {  // full weighting at (2Y, 2X)
-            const int Y = i / nc, X = i - Y * nc, y = 2 * Y, x = 2 * X;
+        const int n = L.n;
+        as_for(C.n, [&](int Y, int X, int i) {  // full weighting at (2Y, 2X)
+            const int y = 2 * Y, x = 2 * X;
             const int ym = y == 0 ? n - 1 : y - 1, yp = y + 1, xm = x == 0 ? n - 1 : x - 1, xp = x + 1;
-            const double c = L.r[y * n + x];
-            const double e = (L.r[y * n + xm] + L.r[y * n + xp]) + (L.r[ym * n + x] + L.r[yp * n + x]);
-            const double k = (L.r[ym * n + xm] + L.r[ym * n + xp]) + (L.r[yp * n + xm] + L.r[yp * n + xp]);
-            C.f[i] = (4.0 * c + 2.0 * e + k) / 16.0;
-        }
+            const float c = L.r[y * n + x];
+            const float e = (L.r[y * n + xm] + L.r[y * n + xp]) + (L.r[ym * n + x] + L.r[yp * n + x]);
+            const float k = (L.r[ym * n + xm] + L.r[ym * n + xp]) + (L.r[yp * n + xm] + L.r[yp * n + xp]);
+            C.f[i] = (4.0f * c + 2.0f * e + k) * 0.0625f;
+        });
         __syncthreads();
     }
     for (int l = nl - 2; l >= 0; --l) {
         const AsLevel &L = lv[l], &C = lv[l + 1];
-        const int n = L.n, nc = C.n, nn = n * n;
-        for (int i = threadIdx.x; i < nn; i += AS_NT) {  // bilinear prolongation (periodic)
-            const int y = i / n, x = i - y * n, Y = y >> 1, X = x >> 1;
+        const int nc = C.n;
+        as_for(L.n, [&](int y, int x, int i) {  // bilinear prolongation (periodic)
+            const int Y = y >> 1, X = x >> 1;
             const int Y1 = (y & 1) ? (Y + 1 == nc ? 0 : Y + 1) : Y, X1 = (x & 1) ? (X + 1 == nc ? 0 : X + 1) : X;
-            const double v = 0.25 * ((C.v[Y * nc + X] + C.v[Y * nc + X1]) + (C.v[Y1 * nc + X] + C.v[Y1 * nc + X1]));
-            L.v[i] += v;
-        }
+            L.v[i] += 0.25f * ((C.v[Y * nc + X] + C.v[Y * nc + X1]) + (C.v[Y1 * nc + X] + C.v[Y1 * nc + X1]));
+        });
         __syncthreads();
-        as_smooth(L, AS_NU, tb1, cg);
+        as_smooth(L, AS_NU, tb1, icg);
     }
 }
 
 __global__ void __launch_bounds__(AS_NT) active_set_kernel(ActiveSetArgs a) {
-    __shared__ double red[AS_NT / 32 + 1];
+    __shared__ double red64[AS_NT / 32 + 1];
+    __shared__ float red32[AS_NT / 32 + 1];
     __shared__ int widths[kMaxR + 1];
     const size_t smp = a.s0 + blockIdx.x;
     const int n = a.n, R = a.R;
     const int nn = n * n;
     double *U = a.buf + smp * as_per_sample(n);
-    double *G = U + nn, *W = G + nn, *D = W + nn, *Rr = D + nn, *Pp = Rr + nn, *Q = Pp + nn, *M = Q + nn;
-    double *Z = M + nn, *T = Z + nn;
+    double *G = U + nn, *W = G + nn;
+    float *D = reinterpret_cast<float *>(W + nn);
+    float *Rr = D + nn, *Pp = Rr + nn, *Q = Pp + nn, *M = Q + nn, *Z = M + nn, *T = Z + nn;
     // multigrid levels of the preconditioner
     int sizes[AS_MAX_LEVELS];
     const int nl = as_levels(n, sizes);
     AsLevel lv[AS_MAX_LEVELS];
     {
-        double *q = T + nn;
+        float *q = T + nn;
         for (int l = 0; l < nl; ++l) {
-            const double tb2h_l = a.tau * a.beta2 * (double)sizes[l] * (double)sizes[l];
+            const float tb2h_l = (float)(a.tau * a.beta2 * (double)sizes[l] * (double)sizes[l]);
             if (l == 0) {
                 lv[0] = AsLevel{Z, Rr, T, M, n, tb2h_l};
             } else {
@@ -207,123 +237,136 @@ __global__ void __launch_bounds__(AS_NT) active_set_kernel(ActiveSetArgs a) {
     const double e2a = eps * eps * a.ahat;              // h^2 gamma = e2a * what
     const double cg = e2a * a.chat;                     // c_gamma
     const double tb1 = a.tau * a.beta1, tb2h = a.tau * a.beta2 * (double)n * (double)n;  // tau beta2 / h^2
-    for (int i = threadIdx.x; i < nn; i += AS_NT) U[i] = (double)a.u0[smp * (size_t)nn + i];
-    __syncthreads();
+    const float tb1f = (float)tb1, tb2hf = lv[0].tb2h, icgf = (float)(1.0 / cg);
+    if (a.load) {
+        as_for(n, [&](int, int, int i) { U[i] = (double)a.u0[smp * (size_t)nn + i]; });
+        __syncthreads();
+    }
     bool failed = false;
     for (int step = 1; step <= a.nsteps && !failed; ++step) {
-        // explicit part g = gamma * u + c_F u (direct sum over the disc, FP64)
-        for (int i = threadIdx.x; i < nn; i += AS_NT) {
-            const int y = i / n, x = i - y * n;
+        // explicit part g = gamma * u + c_F u (direct sum over the disc, FP64; R < n, so one
+        // wrap of each index suffices)
+        if (a.g_given) as_for(n, [&](int, int, int i) { G[i] = e2a * G[i] + a.cF * U[i]; });
+        else as_for(n, [&](int y, int x, int i) {
             double S = 0.0;
             for (int dy = -R; dy <= R; ++dy) {
-                const int w = widths[dy < 0 ? -dy : dy];
-                const double *row = U + (size_t)((y + dy + n) % n) * n;
-                for (int dx = -w; dx <= w; ++dx) {
-                    const double v = row[(x + dx + n) % n];
-                    S += a.wtab ? a.wtab[dx * dx + dy * dy] * v : v;
+                const int ady = dy < 0 ? -dy : dy, w = widths[ady];
+                int yy = y + dy;
+                yy += yy < 0 ? n : 0;
+                yy -= yy >= n ? n : 0;
+                const double *row = U + (size_t)yy * n;
+                int xx = x - w;
+                xx += xx < 0 ? n : 0;
+                if (a.wtab) {
+                    const double *wr = a.wtab + ady * ady;
+                    for (int dx = -w; dx <= w; ++dx) {
+                        S += wr[dx * dx] * row[xx];
+                        xx = xx == n - 1 ? 0 : xx + 1;
+                    }
+                } else {
+                    for (int dx = -w; dx <= w; ++dx) {
+                        S += row[xx];
+                        xx = xx == n - 1 ? 0 : xx + 1;
+                    }
                 }
             }
             G[i] = e2a * S + a.cF * U[i];
-        }
+        });
         __syncthreads();
         // start: the beta2 = 0 step, w = c_gamma u0 - g
-        for (int i = threadIdx.x; i < nn; i += AS_NT) {
+        as_for(n, [&](int, int, int i) {
             const double u0 = as_clip((U[i] + tb1 * G[i]) / (1.0 + tb1 * cg));
             W[i] = cg * u0 - G[i];
-        }
+        });
         __syncthreads();
         for (int it = 1;; ++it) {
-            // residual F(w), the inactive set, and the right-hand side r = -F of J d = -F
+            // FP64 residual F(w), the inactive set, and the right-hand side r = -F of J d = -F
             double fmax = 0.0, changed = 0.0;
-            for (int i = threadIdx.x; i < nn; i += AS_NT) {
-                const int y = i / n, x = i - y * n;
+            as_for(n, [&](int y, int x, int i) {
                 const double xv = (W[i] + G[i]) / cg;
-                const double inact = fabs(xv) < 1.0 ? 1.0 : 0.0;
+                const float inact = fabs(xv) < 1.0 ? 1.0f : 0.0f;
                 const double F = (tb1 * W[i] - tb2h * as_lap_h2(W, n, y, x)) + as_clip(xv) - U[i];
                 if (M[i] != inact) changed = 1.0;
                 M[i] = inact;
-                Rr[i] = -F;
-                D[i] = 0.0;
+                Rr[i] = (float)(-F);
+                D[i] = 0.0f;
                 fmax = fmax > fabs(F) ? fmax : fabs(F);
-            }
-            fmax = as_block_max(fmax, red);
-            changed = as_block_max(changed, red);
+            });
+            fmax = as_block_max(fmax, red64);
+            changed = as_block_max(changed, red64);
             if (it > 1 && changed == 0.0 && fmax <= 1e-11) break;
             if (it > AS_MAX_NEWTON) {
                 failed = true;
                 break;
             }
-            // the inactive mask on the coarse levels (2 x 2 averages)
+            if (fmax == 0.0) continue;  // F = 0 with a new active set: the next pass confirms it
+            // scale to max |r| = 1, and the inactive mask on the coarse levels (2 x 2 averages)
+            const float sc = (float)(1.0 / fmax);
+            as_for(n, [&](int, int, int i) { Rr[i] *= sc; });
             for (int l = 1; l < nl; ++l) {
-                const int nc = sizes[l], nf = sizes[l - 1];
-                double *mc = const_cast<double *>(lv[l].m);
-                const double *mf = lv[l - 1].m;
-                for (int i = threadIdx.x; i < nc * nc; i += AS_NT) {
-                    const int Y = i / nc, X = i - Y * nc;
-                    mc[i] = 0.25 * ((mf[2 * Y * nf + 2 * X] + mf[2 * Y * nf + 2 * X + 1]) +
-                                    (mf[(2 * Y + 1) * nf + 2 * X] + mf[(2 * Y + 1) * nf + 2 * X + 1]));
-                }
+                const int nf = sizes[l - 1];
+                float *mc = const_cast<float *>(lv[l].m);
+                const float *mf = lv[l - 1].m;
+                as_for(sizes[l], [&](int Y, int X, int i) {
+                    mc[i] = 0.25f * ((mf[2 * Y * nf + 2 * X] + mf[2 * Y * nf + 2 * X + 1]) +
+                                     (mf[(2 * Y + 1) * nf + 2 * X] + mf[(2 * Y + 1) * nf + 2 * X + 1]));
+                });
                 __syncthreads();
             }
-            // CG on J d = r preconditioned by one multigrid V-cycle, d = 0 at the start
-            as_vcycle(lv, nl, tb1, cg);  // Z = B Rr
-            double rz = 0.0;
-            for (int i = threadIdx.x; i < nn; i += AS_NT) {
+            __syncthreads();
+            // FP32 CG on J d = r preconditioned by one multigrid V-cycle, d = 0 at the start
+            as_vcycle(lv, nl, tb1f, icgf);  // Z = B Rr
+            float rz = 0.0f;
+            as_for(n, [&](int, int, int i) {
                 Pp[i] = Z[i];
                 rz += Rr[i] * Z[i];
-            }
-            rz = as_block_sum(rz, red);
-            const double rtol = fmax * 1e-6 > 1e-13 ? fmax * 1e-6 : 1e-13;
+            });
+            rz = as_block_sum(rz, red32);
             for (int k = 1;; ++k) {
-                double pq = 0.0;
-                for (int i = threadIdx.x; i < nn; i += AS_NT) {
-                    const int y = i / n, x = i - y * n;
-                    const double q = (tb1 * Pp[i] - tb2h * as_lap_h2(Pp, n, y, x)) + M[i] * Pp[i] / cg;
+                float pq = 0.0f;
+                as_for(n, [&](int y, int x, int i) {
+                    const float q = (tb1f * Pp[i] - tb2hf * as_lap_h2(Pp, n, y, x)) + M[i] * icgf * Pp[i];
                     Q[i] = q;
                     pq += Pp[i] * q;
-                }
-                pq = as_block_sum(pq, red);
-                const double alpha = pq > 0.0 ? rz / pq : 0.0;
-                double rmax = 0.0;
-                for (int i = threadIdx.x; i < nn; i += AS_NT) {
+                });
+                pq = as_block_sum(pq, red32);
+                const float alpha = pq > 0.0f ? rz / pq : 0.0f;
+                float rmax = 0.0f;
+                as_for(n, [&](int, int, int i) {
                     D[i] += alpha * Pp[i];
                     Rr[i] -= alpha * Q[i];
-                    rmax = rmax > fabs(Rr[i]) ? rmax : fabs(Rr[i]);
-                }
-                rmax = as_block_max(rmax, red);
-                if (rmax <= rtol || pq <= 0.0) break;
-                if (k >= AS_MAX_CG) {
-                    failed = true;
-                    break;
-                }
+                    rmax = rmax > fabsf(Rr[i]) ? rmax : fabsf(Rr[i]);
+                });
+                rmax = as_block_max(rmax, red32);
+                if (rmax <= AS_CG_RTOL || !(pq > 0.0f) || !(rz > 0.0f) || k >= AS_MAX_CG) break;
                 __syncthreads();
-                as_vcycle(lv, nl, tb1, cg);  // Z = B Rr
-                double rz2 = 0.0;
-                for (int i = threadIdx.x; i < nn; i += AS_NT) rz2 += Rr[i] * Z[i];
-                rz2 = as_block_sum(rz2, red);
-                const double beta = rz2 / rz;
+                as_vcycle(lv, nl, tb1f, icgf);  // Z = B Rr
+                float rz2 = 0.0f;
+                as_for(n, [&](int, int, int i) { rz2 += Rr[i] * Z[i]; });
+                rz2 = as_block_sum(rz2, red32);
+                const float beta = rz2 / rz;
                 rz = rz2;
-                for (int i = threadIdx.x; i < nn; i += AS_NT) Pp[i] = Z[i] + beta * Pp[i];
+                as_for(n, [&](int, int, int i) { Pp[i] = Z[i] + beta * Pp[i]; });
                 __syncthreads();
             }
-            if (failed) break;
-            for (int i = threadIdx.x; i < nn; i += AS_NT) W[i] += D[i];
+            as_for(n, [&](int, int, int i) { W[i] += fmax * (double)D[i]; });
             __syncthreads();
         }
         if (failed) break;
-        for (int i = threadIdx.x; i < nn; i += AS_NT) U[i] = as_clip((W[i] + G[i]) / cg);
+        as_for(n, [&](int, int, int i) { U[i] = as_clip((W[i] + G[i]) / cg); });
         __syncthreads();
     }
     if (failed) {
         if (threadIdx.x == 0) atomicExch(a.status, 1);
         return;
     }
+    if (!a.finish) return;
     double s = 0.0;
-    for (int i = threadIdx.x; i < nn; i += AS_NT) {
+    as_for(n, [&](int, int, int i) {
         s += U[i];
         if (a.uT) a.uT[smp * (size_t)nn + i] = (float)U[i];
-    }
-    s = as_block_sum(s, red);
+    });
+    s = as_block_sum(s, red64);
     if (threadIdx.x == 0) {
         const double mean = s / (double)nn;
         if (a.ubar) a.ubar[smp] = mean;
@@ -361,19 +404,33 @@ mfmc_status run_solve_active_set(Model &m, const double *eps_dev, const float *u
     for (int d = 0; d <= kMaxR; ++d) a.widths[d] = d <= m.R ? m.widths[d] : 0;
     a.n = m.d.n;
     a.R = m.R;
-    a.nsteps = nsteps;
     a.ahat = m.ahat;
     a.chat = m.chat64;
     a.tau = m.d.tau;
     a.beta1 = m.d.beta1;
     a.beta2 = m.d.beta2;
     a.cF = m.d.c_F;
-    for (size_t o = 0; o < ns; o += 65535) {
-        a.s0 = o;
-        active_set_kernel<<<(unsigned)std::min<size_t>(65535, ns - o), AS_NT, 0, st>>>(a);
-        MFMC_LAUNCHED("active_set launch 1");
+    auto launch = [&](int load, int steps, int g_given, int finish) -> mfmc_status {
+        a.load = load;
+        a.nsteps = steps;
+        a.g_given = g_given;
+        a.finish = finish;
+        for (size_t o = 0; o < ns; o += 65535) {
+            a.s0 = o;
+            active_set_kernel<<<(unsigned)std::min<size_t>(65535, ns - o), AS_NT, 0, st>>>(a);
+            MFMC_LAUNCHED("active_set launch 1");
+        }
+        return MFMC_OK;
+    };
+    if (m.disc < AS_SPECTRAL_MIN_DISC || !fft64_available()) return launch(1, nsteps, 0, 1);
+    // spectral disc sums: g of sample s (at u + n^2 in its block) from u, between one-step launches
+    const size_t nn = (size_t)m.d.n * m.d.n;
+    s = launch(1, 0, 0, nsteps == 0);
+    for (int k = 1; k <= nsteps && s == MFMC_OK; ++k) {
+        s = fft64_disc_sums(m, m.as_buf, per, m.as_buf + nn, per, ns, st);
+        if (s == MFMC_OK) s = launch(0, 1, 1, k == nsteps);
     }
-    return MFMC_OK;
+    return s;
 }
 
 }  // namespace mfmc

@@ -11,6 +11,8 @@
 #include <dlfcn.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstdint>
 #include <mutex>
 #include <vector>
 
@@ -24,6 +26,8 @@ struct CufftApi {
     cufftResult (*plan_many)(cufftHandle *, int, int *, int *, int, int, int *, int, int, cufftType, int) = nullptr;
     cufftResult (*exec_r2c)(cufftHandle, cufftReal *, cufftComplex *) = nullptr;
     cufftResult (*exec_c2r)(cufftHandle, cufftComplex *, cufftReal *) = nullptr;
+    cufftResult (*exec_d2z)(cufftHandle, cufftDoubleReal *, cufftDoubleComplex *) = nullptr;
+    cufftResult (*exec_z2d)(cufftHandle, cufftDoubleComplex *, cufftDoubleReal *) = nullptr;
     cufftResult (*set_stream)(cufftHandle, cudaStream_t) = nullptr;
     cufftResult (*destroy)(cufftHandle) = nullptr;
 };
@@ -40,12 +44,15 @@ static const CufftApi &cufft_api() {
         api.exec_c2r = reinterpret_cast<decltype(api.exec_c2r)>(dlsym(h, "cufftExecC2R"));
         api.set_stream = reinterpret_cast<decltype(api.set_stream)>(dlsym(h, "cufftSetStream"));
         api.destroy = reinterpret_cast<decltype(api.destroy)>(dlsym(h, "cufftDestroy"));
+        api.exec_d2z = reinterpret_cast<decltype(api.exec_d2z)>(dlsym(h, "cufftExecD2Z"));
+        api.exec_z2d = reinterpret_cast<decltype(api.exec_z2d)>(dlsym(h, "cufftExecZ2D"));
         api.ok = api.plan_many && api.exec_r2c && api.exec_c2r && api.set_stream && api.destroy;
     });
     return api;
 }
 
 bool fft_available() { return cufft_api().ok; }
+bool fft64_available() { return cufft_api().ok && cufft_api().exec_d2z && cufft_api().exec_z2d; }
 
 // Per-model state: plans for the last batch size, the spectrum of K and the buffers.
 struct FftState {
@@ -225,6 +232,115 @@ mfmc_status run_solve_fft(Model &m, const StepCoef *coef, const float *u0, size_
         fft_ooi_kernel<<<g, 256, 0, st>>>(src + o * nn, nn, ubar ? ubar + o : nullptr, ooi ? ooi + o : nullptr);
     }
     MFMC_LAUNCHED("fft_solver launch 3");
+    return MFMC_OK;
+}
+
+// ---- FP64 disc sums for the beta2 > 0 solver ----------------------------------------------
+// S_i = sum_{z in D} w_z u_{i+z} for a batch of FP64 fields held in strided per-sample blocks,
+// as IFFT(FFT(u) * Khat).  The weights are radial, hence even in dx and in dy, so
+// Khat(kx, ky) = sum_z w_z cos(2 pi kx dx / n) cos(2 pi ky dy / n) is real; it is formed on the
+// host from a table of cos(2 pi j / n), row by row: C(|dy|, kx) = sum_dx w(dx, dy) cos(...),
+// then Khat = sum_dy C(|dy|, kx) cos(...), scaled by 1 / n^2 (the inverse is unnormalised).
+struct Fft64State {
+    int n = 0;
+    size_t batch = 0, u_dist = 0, s_dist = 0;
+    cufftHandle fwd = 0, inv = 0;
+    bool have_plans = false;
+    double *khat = nullptr;              // [n][n/2 + 1]
+    cufftDoubleComplex *spec = nullptr;  // [batch][n][n/2 + 1]
+};
+
+void fft64_release(Fft64State *f) {
+    if (!f) return;
+    const CufftApi &api = cufft_api();
+    if (f->have_plans && api.ok) {
+        api.destroy(f->fwd);
+        api.destroy(f->inv);
+    }
+    cudaFree(f->khat);
+    cudaFree(f->spec);
+    delete f;
+}
+
+__global__ void fft64_multiply_kernel(cufftDoubleComplex *spec, const double *khat, size_t per, size_t total) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const double k = khat[i % per];
+        spec[i].x *= k;
+        spec[i].y *= k;
+    }
+}
+
+mfmc_status fft64_disc_sums(Model &m, const double *u, size_t u_dist, double *S, size_t s_dist, size_t ns,
+                            cudaStream_t st) {
+    const CufftApi &api = cufft_api();
+    if (!fft64_available()) return fail(MFMC_ECUDA, "cuFFT (libcufft.so) could not be loaded");
+    if (ns == 0) return MFMC_OK;
+    const int n = m.d.n, nh1 = n / 2 + 1;
+    const size_t nh = (size_t)n * nh1;
+    if (ns > (size_t)INT32_MAX || u_dist > (size_t)INT32_MAX || s_dist > (size_t)INT32_MAX)
+        return fail(MFMC_EINVAL, "batch too large for the spectral disc sums");
+    if (!m.fft64) m.fft64 = new Fft64State();
+    Fft64State &f = *m.fft64;
+    if (f.n != n) {
+        std::vector<double> cs(n), C((size_t)(m.R + 1) * nh1, 0.0), K(nh, 0.0);
+        for (int j = 0; j < n; ++j) cs[j] = std::cos(2.0 * M_PI * j / n);
+        for (int ady = 0; ady <= m.R; ++ady) {
+            const int w = m.widths[ady];
+            for (int kx = 0; kx < nh1; ++kx) {
+                double c = 0.0;
+                for (int dx = -w; dx <= w; ++dx) {
+                    const double wt = m.d.kernel == MFMC_KERNEL_CONSTANT ? 1.0 : m.wtab64[dx * dx + ady * ady];
+                    c += wt * cs[(size_t)(((long)kx * dx) % n + n) % n];
+                }
+                C[(size_t)ady * nh1 + kx] = c;
+            }
+        }
+        const double inv_nn = 1.0 / ((double)n * n);
+        for (int ky = 0; ky < n; ++ky)
+            for (int kx = 0; kx < nh1; ++kx) {
+                double k = 0.0;
+                for (int dy = -m.R; dy <= m.R; ++dy)
+                    k += C[(size_t)(dy < 0 ? -dy : dy) * nh1 + kx] * cs[(size_t)(((long)ky * dy) % n + n) % n];
+                K[(size_t)ky * nh1 + kx] = k * inv_nn;
+            }
+        cudaFree(f.khat);
+        f.khat = nullptr;
+        MFMC_CUDA(cudaMalloc((void **)&f.khat, nh * sizeof(double)));
+        MFMC_CUDA(cudaMemcpy(f.khat, K.data(), nh * sizeof(double), cudaMemcpyHostToDevice));
+        f.n = n;
+        f.batch = 0;
+    }
+    if (!f.have_plans || f.batch != ns || f.u_dist != u_dist || f.s_dist != s_dist) {
+        MFMC_CUDA(cudaStreamSynchronize(st));
+        if (f.have_plans) {
+            api.destroy(f.fwd);
+            api.destroy(f.inv);
+        }
+        f.have_plans = false;
+        cudaFree(f.spec);
+        f.spec = nullptr;
+        int dims[2] = {n, n}, emb_r[2] = {n, n}, emb_c[2] = {n, nh1};
+        MFMC_CUFFT(api.plan_many(&f.fwd, 2, dims, emb_r, 1, (int)u_dist, emb_c, 1, (int)nh, CUFFT_D2Z, (int)ns));
+        cufftResult r = api.plan_many(&f.inv, 2, dims, emb_c, 1, (int)nh, emb_r, 1, (int)s_dist, CUFFT_Z2D, (int)ns);
+        if (r != CUFFT_SUCCESS) {
+            api.destroy(f.fwd);
+            return fail(MFMC_ECUDA, "cufftPlanMany (FP64 inverse) failed (%d)", (int)r);
+        }
+        f.have_plans = true;
+        MFMC_CUDA(cudaMalloc((void **)&f.spec, ns * nh * sizeof(cufftDoubleComplex)));
+        f.batch = ns;
+        f.u_dist = u_dist;
+        f.s_dist = s_dist;
+    }
+    MFMC_CUFFT(api.set_stream(f.fwd, st));
+    MFMC_CUFFT(api.set_stream(f.inv, st));
+    // cuFFT's D2Z input is non-const in its signature; an out-of-place transform does not write it
+    MFMC_CUFFT(api.exec_d2z(f.fwd, const_cast<double *>(u), f.spec));
+    const size_t tot = ns * nh;
+    fft64_multiply_kernel<<<(unsigned)std::min<size_t>((tot + 255) / 256, 152 * 64), 256, 0, st>>>(f.spec, f.khat,
+                                                                                                nh, tot);
+    MFMC_LAUNCHED("fft_solver launch 4");
+    MFMC_CUFFT(api.exec_z2d(f.inv, f.spec, S));
     return MFMC_OK;
 }
 

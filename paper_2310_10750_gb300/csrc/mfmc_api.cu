@@ -58,6 +58,7 @@ Model::~Model() {
     if (gexec) cudaGraphExecDestroy(gexec);
     if (stream) cudaStreamDestroy(stream);
     fft_release(fft);
+    fft64_release(fft64);
 }
 
 template <typename T>

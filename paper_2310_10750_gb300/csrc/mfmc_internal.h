@@ -30,6 +30,9 @@ struct StepCoef {
 struct FftState;  // spectral-convolution state of the FFT path (fft_solver.cu)
 void fft_release(FftState *f);
 bool fft_available();
+struct Fft64State;  // FP64 spectral disc sums of the beta2 > 0 solver (fft_solver.cu)
+void fft64_release(Fft64State *f);
+bool fft64_available();
 
 // A validated model: descriptor plus derived constants.
 struct Model {
@@ -88,6 +91,7 @@ struct Model {
     std::vector<uintptr_t> gkey;
     int graphs_off = 0;
     FftState *fft = nullptr;  // created by the first FFT-path solve
+    Fft64State *fft64 = nullptr;  // created by the first spectral beta2 > 0 solve
     ~Model();
 };
 
@@ -193,8 +197,12 @@ mfmc_status run_solve_tma(Model &m, int kahan, int variant, const StepCoef *coef
 // The spectral (cuFFT) form of the disc sum, periodic lattice, any kernel and radius.
 mfmc_status run_solve_fft(Model &m, const StepCoef *coef, const float *u0, size_t ns, int nsteps, float *uT,
                           double *ubar, double *ooi, cudaStream_t st);
-// The beta2 > 0 step (semismooth Newton with preconditioned CG per step, FP64, one CTA per
-// sample); eps_dev: per-sample eps (FP64) or nullptr for the nominal eps.
+// FP64 disc sums S = sum_z w_z u_{i+z} of ns fields by cuFFT: u and S are strided per-sample
+// blocks (u_dist, s_dist doubles apart); S may not overlap u.
+mfmc_status fft64_disc_sums(Model &m, const double *u, size_t u_dist, double *S, size_t s_dist, size_t ns,
+                            cudaStream_t st);
+// The beta2 > 0 step (semismooth Newton per step: FP64 fields and residual, FP32 preconditioned
+// CG corrections, one CTA per sample); eps_dev: per-sample eps (FP64) or nullptr for the nominal eps.
 mfmc_status run_solve_active_set(Model &m, const double *eps_dev, const float *u0, size_t ns, int nsteps,
                                  float *uT, double *ubar, double *ooi, cudaStream_t st);
 // Whether an algorithm can run this model.

@@ -3,7 +3,9 @@
 Both sides work in FP64 from the same FP32-rounded initial field and solve each step's
 resolvent equation to max |F| <= 1e-11 (GPU: Newton with preconditioned CG; oracle: Newton with
 sparse direct solves), so a step agrees to about 1e-11 / c_gamma; over k steps the map is
-Lipschitz with constant about 1, so fields agree to k * 1e-9 and the OoI to 1e-8 relative."""
+Lipschitz with constant about 1, so fields agree to k * 1e-9 and the OoI to 1e-8 relative.
+The GPU forms the explicit disc sum directly for discs of fewer than 100 points and through an
+FP64 cuFFT convolution otherwise; the cases below cover both sides."""
 import math
 
 import numpy as np
@@ -101,3 +103,28 @@ def test_active_set_stationary_batch_and_rejections(gpu_lib):
         assert abs(f[i] - fr) <= 1e-8 * fr
     with pytest.raises(mf.MfmcError):      # the mixed-fidelity call serves beta2 = 0 only
         mf.mfmc_solve_batch_mixed([g], [1])
+
+
+SUM_CASES = [dict(n=48, delta=5 / 48, kernel=0),                          # 81 disc points: direct sum
+             dict(n=48, delta=6 / 48, kernel=0),                          # 113 points: spectral sum
+             dict(n=88, delta=0.1875, kernel=1, delta_hf=0.25)]           # delta/h = 16.5: spectral
+
+
+@pytest.mark.parametrize("case", range(len(SUM_CASES)))
+def test_active_set_direct_and_spectral_disc_sums(gpu_lib, case):
+    mf = gpu_lib
+    steps = 8
+    kw = dict(SUM_CASES[case], eps=0.04219, tau=0.01, nsteps=steps, ic=2, beta2=0.05)
+    g = mf.Model(**kw)
+    o = O.OracleModel(**{k: v for k, v in kw.items() if k != "beta2"})
+    seeds = np.arange(3, dtype=np.uint64) + 300 + 7 * case
+    u0, uT, f, ubar = gpu_solve(mf, g, seeds)
+    for i, s in enumerate(seeds):
+        fr, mean, ur, _ = B2.solve_sample(o, int(s), 0.05, steps)
+        assert abs(f[i] - fr) <= 1e-8 * fr
+        assert abs(ubar[i] - mean) <= 2e-8
+        assert np.abs(uT[i] - ur).max() <= 1e-6
+    one = mf.Model(**dict(kw, nsteps=1))
+    u0, u1, _, _ = gpu_solve(mf, one, seeds[:1])
+    ref, _, _ = B2.step(o, u0[0], 0.04219, 0.05)
+    assert np.abs(u1[0] - ref).max() <= 1e-7
