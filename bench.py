@@ -624,7 +624,13 @@ def run_paper(args):
     t = time.perf_counter()
     pilot = np.stack([mfmc.mfmc_solve_batch([m] * n_pilot, _seeds(base, n_pilot))[0] for m in models])
     t_pilot = time.perf_counter() - t
-    cost = [_batched_cost(mfmc, m, 256 if args.beta2 == 0 else 152, base + 10 ** 7) for m in models]
+    cost, iters = [], []
+    for m in models:
+        ns_cost = 256 if args.beta2 == 0 else 152
+        cost.append(_batched_cost(mfmc, m, ns_cost, base + 10 ** 7))
+        if args.beta2 > 0:  # Newton and CG iterations per sample and step of the timed solve
+            nw, cgi = mfmc.mfmc_model_solver_stats(m)
+            iters.append((nw / (ns_cost * m.nsteps), cgi / (ns_cost * m.nsteps)))
     if args.beta2 == 0:
         fft_models = [mfmc.Model(n=n, delta=d, algo=mfmc.ALGO_FFT, **common) for n, d in levels]
         fft_cost = [_batched_cost(mfmc, m, 256, base + 10 ** 7) for m in fft_models]
@@ -651,6 +657,8 @@ def run_paper(args):
                "algo": algo_names.get(m.info().algo, str(m.info().algo)),
                "rho_1k": p0["rho_all"][k], "cost_ratio": cost[k] / cost[0], "sigma": p0["sigma_all"][k],
                "gpu_s_per_sample": cost[k], "fft_gpu_s_per_sample": fft_cost[k]}
+        if iters:
+            row["newton_per_step"], row["cg_per_step"] = iters[k]
         if k + 1 in paper:
             row["paper"] = paper[k + 1]
         table.append(row)

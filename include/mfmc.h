@@ -168,9 +168,11 @@ const char *mfmc_version(void);
 const char *mfmc_last_error(void);
 
 /* Validate a descriptor and create a model handle (host-side only; no device work).
- * Returns MFMC_EINVAL for: NULL pointers, n % 4 != 0 or n < 8, delta/h not an
- * integer in [1, 32], tau <= 0, beta1 <= 0, beta2 != 0, eps <= 0, c_F < 0, nsteps < 0,
- * an unknown kernel/ic/algo/bc, or a GAUSSIAN kernel with delta_hf <= 0. */
+ * Returns MFMC_EINVAL for: NULL pointers, n % 4 != 0 or n outside [8, 16384],
+ * floor(delta/h) outside [1, 32] or a disc wider than n, tau <= 0, beta1 <= 0, beta2 < 0,
+ * beta2 > 0 off the periodic lattice, eps <= 0 (without a valid eps range), c_F < 0,
+ * nsteps < 0, an unknown kernel/ic/algo/bc, a collar value outside [-1, 1], a GAUSSIAN
+ * kernel with delta_hf <= 0, or an algo that cannot run the model. */
 mfmc_status mfmc_model_create(const mfmc_model_desc *desc, mfmc_model **out);
 
 /* Release a model handle (NULL is ignored). */
@@ -178,6 +180,13 @@ void mfmc_model_destroy(mfmc_model *model);
 
 /* Derived constants of a model. */
 mfmc_status mfmc_model_query(const mfmc_model *model, mfmc_model_info *out);
+
+/* Iteration totals of the model's last beta2 > 0 solve (MFMC_ALGO_ACTIVE_SET), summed over
+ * its samples and steps: newton_iters = Newton residual evaluations, cg_iters = FP32 CG
+ * iterations (one multigrid V-cycle each).  Reads device memory: synchronise the stream of
+ * that solve first.  Zeros for a model that has run no such solve.  Either output may be
+ * NULL. */
+mfmc_status mfmc_model_solver_stats(const mfmc_model *model, uint64_t *newton_iters, uint64_t *cg_iters);
 
 /* Pin the tile shape (0..7) of the TMA kernel instead of letting the autotuner choose
  * (for measurements and tests).  MFMC_EINVAL for an unknown variant. */

@@ -25,7 +25,8 @@
 //
 // One CTA per sample runs every step of its solve (every step of one launch with the direct
 // sum; one step per launch with the spectral sum, the state staying in global scratch between
-// launches); its vectors live in global scratch and the CTA's reductions use a fixed order.  No CTA waits on another.  Every loop is bounded; a
+// launches); its fine-level vectors live in global scratch, the coarse multigrid levels that fit
+// in shared memory, and the CTA's reductions use a fixed order.  No CTA waits on another.  Every loop is bounded; a
 // Newton iteration that does not converge within its bound sets the status flag (a CG solve
 // that reaches its bound hands its iterate to the next Newton iteration).
 #include <cuda_runtime.h>
@@ -70,6 +71,25 @@ __host__ __device__ inline size_t as_per_sample(int n) {
     return (size_t)AS_VEC64 * n * n + (f + 1) / 2;
 }
 
+// The coarse levels from as_smem_from(n) on live in dynamic shared memory (at most
+// AS_SMEM_BUDGET bytes): their passes are short, and each then costs a shared-memory round trip
+// and a barrier instead of a global one.  Returns that level and sets *bytes.
+constexpr size_t AS_SMEM_BUDGET = 160 * 1024;
+__host__ __device__ inline int as_smem_from(int n, size_t *bytes) {
+    int sz[AS_MAX_LEVELS];
+    const int L = as_levels(n, sz);
+    size_t b = 0;
+    int l0 = L;
+    for (int l = L - 1; l >= 1; --l) {
+        const size_t add = (size_t)4 * sz[l] * sz[l] * sizeof(float);
+        if (b + add > AS_SMEM_BUDGET) break;
+        b += add;
+        l0 = l;
+    }
+    *bytes = b;
+    return l0;
+}
+
 struct ActiveSetArgs {
     const float *u0;
     float *uT;
@@ -78,6 +98,7 @@ struct ActiveSetArgs {
     double eps_nominal;
     double *buf;         // [ns][as_per_sample(n)]
     int *status;         // set to 1 when an iteration bound is reached
+    unsigned long long *iters;  // [2]: Newton and CG iterations, added by every CTA
     const double *wtab;  // Gaussian: FP64 weight / eps^2 by r^2; nullptr: constant kernel
     int widths[kMaxR + 1];
     int n, R, nsteps;
@@ -94,6 +115,34 @@ template <typename Fn>
 __device__ __forceinline__ void as_for(int n, Fn f) {
     for (int y = threadIdx.x >> 5; y < n; y += AS_NT / 32)
         for (int x = threadIdx.x & 31; x < n; x += 32) f(y, x, y * n + x);
+}
+
+// The same visit, NP points of a thread at a time: v = f(y, x, i) for all NP, then st(i, v)
+// for each, so no store stands between the loads of the NP points and they are in flight
+// together (a pass over the vectors in global scratch is bound by their latency otherwise).
+template <int NP = 4, typename Fn, typename St>
+__device__ __forceinline__ void as_map(int n, Fn f, St st) {
+    const int J = (n + 31) >> 5, lane = threadIdx.x & 31;
+    int y = threadIdx.x >> 5, j = 0;
+    while (y < n) {
+        int yy[NP], xx[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            yy[q] = y;
+            xx[q] = lane + 32 * j;
+            if (++j == J) {
+                j = 0;
+                y += AS_NT / 32;
+            }
+        }
+        decltype(f(0, 0, 0)) v[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q)
+            if (yy[q] < n && xx[q] < n) v[q] = f(yy[q], xx[q], yy[q] * n + xx[q]);
+#pragma unroll
+        for (int q = 0; q < NP; ++q)
+            if (yy[q] < n && xx[q] < n) st(yy[q] * n + xx[q], v[q]);
+    }
 }
 
 // Block-wide sum and maximum in a fixed order (warp trees, then the warps in order).
@@ -154,54 +203,80 @@ __device__ __forceinline__ float as_apply(const AsLevel &L, const float *v, int 
     return tb1 * v[i] - L.tb2h * as_lap_h2(v, L.n, y, x) + L.m[i] * icg * v[i];
 }
 
-// nu damped-Jacobi sweeps on level L (v <- v + omega D^-1 (f - J v)), r as the temporary
-__device__ void as_smooth(const AsLevel &L, int nu, float tb1, float icg) {
+// One damped-Jacobi sweep on level L: dst = src + omega D^-1 (f - J src), or dst = omega D^-1 f
+// when src is nullptr (a sweep from zero).  dst != src.  Returns the thread's partial sum of
+// f * dst.
+__device__ __noinline__ float as_sweep(const AsLevel &L, const float *src, float *dst, float tb1, float icg) {
     const float dconst = tb1 + 4.0f * L.tb2h;
-    for (int k = 0; k < nu; ++k) {
-        as_for(L.n, [&](int y, int x, int i) { L.r[i] = L.f[i] - as_apply(L, L.v, y, x, i, tb1, icg); });
-        __syncthreads();
-        as_for(L.n, [&](int, int, int i) { L.v[i] += AS_OMEGA * L.r[i] / (dconst + L.m[i] * icg); });
-        __syncthreads();
+    float acc = 0.0f;
+    auto store = [&](int i, float2 v) {
+        dst[i] = v.x;
+        acc += v.y;
+    };
+    if (!src) {
+        as_map(L.n, [&](int, int, int i) {
+            const float f = L.f[i], v = AS_OMEGA * f / (dconst + L.m[i] * icg);
+            return make_float2(v, f * v);
+        }, store);
+    } else {
+        as_map(L.n, [&](int y, int x, int i) {
+            const float f = L.f[i], v = src[i] + AS_OMEGA * (f - as_apply(L, src, y, x, i, tb1, icg)) /
+                                                     (dconst + L.m[i] * icg);
+            return make_float2(v, f * v);
+        }, store);
     }
+    __syncthreads();
+    return acc;
 }
 
-// One V-cycle z = B r (symmetric: damped Jacobi before and after each correction, full-weighting
-// restriction = prolongation transpose / 4), levels[0].f = r and levels[0].v = z.
-__device__ void as_vcycle(const AsLevel *lv, int nl, float tb1, float icg) {
+// One V-cycle z = B r (levels[0].f = r in, levels[0].v = z out; symmetric: damped Jacobi before
+// and after each coarse correction, full-weighting restriction = prolongation transpose / 4).
+// Each visit of a level makes an even number of sweeps alternating between v and r, the first
+// from zero, so z ends in v.  Returns the thread's partial sum of r * z.
+static_assert(AS_NU == 2 && AS_NU_COARSE % 2 == 0, "the sweeps alternate between two buffers");
+__device__ __noinline__ float as_vcycle(const AsLevel *lv, int nl, float tb1, float icg) {
+    float dot = 0.0f;
     for (int l = 0; l < nl; ++l) {
         const AsLevel &L = lv[l];
-        as_for(L.n, [&](int, int, int i) { L.v[i] = 0.0f; });
-        __syncthreads();
         if (l == nl - 1) {
-            as_smooth(L, AS_NU_COARSE, tb1, icg);
+            as_sweep(L, nullptr, L.r, tb1, icg);
+            for (int k = 2; k <= AS_NU_COARSE; ++k) {
+                const float d = (k & 1) ? as_sweep(L, L.v, L.r, tb1, icg) : as_sweep(L, L.r, L.v, tb1, icg);
+                if (l == 0 && k == AS_NU_COARSE) dot = d;
+            }
             break;
         }
-        as_smooth(L, AS_NU, tb1, icg);
-        as_for(L.n, [&](int y, int x, int i) { L.r[i] = L.f[i] - as_apply(L, L.v, y, x, i, tb1, icg); });
+        as_sweep(L, nullptr, L.r, tb1, icg);
+        as_sweep(L, L.r, L.v, tb1, icg);
+        as_map(L.n, [&](int y, int x, int i) { return L.f[i] - as_apply(L, L.v, y, x, i, tb1, icg); },
+               [&](int i, float v) { L.r[i] = v; });
         __syncthreads();
         const AsLevel &C = lv[l + 1];
         const int n = L.n;
-        as_for(C.n, [&](int Y, int X, int i) {  // full weighting at (2Y, 2X)
+        as_map(C.n, [&](int Y, int X, int) {  // full weighting at (2Y, 2X)
             const int y = 2 * Y, x = 2 * X;
             const int ym = y == 0 ? n - 1 : y - 1, yp = y + 1, xm = x == 0 ? n - 1 : x - 1, xp = x + 1;
             const float c = L.r[y * n + x];
             const float e = (L.r[y * n + xm] + L.r[y * n + xp]) + (L.r[ym * n + x] + L.r[yp * n + x]);
             const float k = (L.r[ym * n + xm] + L.r[ym * n + xp]) + (L.r[yp * n + xm] + L.r[yp * n + xp]);
-            C.f[i] = (4.0f * c + 2.0f * e + k) * 0.0625f;
-        });
+            return (4.0f * c + 2.0f * e + k) * 0.0625f;
+        }, [&](int i, float v) { C.f[i] = v; });
         __syncthreads();
     }
     for (int l = nl - 2; l >= 0; --l) {
         const AsLevel &L = lv[l], &C = lv[l + 1];
         const int nc = C.n;
-        as_for(L.n, [&](int y, int x, int i) {  // bilinear prolongation (periodic)
+        as_map(L.n, [&](int y, int x, int i) {  // bilinear prolongation (periodic)
             const int Y = y >> 1, X = x >> 1;
             const int Y1 = (y & 1) ? (Y + 1 == nc ? 0 : Y + 1) : Y, X1 = (x & 1) ? (X + 1 == nc ? 0 : X + 1) : X;
-            L.v[i] += 0.25f * ((C.v[Y * nc + X] + C.v[Y * nc + X1]) + (C.v[Y1 * nc + X] + C.v[Y1 * nc + X1]));
-        });
+            return L.v[i] + 0.25f * ((C.v[Y * nc + X] + C.v[Y * nc + X1]) + (C.v[Y1 * nc + X] + C.v[Y1 * nc + X1]));
+        }, [&](int i, float v) { L.v[i] = v; });
         __syncthreads();
-        as_smooth(L, AS_NU, tb1, icg);
+        as_sweep(L, L.v, L.r, tb1, icg);
+        const float d = as_sweep(L, L.r, L.v, tb1, icg);
+        if (l == 0) dot = d;
     }
+    return dot;
 }
 
 __global__ void __launch_bounds__(AS_NT) active_set_kernel(ActiveSetArgs a) {
@@ -220,15 +295,19 @@ __global__ void __launch_bounds__(AS_NT) active_set_kernel(ActiveSetArgs a) {
     const int nl = as_levels(n, sizes);
     AsLevel lv[AS_MAX_LEVELS];
     {
-        float *q = T + nn;
+        extern __shared__ float as_smem[];
+        size_t smem_bytes;
+        const int l0 = as_smem_from(n, &smem_bytes);
+        float *q = T + nn, *qs = as_smem;  // global levels 1 .. l0 - 1, shared levels l0 ..
         for (int l = 0; l < nl; ++l) {
             const float tb2h_l = (float)(a.tau * a.beta2 * (double)sizes[l] * (double)sizes[l]);
             if (l == 0) {
                 lv[0] = AsLevel{Z, Rr, T, M, n, tb2h_l};
             } else {
                 const size_t ml = (size_t)sizes[l] * sizes[l];
-                lv[l] = AsLevel{q, q + ml, q + 2 * ml, q + 3 * ml, sizes[l], tb2h_l};
-                q += 4 * ml;
+                float *b = l >= l0 ? qs : q;
+                lv[l] = AsLevel{b, b + ml, b + 2 * ml, b + 3 * ml, sizes[l], tb2h_l};
+                (l >= l0 ? qs : q) += 4 * ml;
             }
         }
     }
@@ -243,6 +322,7 @@ __global__ void __launch_bounds__(AS_NT) active_set_kernel(ActiveSetArgs a) {
         __syncthreads();
     }
     bool failed = false;
+    unsigned long long n_newton = 0, n_cg = 0;
     for (int step = 1; step <= a.nsteps && !failed; ++step) {
         // explicit part g = gamma * u + c_F u (direct sum over the disc, FP64; R < n, so one
         // wrap of each index suffices)
@@ -280,6 +360,7 @@ __global__ void __launch_bounds__(AS_NT) active_set_kernel(ActiveSetArgs a) {
         });
         __syncthreads();
         for (int it = 1;; ++it) {
+            ++n_newton;
             // FP64 residual F(w), the inactive set, and the right-hand side r = -F of J d = -F
             double fmax = 0.0, changed = 0.0;
             as_for(n, [&](int y, int x, int i) {
@@ -314,40 +395,40 @@ __global__ void __launch_bounds__(AS_NT) active_set_kernel(ActiveSetArgs a) {
                 __syncthreads();
             }
             __syncthreads();
-            // FP32 CG on J d = r preconditioned by one multigrid V-cycle, d = 0 at the start
-            as_vcycle(lv, nl, tb1f, icgf);  // Z = B Rr
-            float rz = 0.0f;
-            as_for(n, [&](int, int, int i) {
-                Pp[i] = Z[i];
-                rz += Rr[i] * Z[i];
-            });
-            rz = as_block_sum(rz, red32);
+            // FP32 CG on J d = r preconditioned by one multigrid V-cycle, d = 0 at the start.  q = J p
+            // follows the recurrence q = J z + beta q, so one stencil pass (on z) serves each
+            // iteration, and r . z comes out of the V-cycle's last sweep.
+            float rz = as_block_sum(as_vcycle(lv, nl, tb1f, icgf), red32);  // Z = B Rr
+            float beta = 0.0f;
             for (int k = 1;; ++k) {
+                const bool first = k == 1;
                 float pq = 0.0f;
-                as_for(n, [&](int y, int x, int i) {
-                    const float q = (tb1f * Pp[i] - tb2hf * as_lap_h2(Pp, n, y, x)) + M[i] * icgf * Pp[i];
-                    Q[i] = q;
-                    pq += Pp[i] * q;
+                as_map(n, [&](int y, int x, int i) {
+                    const float z = Z[i];
+                    const float jz = (tb1f * z - tb2hf * as_lap_h2(Z, n, y, x)) + M[i] * icgf * z;
+                    return first ? make_float2(z, jz) : make_float2(z + beta * Pp[i], jz + beta * Q[i]);
+                }, [&](int i, float2 v) {
+                    Pp[i] = v.x;
+                    Q[i] = v.y;
+                    pq += v.x * v.y;
                 });
                 pq = as_block_sum(pq, red32);
                 const float alpha = pq > 0.0f ? rz / pq : 0.0f;
                 float rmax = 0.0f;
-                as_for(n, [&](int, int, int i) {
-                    D[i] += alpha * Pp[i];
-                    Rr[i] -= alpha * Q[i];
-                    rmax = rmax > fabsf(Rr[i]) ? rmax : fabsf(Rr[i]);
-                });
+                as_map(n, [&](int, int, int i) { return make_float2(D[i] + alpha * Pp[i], Rr[i] - alpha * Q[i]); },
+                       [&](int i, float2 v) {
+                           D[i] = v.x;
+                           Rr[i] = v.y;
+                           rmax = rmax > fabsf(v.y) ? rmax : fabsf(v.y);
+                       });
                 rmax = as_block_max(rmax, red32);
-                if (rmax <= AS_CG_RTOL || !(pq > 0.0f) || !(rz > 0.0f) || k >= AS_MAX_CG) break;
-                __syncthreads();
-                as_vcycle(lv, nl, tb1f, icgf);  // Z = B Rr
-                float rz2 = 0.0f;
-                as_for(n, [&](int, int, int i) { rz2 += Rr[i] * Z[i]; });
-                rz2 = as_block_sum(rz2, red32);
-                const float beta = rz2 / rz;
+                if (rmax <= AS_CG_RTOL || !(pq > 0.0f) || !(rz > 0.0f) || k >= AS_MAX_CG) {
+                    n_cg += k;
+                    break;
+                }
+                const float rz2 = as_block_sum(as_vcycle(lv, nl, tb1f, icgf), red32);  // Z = B Rr
+                beta = rz2 / rz;
                 rz = rz2;
-                as_for(n, [&](int, int, int i) { Pp[i] = Z[i] + beta * Pp[i]; });
-                __syncthreads();
             }
             as_for(n, [&](int, int, int i) { W[i] += fmax * (double)D[i]; });
             __syncthreads();
@@ -355,6 +436,10 @@ __global__ void __launch_bounds__(AS_NT) active_set_kernel(ActiveSetArgs a) {
         if (failed) break;
         as_for(n, [&](int, int, int i) { U[i] = as_clip((W[i] + G[i]) / cg); });
         __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(&a.iters[0], n_newton);
+        atomicAdd(&a.iters[1], n_cg);
     }
     if (failed) {
         if (threadIdx.x == 0) atomicExch(a.status, 1);
@@ -389,6 +474,8 @@ mfmc_status run_solve_active_set(Model &m, const double *eps_dev, const float *u
         MFMC_CUDA(cudaMalloc((void **)&m.d_wtab64, m.wtab64.size() * sizeof(double)));
         MFMC_CUDA(cudaMemcpy(m.d_wtab64, m.wtab64.data(), m.wtab64.size() * sizeof(double), cudaMemcpyHostToDevice));
     }
+    if (!m.d_as_iters) MFMC_CUDA(cudaMalloc((void **)&m.d_as_iters, 2 * sizeof(unsigned long long)));
+    MFMC_CUDA(cudaMemsetAsync(m.d_as_iters, 0, 2 * sizeof(unsigned long long), st));
     // the inactive-set vector starts at an impossible value, so no step sees a stale set
     MFMC_CUDA(cudaMemsetAsync(m.as_buf, 0xff, ns * per * sizeof(double), st));
     ActiveSetArgs a;
@@ -400,6 +487,7 @@ mfmc_status run_solve_active_set(Model &m, const double *eps_dev, const float *u
     a.eps_nominal = m.d.eps;
     a.buf = m.as_buf;
     a.status = m.d_status;
+    a.iters = m.d_as_iters;
     a.wtab = m.d.kernel == MFMC_KERNEL_GAUSSIAN ? m.d_wtab64 : nullptr;
     for (int d = 0; d <= kMaxR; ++d) a.widths[d] = d <= m.R ? m.widths[d] : 0;
     a.n = m.d.n;
@@ -410,6 +498,9 @@ mfmc_status run_solve_active_set(Model &m, const double *eps_dev, const float *u
     a.beta1 = m.d.beta1;
     a.beta2 = m.d.beta2;
     a.cF = m.d.c_F;
+    size_t smem = 0;
+    as_smem_from(m.d.n, &smem);
+    MFMC_CUDA(cudaFuncSetAttribute(active_set_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     auto launch = [&](int load, int steps, int g_given, int finish) -> mfmc_status {
         a.load = load;
         a.nsteps = steps;
@@ -417,7 +508,7 @@ mfmc_status run_solve_active_set(Model &m, const double *eps_dev, const float *u
         a.finish = finish;
         for (size_t o = 0; o < ns; o += 65535) {
             a.s0 = o;
-            active_set_kernel<<<(unsigned)std::min<size_t>(65535, ns - o), AS_NT, 0, st>>>(a);
+            active_set_kernel<<<(unsigned)std::min<size_t>(65535, ns - o), AS_NT, smem, st>>>(a);
             MFMC_LAUNCHED("active_set launch 1");
         }
         return MFMC_OK;

@@ -59,6 +59,7 @@ Model::~Model() {
     if (stream) cudaStreamDestroy(stream);
     fft_release(fft);
     fft64_release(fft64);
+    cudaFree(d_as_iters);
 }
 
 template <typename T>
@@ -222,6 +223,15 @@ mfmc_status mfmc_model_create(const mfmc_model_desc *desc, mfmc_model **out) {
 }
 
 void mfmc_model_destroy(mfmc_model *model) { delete model; }
+
+mfmc_status mfmc_model_solver_stats(const mfmc_model *m, uint64_t *newton_iters, uint64_t *cg_iters) {
+    if (!m) return fail(MFMC_EINVAL, "NULL model");
+    unsigned long long it[2] = {0, 0};
+    if (m->d_as_iters) MFMC_CUDA(cudaMemcpy(it, m->d_as_iters, sizeof(it), cudaMemcpyDeviceToHost));
+    if (newton_iters) *newton_iters = it[0];
+    if (cg_iters) *cg_iters = it[1];
+    return MFMC_OK;
+}
 
 mfmc_status mfmc_model_query(const mfmc_model *m, mfmc_model_info *out) {
     if (!m || !out) return fail(MFMC_EINVAL, "NULL argument");

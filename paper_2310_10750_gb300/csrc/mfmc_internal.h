@@ -92,6 +92,7 @@ struct Model {
     int graphs_off = 0;
     FftState *fft = nullptr;  // created by the first FFT-path solve
     Fft64State *fft64 = nullptr;  // created by the first spectral beta2 > 0 solve
+    unsigned long long *d_as_iters = nullptr;  // Newton and CG iterations of the last beta2 > 0 solve
     ~Model();
 };
 

@@ -96,6 +96,7 @@ _sig("mfmc_model_create", _st, [ctypes.POINTER(mfmc_model_desc), ctypes.POINTER(
 _sig("mfmc_model_destroy", None, [_vp])
 _sig("mfmc_model_query", _st, [_vp, ctypes.POINTER(mfmc_model_info)])
 _sig("mfmc_model_set_tile_variant", _st, [_vp, ctypes.c_int])
+_sig("mfmc_model_solver_stats", _st, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)])
 _sig("mfmc_model_set_band_height", _st, [_vp, ctypes.c_int, ctypes.c_int])
 _sig("mfmc_sample_eps", _st, [_vp, _vp, _vp, ctypes.c_size_t, _vp])
 _sig("mfmc_init_fields", _st, [_vp, _vp, _vp, ctypes.c_size_t, _vp, _vp])
@@ -200,6 +201,14 @@ def mfmc_model_create(**kw) -> Model:
 
 def mfmc_model_set_tile_variant(model: Model, variant: int):
     model.set_tile_variant(variant)
+
+
+def mfmc_model_solver_stats(model: Model):
+    """(Newton iterations, CG iterations) of the model's last beta2 > 0 solve, summed over its
+    samples and steps (synchronise that solve's stream first)."""
+    nw, cgi = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    _check(_L.mfmc_model_solver_stats(model.handle, ctypes.byref(nw), ctypes.byref(cgi)))
+    return int(nw.value), int(cgi.value)
 
 
 def make_params(ns, eps=None, theta=None, nsteps=None):

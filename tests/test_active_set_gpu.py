@@ -62,6 +62,11 @@ def test_active_set_solve_matches_oracle(gpu_lib, case):
     seeds = np.arange(2, dtype=np.uint64) + 100 + case
     _, uT, f, ubar = gpu_solve(mf, g, seeds)
     assert g.info().algo == mf.ALGO_ACTIVE_SET
+    newton, cg = mf.mfmc_model_solver_stats(g)
+    # per sample and step: the start, a few corrections and the confirming residual; each FP32
+    # correction a few multigrid-preconditioned CG iterations
+    assert 2 * len(seeds) * steps <= newton <= 12 * len(seeds) * steps
+    assert newton - len(seeds) * steps <= cg <= 30 * (newton - len(seeds) * steps)
     for i, s in enumerate(seeds):
         fr, mean, ur, _ = B2.solve_sample(o, int(s), 0.05, steps)
         assert abs(f[i] - fr) <= 1e-8 * fr
