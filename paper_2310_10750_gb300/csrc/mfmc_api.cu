@@ -54,7 +54,6 @@ Model::~Model() {
     cudaFree(d_wtab64);
     cudaFree(d_wsq);
     cudaFree(as_buf);
-    cudaFree(as_status);
     if (gexec) cudaGraphExecDestroy(gexec);
     if (stream) cudaStreamDestroy(stream);
     fft_release(fft);

@@ -53,7 +53,6 @@ struct Model {
     float *d_wsq = nullptr;
     double *as_buf = nullptr;
     size_t as_cap = 0;        // doubles
-    int *as_status = nullptr;
     int algo;                 // resolved algorithm (never AUTO after the autotuner ran)
     int tuned;                // 1 once AUTO was resolved
     // library-owned scratch, reused across calls on this model
