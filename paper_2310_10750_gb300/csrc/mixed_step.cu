@@ -178,8 +178,8 @@ static MixWorkspace &mix_ws() {
 
 static mfmc_status ensure_group(MixGroupBufs &b, const Model &m, size_t k, bool padded, cudaStream_t st,
                                 uint64_t *generation) {
-    MixGeom geo;
-    mix_geom(m.R, &geo);
+    MixGeom geo{};
+    if (!mix_geom(m.R, &geo)) return fail(MFMC_EINVAL, "no mixed-batch tile shape for R = %d", m.R);
     if (b.cap >= k && b.n == m.d.n && b.R == m.R && (b.padded || !padded)) return MFMC_OK;
     ++*generation;
     MFMC_CUDA(cudaStreamSynchronize(st));
@@ -348,8 +348,8 @@ extern "C" mfmc_status mfmc_solve_batch_mixed(mfmc_model *const *models, const m
             int total = 0;
             for (int qi = 0; qi < nq; ++qi) {
                 const int g = queue[qi];
-                MixGeom geo;
-                mix_geom(order[g]->R, &geo);
+                MixGeom geo{};
+                if (!mix_geom(order[g]->R, &geo)) return fail(MFMC_EINVAL, "no mixed-batch tile shape for R = %d", order[g]->R);
                 const int n = order[g]->d.n;
                 TmaArgs &t = a.g[qi];
                 t.dst_plain = nullptr;
