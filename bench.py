@@ -202,7 +202,7 @@ def run_ours(args):
         dist.barrier()
     else:
         torch.cuda.set_device(local)
-    from paper_2310_10750_gb300 import mfmc
+    from paper_2310_10750_gb300 import mfmc, replicas
     dev = torch.cuda.current_device()
     stream = torch.cuda.current_stream()
 
@@ -217,7 +217,8 @@ def run_ours(args):
     if args.band_height > 0:
         model.set_band_height(args.band_height, args.columns)
     ns = NSAMPLES
-    seeds = np.arange(ns, dtype=np.uint64) + SEED_BASE + rank * ns
+    first, last = replicas.shard(ws * ns, ws, rank)  # this rank's own ns samples (weak scaling)
+    seeds = np.arange(first, last, dtype=np.uint64) + np.uint64(SEED_BASE)
     u0 = torch.empty((ns, N_LATTICE, N_LATTICE), dtype=torch.float32, device="cuda")
     ooi = torch.empty(ns, dtype=torch.float64, device="cuda")
     eps = torch.tensor(mfmc.mfmc_sample_eps(model, seeds), dtype=torch.float64, device="cuda")
@@ -246,11 +247,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1), ws)
     ms_step = ms / args.steps
     pts_step = ws * ns * N_LATTICE * N_LATTICE * NSTEPS
     value = pts_step / (ms_step * 1e-3)
@@ -269,11 +266,7 @@ def run_ours(args):
         t = time.perf_counter()
         for _ in range(args.steps):
             f_host, _ = mfmc.mfmc_solve_batch(models, seeds)
-        e2e_s = (time.perf_counter() - t) / args.steps
-        if ws > 1:
-            tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
+        e2e_s = replicas.max_over_ranks((time.perf_counter() - t) / args.steps, ws)
 
     # plain form: one sample per launch, one launch per step (same GPU), on 4 samples
     plain_sps = None
