@@ -54,8 +54,12 @@ def test_model_validation_on_host(lib):
     assert info.c_gamma == pytest.approx(8 * 0.03 ** 2 / (3.141592653589793 * (4 / 64) ** 4) / 64 ** 2 * 49)
     assert info.c_gamma == pytest.approx(1.7968, abs=1e-4)
     # beta2 > 0: the active-set solver, chosen by AUTO or named
-    mfmc.Model(n=64, delta=4 / 64, beta2=0.05)
+    b2 = mfmc.Model(n=64, delta=4 / 64, beta2=0.05)
     mfmc.Model(n=64, delta=4 / 64, beta2=0.05, algo=mfmc.ALGO_ACTIVE_SET)
+    # no solve yet: the iteration totals are zero and no device memory is read
+    assert mfmc.mfmc_model_solver_stats(b2) == (0, 0)
+    assert mfmc.mfmc_model_solver_stats(m) == (0, 0)
+    assert mfmc._L.mfmc_model_solver_stats(None, None, None) == mfmc.MFMC_EINVAL
     # a non-integer delta/h: the disc is { |z| <= 4.5 } and only the generic kernel serves it
     g = mfmc.Model(n=64, delta=4.5 / 64, eps=0.03)
     assert g.info().R == 4
