@@ -13,8 +13,10 @@
  *     stream).  Calls with device pointers are asynchronous on `stream`; calls with
  *     host output pointers return after the result has been copied back.
  *   - Fields are FP32, row-major [sample][y][x] with x fastest, n*n values each.
- *   - A device-side wait that runs out of its iteration limit returns
- *     MFMC_ETIMEOUT; the context stays usable.
+ *   - A device-side wait that runs out of its iteration limit, or a beta2 > 0 Newton
+ *     iteration that reaches its bound, sets the model's status flag; the calls that wait
+ *     for their results (mfmc_solve_batch and the mixed batch) then return
+ *     MFMC_ETIMEOUT.  The context stays usable.
  */
 #ifndef MFMC_H
 #define MFMC_H
@@ -211,7 +213,9 @@ mfmc_status mfmc_init_fields(const mfmc_model *model, const mfmc_sample_params *
  *                   / (1 + tau beta1 c_gamma) )
  * (Eq. (nonl_CH_nm) with beta2 = 0, implicit Euler with the convolution explicit as
  * Section 4 states, the convex part c_gamma u + dI implicit), and reduce the output of
- * interest f = (1 + mean u(T)) / 2 (Eq. (ooi)).
+ * interest f = (1 + mean u(T)) / 2 (Eq. (ooi)).  A model with beta2 > 0 takes the implicit
+ * step of MFMC_ALGO_ACTIVE_SET instead (the same equation with the screened Laplacian
+ * coupling, solved to max|F| <= 1e-11 per step).
  *   eps   device, ns per-sample eps values, or NULL for the nominal eps
  *   u0    device, [ns][n][n] FP32, read only
  *   uT    device, [ns][n][n] FP32 final fields, or NULL
