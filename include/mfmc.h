@@ -324,6 +324,15 @@ mfmc_status mfmc_plan(int K, int n_pilot, const double *pilot_ooi, const double 
                       double budget, int policy, const int *explicit_idx, int explicit_len,
                       mfmc_plan_t *out);
 
+/* mfmc_plan from statistics that are already known (a previous study's table, such as
+ * the paper's Table 1), host only, no device work: rho[K] = rho_{1,k} (rho[0] is f_1's
+ * own, 1), sigma[K] > 0, costs[K] > 0 (host), budget, policy and explicit subset as for
+ * mfmc_plan; the plan's mean_all is zero.  MFMC_EINVAL for a NULL pointer, K outside
+ * [1, 16], |rho| > 1 or a non-finite value; MFMC_EBUDGET as for mfmc_plan. */
+mfmc_status mfmc_plan_from_stats(int K, const double *rho, const double *sigma, const double *costs,
+                                 double budget, int policy, const int *explicit_idx, int explicit_len,
+                                 mfmc_plan_t *out);
+
 /* Eq. (MFMC_estimator) in FP64 on the GPU: ooi[j] (host) holds model i_j on the
  * shared sample sequence, at least m_j values; Q^{(i_j)}_m is the mean of the first m.
  * Writes the estimate to *estimate (host). */

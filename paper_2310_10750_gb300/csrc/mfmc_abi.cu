@@ -125,6 +125,20 @@ mfmc_status mfmc_plan(int K, int n_pilot, const double *pilot_ooi, const double 
                            out);
 }
 
+mfmc_status mfmc_plan_from_stats(int K, const double *rho, const double *sigma, const double *costs, double budget,
+                                 int policy, const int *explicit_idx, int explicit_len, mfmc_plan_t *out) {
+    if (K < 1 || K > MFMC_MAX_MODELS || !rho || !sigma || !costs || !out)
+        return fail(MFMC_EINVAL, "invalid plan arguments");
+    for (int k = 0; k < K; ++k) {
+        if (!std::isfinite(rho[k]) || std::fabs(rho[k]) > 1.0) return fail(MFMC_EINVAL, "rho of model %d outside [-1, 1]", k);
+        if (!std::isfinite(sigma[k]) || !(sigma[k] > 0)) return fail(MFMC_EINVAL, "sigma of model %d must be > 0", k);
+        if (!std::isfinite(costs[k])) return fail(MFMC_EINVAL, "cost of model %d is not finite", k);
+    }
+    if (!std::isfinite(budget)) return fail(MFMC_EINVAL, "budget is not finite");
+    const std::vector<double> mean(K, 0.0);
+    return plan_from_stats(K, mean.data(), sigma, rho, costs, budget, policy, explicit_idx, explicit_len, out);
+}
+
 mfmc_status mfmc_estimate_device(const mfmc_plan_t *plan, const double *const *ooi_dev, double *estimate_dev,
                                  void *stream) {
     if (!plan || !ooi_dev || !estimate_dev || plan->K_sel < 1 || plan->K_sel > MFMC_MAX_MODELS)

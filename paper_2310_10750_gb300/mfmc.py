@@ -107,6 +107,8 @@ _sig("mfmc_solve_batch_mixed", _st, [_vp, _vp, _vp, ctypes.c_size_t, _vp, _vp])
 _sig("mfmc_pilot_stats", _st, [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp])
 _sig("mfmc_plan", _st, [ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_double, ctypes.c_int, _vp, ctypes.c_int,
                         ctypes.POINTER(mfmc_plan_t)])
+_sig("mfmc_plan_from_stats", _st, [ctypes.c_int, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _vp, ctypes.c_int,
+                                    ctypes.POINTER(mfmc_plan_t)])
 _sig("mfmc_estimate", _st, [ctypes.POINTER(mfmc_plan_t), _vp, _vp])
 _sig("mfmc_estimate_device", _st, [ctypes.POINTER(mfmc_plan_t), _vp, _vp, _vp])
 _sig("mfmc_run", _st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_uint64, _vp,
@@ -298,6 +300,20 @@ def mfmc_plan(pilot_ooi, costs, budget, policy=0, explicit=None) -> mfmc_plan_t:
     ex = None if explicit is None else np.ascontiguousarray(np.asarray(explicit, dtype=np.int32))
     _check(_L.mfmc_plan(K, n, P.ctypes.data, C.ctypes.data, float(budget), policy,
                         None if ex is None else ex.ctypes.data, 0 if ex is None else len(ex), ctypes.byref(out)))
+    return out
+
+
+def mfmc_plan_from_stats(rho, sigma, costs, budget, policy=0, explicit=None) -> mfmc_plan_t:
+    R = np.ascontiguousarray(np.asarray(rho, dtype=np.float64))
+    S = np.ascontiguousarray(np.asarray(sigma, dtype=np.float64))
+    C = np.ascontiguousarray(np.asarray(costs, dtype=np.float64))
+    if not (len(R) == len(S) == len(C)):
+        raise ValueError("rho, sigma and costs must have one entry per model")
+    out = mfmc_plan_t()
+    ex = None if explicit is None else np.ascontiguousarray(np.asarray(explicit, dtype=np.int32))
+    _check(_L.mfmc_plan_from_stats(len(R), R.ctypes.data, S.ctypes.data, C.ctypes.data, float(budget), policy,
+                                   None if ex is None else ex.ctypes.data, 0 if ex is None else len(ex),
+                                   ctypes.byref(out)))
     return out
 
 

@@ -1,0 +1,98 @@
+"""The library's host planner (Section 3 selection and allocation) through
+mfmc_plan_from_stats, with no GPU: against the oracle's planner on the paper's Table 1
+statistics (tests/golden/table1_pilot_statistics.txt) for every policy and budgets on both
+sides of B_min, the paper's Case 1 and Case 3 subsets and its 131 feasible subsets, a
+printed V of Table 2, and the argument checks."""
+import numpy as np
+import pytest
+
+from oracle import mfmc_oracle as M
+from tests.conftest import read_golden
+
+
+@pytest.fixture(scope="module")
+def mf():
+    from paper_2310_10750_gb300 import build
+    build.build()
+    from paper_2310_10750_gb300 import mfmc
+    return mfmc
+
+
+def table1():
+    rows = read_golden("table1_pilot_statistics.txt")
+    return ([float(r[3]) for r in rows], [float(r[5]) for r in rows], [float(r[4]) for r in rows])
+
+
+def same_plan(p, ref):
+    assert p["idx"] == ref.subset
+    assert p["below_min_budget"] == ref.below_min_budget
+    assert np.allclose(p["alpha"], ref.alpha, rtol=1e-12)
+    assert np.allclose(p["m_real"], ref.m_real, rtol=1e-9)
+    for a, b, x in zip(p["m"], ref.m, ref.m_real):   # floor may differ only at an integer
+        assert a == b or abs(x - round(x)) < 1e-9
+    assert p["V"] == pytest.approx(ref.V, rel=1e-11)
+    assert p["Bmin"] == pytest.approx(ref.Bmin, rel=1e-9)
+    assert p["mse_theory"] == pytest.approx(ref.mse_theory, rel=1e-9)
+
+
+@pytest.mark.parametrize("policy", [0, 1, 2])
+@pytest.mark.parametrize("budget", [4.0, 12.0, 40.0, 300.0, 1e4])
+def test_table1_plans_match_the_oracle(mf, policy, budget):
+    rho, sigma, C = table1()
+    ref = M.select(rho, sigma, C, budget, policy=policy)
+    if ref is None:
+        with pytest.raises(mf.MfmcError) as e:
+            mf.mfmc_plan_from_stats(rho, sigma, C, budget, policy)
+        assert e.value.status == mf.MFMC_EBUDGET
+        return
+    same_plan(mf.mfmc_plan_from_stats(rho, sigma, C, budget, policy).as_dict(), ref)
+
+
+def test_table1_cases_and_feasible_count(mf):
+    rho, sigma, C = table1()
+    p1 = mf.mfmc_plan_from_stats(rho, sigma, C, 1e6, 1).as_dict()
+    assert sorted(i + 1 for i in p1["idx"]) == [1, 2, 3, 9]          # Case 1: smallest V
+    assert p1["n_feasible"] == 131
+    p2 = mf.mfmc_plan_from_stats(rho, sigma, C, 1e6, 2).as_dict()
+    assert sorted(i + 1 for i in p2["idx"]) == [1, 9]                # Case 3: smallest B_min
+    # Table 2: V of {f1, f3, f9} printed as 0.10172 (1e-3 relative: the printed statistics
+    # are rounded)
+    p3 = mf.mfmc_plan_from_stats(rho, sigma, C, 1e6, 3, explicit=[0, 2, 8]).as_dict()
+    assert p3["V"] == pytest.approx(0.10172, rel=1e-3)
+    same_plan(p3, M.select(rho, sigma, C, 1e6, policy=3, explicit=[0, 2, 8]))
+
+
+def test_synthetic_statistics_and_single_model(mf):
+    rng = np.random.default_rng(4)
+    for K in (2, 3, 5, 8):
+        rho = np.concatenate([[1.0], np.sort(rng.uniform(0.3, 0.999, K - 1))[::-1]])
+        sigma = rng.uniform(0.5, 2.0, K)
+        C = np.concatenate([[1.0], np.sort(rng.uniform(1e-3, 0.5, K - 1))[::-1]])
+        for B in (2.0, 25.0, 1e3):
+            for policy in (0, 1, 2):
+                ref = M.select(list(rho), list(sigma), list(C), B, policy=policy)
+                if ref is None:
+                    continue
+                same_plan(mf.mfmc_plan_from_stats(rho, sigma, C, B, policy).as_dict(), ref)
+    # K = 1 is plain Monte Carlo: the whole budget on f_1
+    p = mf.mfmc_plan_from_stats([1.0], [0.5], [2.0], 9.0).as_dict()
+    assert p["idx"] == [0] and p["m"] == [4] and p["V"] == 1.0
+    assert p["mse_theory"] == pytest.approx(0.25 / 4.5)
+
+
+def test_argument_errors(mf):
+    rho, sigma, C = table1()
+    bad = [(rho[:1] * 17, sigma[:1] * 17, C[:1] * 17, 10.0),              # K > 16
+           ([1.0, 1.5], [1.0, 1.0], [1.0, 0.1], 10.0),                    # |rho| > 1
+           ([1.0, 0.9], [1.0, 0.0], [1.0, 0.1], 10.0),                    # sigma = 0
+           ([1.0, 0.9], [1.0, 1.0], [1.0, 0.0], 10.0),                    # zero cost
+           ([1.0, float("nan")], [1.0, 1.0], [1.0, 0.1], 10.0),           # not finite
+           ([1.0, 0.9], [1.0, 1.0], [1.0, 0.1], 0.0)]                     # no budget
+    for r, s, c, b in bad:
+        with pytest.raises(mf.MfmcError) as e:
+            mf.mfmc_plan_from_stats(r, s, c, b)
+        assert e.value.status == mf.MFMC_EINVAL
+    with pytest.raises(mf.MfmcError) as e:
+        mf.mfmc_plan_from_stats(rho, sigma, C, 0.5)                       # below one f_1 sample
+    assert e.value.status == mf.MFMC_EBUDGET
+    assert mf._L.mfmc_plan_from_stats(2, None, None, None, 1.0, 0, None, 0, None) == mf.MFMC_EINVAL
