@@ -107,6 +107,29 @@ def test_L_on_quadratic_closed_form():
     assert closed == pytest.approx(-2 * eps * eps, rel=0.06)
 
 
+@pytest.mark.parametrize("n,delta", [(64, 4.5 / 64), (88, 0.1875)])
+def test_non_integer_horizon_disc_and_operator(n, delta):
+    # delta/h = 4.5, and the paper's h = 1/88, delta = 0.1875 (delta/h = 16.5): the disc is the
+    # lattice ball { z : |z|^2 <= (delta/h)^2 } (brute force over its bounding square), L
+    # vanishes on constants, and L(x^2) = -h^2 a sum_{z in D} dx^2 on a non-wrapping patch
+    eps = 0.03
+    m = model(n=n, delta=delta, eps=eps)
+    rad = delta * n
+    Ri = int(math.floor(rad))
+    ball = {(i, j) for i in range(-Ri, Ri + 1) for j in range(-Ri, Ri + 1) if i * i + j * j <= rad * rad}
+    dx, dy = m.offsets()
+    assert len(dx) == len(ball) and set(zip(np.asarray(dx).tolist(), np.asarray(dy).tolist())) == ball
+    if n == 88:
+        assert len(ball) == 861
+    assert np.all(m.apply_L(np.full((n, n), -0.4375), eps) == 0.0)
+    h = 1.0 / n
+    u = np.tile((np.arange(n) * h) ** 2, (n, 1))
+    A = 8 * eps * eps / (math.pi * delta ** 4)
+    closed = -h * h * (A * h * h) * sum(i * i for i, _ in ball)
+    inner = m.apply_L_open(u, eps)[Ri:n - Ri, Ri:n - Ri]
+    assert np.allclose(inner, closed, rtol=1e-12, atol=0)
+
+
 def test_L_on_fourier_modes_matches_fft_symbol():
     n, R, eps = 32, 3, 0.03
     for kernel in (0, 1):
