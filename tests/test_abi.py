@@ -91,3 +91,24 @@ def test_host_eps_resolution_matches_oracle_generator(lib):
     got = mfmc.mfmc_sample_eps(m, seeds)
     ref = oracle.OracleModel(n=64, delta=4 / 64, eps_lo=0.024, eps_hi=0.036)
     assert [ref.sample_eps(int(s)) for s in seeds] == got.tolist()
+
+
+def test_host_setters_and_version(lib):
+    _, mfmc = lib
+    assert mfmc.mfmc_version()
+    m = mfmc.Model(n=256, delta=8 / 256, eps=0.02)
+    for v in range(8):
+        m.set_tile_variant(v)
+        assert m.info().tile_variant == v
+    for v in (-1, 8):
+        with pytest.raises(mfmc.MfmcError) as e:
+            m.set_tile_variant(v)
+        assert e.value.status == mfmc.MFMC_EINVAL
+    assert m.info().tile_variant == 7            # a rejected call changes nothing
+    m.set_band_height(64, 4)
+    assert (m.info().band_height, m.info().columns_per_thread) == (64, 4)
+    for rows, cols in ((7, 2), (16385, 2), (64, 3)):
+        with pytest.raises(mfmc.MfmcError) as e:
+            m.set_band_height(rows, cols)
+        assert e.value.status == mfmc.MFMC_EINVAL
+    assert (m.info().band_height, m.info().columns_per_thread) == (64, 4)
