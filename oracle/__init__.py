@@ -68,6 +68,8 @@ def lib():
         L.orc_initial_field.restype = None
         L.orc_initial_field.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                         ctypes.c_uint64, _dp, _dp, ctypes.c_int, _dp]
+        L.orc_block_mean.restype = None
+        L.orc_block_mean.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
         L.orc_draw_theta.restype = None
         L.orc_draw_theta.argtypes = [ctypes.c_uint64, _dp, _dp]
         L.orc_sample_eps.restype = ctypes.c_double
@@ -273,6 +275,15 @@ class OracleModel:
         u0 = self.initial_field(seed, theta)
         uT, mean = self.solve(u0, eps, nsteps)
         return 0.5 * (1.0 + mean), mean, uT, eps
+
+
+def block_mean(f: np.ndarray, n: int) -> np.ndarray:
+    """Mean of the b x b base-lattice blocks of f (B x B, B = b n) around each n-lattice node,
+    the map the noise initial conditions use to share one random field across lattices."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    u = np.zeros((n, n))
+    lib().orc_block_mean(n, f.shape[0], _d(f), _d(u))
+    return u
 
 
 def ooi(u: np.ndarray) -> float:

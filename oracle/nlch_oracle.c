@@ -311,22 +311,29 @@ static void orc_noise_field(int N, int ic, double amp, uint64_t seed, double *f)
     free(z);
 }
 
+/* Block mean of a base-lattice field f (B x B, B = b n) onto the n-lattice: node (y, x)
+ * takes the mean of the b x b base nodes (b y + a, b x + c), a, c in [-(b/2), b - b/2)
+ * (periodic), summed a-major in FP64. */
+void orc_block_mean(int n, int B, const double *f, double *u) {
+    int b = B / n;
+    for (int y = 0; y < n; ++y)
+        for (int x = 0; x < n; ++x) {
+            double s = 0.0;
+            for (int a = -(b / 2); a < b - b / 2; ++a)
+                for (int c = -(b / 2); c < b - b / 2; ++c)
+                    s += f[orc_wrap(b * y + a, B) * B + orc_wrap(b * x + c, B)];
+            u[y * n + x] = s / ((double)b * (double)b);
+        }
+}
+
 void orc_initial_field(int n, int ic, double amp, uint64_t seed, const double *mu,
                        const double *eta, int base_n, double *u0) {
     long N = (long)n * n;
     if (ic == 0 || ic == 1) {
         int B = base_n > 0 ? base_n : n;
-        int b = B / n;
         double *f = (double *)malloc(sizeof(double) * (size_t)B * B);
         orc_noise_field(B, ic, amp, seed, f);
-        for (int y = 0; y < n; ++y)
-            for (int x = 0; x < n; ++x) {
-                double s = 0.0;
-                for (int a = -(b / 2); a < b - b / 2; ++a)
-                    for (int c = -(b / 2); c < b - b / 2; ++c)
-                        s += f[orc_wrap(b * y + a, B) * B + orc_wrap(b * x + c, B)];
-                u0[y * n + x] = s / ((double)b * (double)b);
-            }
+        orc_block_mean(n, B, f, u0);
         free(f);
     } else {
         static const double cx[4] = {0.25, 0.75, 0.5, 0.5};

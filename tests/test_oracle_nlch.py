@@ -231,6 +231,74 @@ def test_energy_decreases_when_splitting_condition_holds():
             e = e2
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_energy_closed_form_on_fourier_modes(kernel):
+    # E_h(u) = h^2 [1/4 sum_i sum_z w_z (u_i - u_{i+z})^2 + sum_i (c_F/2)(1 - u_i^2)]
+    # (Section 2, the nonlocal free energy with the obstacle potential; |u| <= 1).
+    # On u = A cos(2 pi (p x + q y)) at the nodes x = j h, with 2p, 2q not both = 0 mod n:
+    # averaged over the lattice, cos^2 = 1/2 and (cos t - cos(t + phi))^2 = 1 - cos phi, so
+    #   E_h = (A^2 / 4) sum_z w_z (1 - cos(k.z)) + (c_F / 2)(1 - A^2 / 2)     (h^2 n^2 = 1).
+    # The symbol sum_z w_z (1 - cos(k.z)) is taken from numpy's FFT of the stencil.
+    n = 32
+    m = model(n=n, delta=5 / n, kernel=kernel, delta_hf=6 / n, c_F=1.0)
+    eps = 0.03
+    w, cg = m.weights(eps)
+    dx, dy = m.offsets()
+    st = np.zeros((n, n))
+    for k in range(len(w)):
+        st[dy[k] % n, dx[k] % n] += w[k]
+    spec = np.fft.fft2(st)
+    y, x = np.meshgrid(np.arange(n) / n, np.arange(n) / n, indexing="ij")
+    for (p, q), A in (((3, 5), 0.8), ((1, 0), 1.0), ((0, 7), -0.35), ((11, 2), 0.5)):
+        u = A * np.cos(2 * np.pi * (p * x + q * y))
+        sym = cg - spec[q, p].real
+        want = 0.25 * A * A * sym + 0.5 * m.c_F * (1 - A * A / 2)
+        assert m.energy(u, eps) == pytest.approx(want, rel=1e-12, abs=1e-15)
+    # pure phases: no interaction, no potential energy
+    assert m.energy(np.ones((n, n)), eps) == 0.0
+    assert m.energy(-np.ones((n, n)), eps) == 0.0
+    # a plausible slip (1/2 for the 1/4, a dropped h^2) would change the value by O(1)
+    u = 0.8 * np.cos(2 * np.pi * (3 * x + 5 * y))
+    assert abs(m.energy(u, eps) - (0.5 * 0.64 * (cg - spec[5, 3].real) + 0.5 * (1 - 0.32))) > 1e-3
+
+
+@pytest.mark.parametrize("b", [1, 2, 4])
+def test_base_lattice_block_mean(b):
+    # Noise ICs shared across lattices: node (y, x) of the n-lattice takes the mean of the
+    # b x b base nodes centred on it, rows and columns b y + a, a in [-(b // 2), b - b // 2).
+    n = 8
+    B = b * n
+    rng = np.random.default_rng(b)
+    f = rng.standard_normal((B, B))
+    u = O.block_mean(f, n)
+    # b = 1 is the identity, bit for bit
+    if b == 1:
+        assert np.array_equal(u, f)
+    # the n-lattice mean equals the base-lattice mean (the blocks tile the base torus)
+    assert u.mean() == pytest.approx(f.mean(), rel=1e-13, abs=1e-15)
+    # a single base node lands, with weight 1 / b^2, in exactly one n-node: the one whose
+    # block [b y - b // 2, b y + b - b // 2) contains it (periodically)
+    for Y, X in ((0, 0), (1, 2), (B - 1, B - 1), (b // 2, B - b // 2 - 1), (3 * b - 1, 5 * b)):
+        e = np.zeros((B, B))
+        e[Y % B, X % B] = 1.0
+        ue = O.block_mean(e, n)
+        ys, xs = np.nonzero(ue)
+        assert len(ys) == 1 and ue[ys[0], xs[0]] == 1.0 / (b * b)
+        assert ys[0] == ((Y % B) + b // 2) // b % n and xs[0] == ((X % B) + b // 2) // b % n
+    # the block centroid sits within half a base cell of the node (exactly on it for odd b)
+    cen = np.mean([b * 3 + a for a in range(-(b // 2), b - b // 2)])
+    assert abs(cen - 3 * b) <= 0.5
+    # the oracle's noise IC on the n-lattice is this block mean of its base-lattice field
+    # (both fields are rounded to FP32 after they are formed: agreement to 2 FP32 ulps)
+    for ic in (0, 1):
+        base = model(n=B, ic=ic, ic_amp=0.05)
+        coarse = model(n=n, ic=ic, ic_amp=0.05, ic_base_n=B)
+        want = O.block_mean(base.initial_field(17), n)
+        assert np.abs(coarse.initial_field(17) - want).max() <= 2 ** -22 * np.abs(want).max()
+        fb = base.initial_field(17)
+        assert abs(coarse.initial_field(17).mean() - fb.mean()) <= 2 ** -23 * np.abs(fb).max()
+
+
 def test_ooi_values():
     n = 16
     assert O.ooi(np.ones((n, n))) == 1.0
