@@ -214,7 +214,7 @@ def run_ours(args):
                        bc_value=BC_VALUE)
     if args.tile_variant >= 0:
         model.set_tile_variant(args.tile_variant)
-    if args.band_height > 0:
+    if args.band_height >= 0:
         model.set_band_height(args.band_height, args.columns)
     ns = NSAMPLES
     first, last = replicas.shard(ws * ns, ws, rank)  # this rank's own ns samples (weak scaling)
@@ -685,8 +685,9 @@ def main():
     ap.add_argument("--nsteps", type=int, default=0, help="profiling: time steps per solve")
     ap.add_argument("--samples", type=int, default=0, help="profiling: samples per GPU")
     ap.add_argument("--algo", default="auto", choices=["auto", "prefix", "direct", "kahan", "tma", "rows", "fft"])
-    ap.add_argument("--band-height", type=int, default=0, help="profiling: pin the row-streaming band height")
-    ap.add_argument("--columns", type=int, default=2, help="profiling: row-streaming columns per thread")
+    ap.add_argument("--band-height", type=int, default=-1,
+                    help="profiling: pin the row-streaming work split (rows per range, 0 = even split)")
+    ap.add_argument("--columns", type=int, default=4, help="profiling: row-streaming columns per thread")
     ap.add_argument("--tile-variant", type=int, default=-1, help="profiling: pin the TMA tile shape")
     ap.add_argument("--bc", default="periodic", choices=["periodic", "collar"],
                     help="boundary of the single-fidelity workload (collar: volume constraint)")

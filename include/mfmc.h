@@ -81,9 +81,11 @@ typedef enum {
     MFMC_ALGO_PLAIN = 5,       /* reference form: one sample per launch, direct   */
     MFMC_ALGO_PREFIX_TMA = 6,  /* prefix form, persistent CTAs, TMA double-buffered
                                   tiles of a ghost-framed field                   */
-    MFMC_ALGO_ROWS = 7         /* prefix form, each thread streams 2 or 4 columns down
-                                  a band of rows with a ring of 2R+1 accumulators
-                                  (R in {2,4,6,8}, n % 64 == 0, n <= 1024)         */,
+    MFMC_ALGO_ROWS = 7         /* row streaming: each warp streams a 128-column strip down
+                                  its share of the batch's rows through its own TMA chunk
+                                  ring; a lane owns 4 columns and keeps a ring of 2R+1
+                                  accumulators, every staged row summed once per segment
+                                  (constant kernel, R in {2,4,6,8}, n % 128 == 0)  */,
     MFMC_ALGO_FFT = 8          /* spectral form of the disc sum: cuFFT transforms (a library,
                                   loaded at run time) of each field, a product with the
                                   transform of the disc weights and the fused update; cost
@@ -155,9 +157,10 @@ typedef struct {
     double xi;             /* c_gamma - c_F, Eq. (xi_constant)                      */
     int algo;              /* mfmc_algo the solver uses for this model             */
     size_t field_bytes;    /* n * n * 4                                             */
-    int tile_variant;      /* tile shape of the TMA kernel (0..7) the solver uses  */
-    int band_height;       /* band height of the row-streaming kernel              */
-    int columns_per_thread;/* columns per thread of the row-streaming kernel       */
+    int tile_variant;      /* tile shape of the TMA kernel (0..10) the solver uses */
+    int band_height;       /* rows per work range of the row-streaming kernel
+                              (0: the batch's rows split evenly over the warps)     */
+    int columns_per_thread;/* columns per thread of the row-streaming kernel (4)   */
 } mfmc_model_info;
 
 typedef struct mfmc_model mfmc_model;
@@ -190,12 +193,14 @@ mfmc_status mfmc_model_query(const mfmc_model *model, mfmc_model_info *out);
  * NULL. */
 mfmc_status mfmc_model_solver_stats(const mfmc_model *model, uint64_t *newton_iters, uint64_t *cg_iters);
 
-/* Pin the tile shape (0..7) of the TMA kernel instead of letting the autotuner choose
+/* Pin the tile shape (0..10) of the TMA kernel instead of letting the autotuner choose
  * (for measurements and tests).  MFMC_EINVAL for an unknown variant. */
 mfmc_status mfmc_model_set_tile_variant(mfmc_model *model, int variant);
 
-/* Pin the band height (rows per work item, >= 8) and the columns per thread (2 or 4) of
- * the row-streaming kernel. */
+/* Pin the work split of the row-streaming kernel: rows = rows per work range (>= 8; ranges
+ * are taken in (sample, strip, row) order, warp w owning ranges w, w + W, ...), or 0 for the
+ * batch's rows split evenly over the resident warps (the default); columns_per_thread must
+ * be 4.  MFMC_EINVAL otherwise. */
 mfmc_status mfmc_model_set_band_height(mfmc_model *model, int rows, int columns_per_thread);
 
 /* Host-side resolution of each sample's eps (model eps, eps range draw, or

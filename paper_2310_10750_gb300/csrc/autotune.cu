@@ -46,10 +46,9 @@ mfmc_status autotune(Model &m, cudaStream_t st) {
         if (a == MFMC_ALGO_PREFIX_TMA) {
             for (int v = 0; v < kTmaVariants; ++v) cands.push_back({a, v});
         } else if (a == MFMC_ALGO_ROWS) {
-            // second: band height * 8 + columns per thread
-            for (int rx : {2, 4})
-                for (int bh : {64, 128, 256, 512})
-                    if (bh <= m.d.n && rows_supported(m, rx)) cands.push_back({a, bh * 8 + rx});
+            // second: band height * 8 + columns per thread (band 0: the rows split evenly)
+            for (int bh : {0, 64, 128})
+                if (bh <= m.d.n && rows_supported(m, 4)) cands.push_back({a, bh * 8 + 4});
         } else {
             cands.push_back({a, 0});
         }

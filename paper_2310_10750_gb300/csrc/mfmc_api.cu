@@ -254,7 +254,7 @@ mfmc_status mfmc_model_set_tile_variant(mfmc_model *m, int variant) {
 }
 
 mfmc_status mfmc_model_set_band_height(mfmc_model *m, int rows, int columns_per_thread) {
-    if (!m || rows < 8 || rows > 16384 || (columns_per_thread != 2 && columns_per_thread != 4))
+    if (!m || (rows != 0 && (rows < 8 || rows > 16384)) || columns_per_thread != 4)
         return fail(MFMC_EINVAL, "invalid band height or columns per thread");
     std::lock_guard<std::mutex> lk(m->mu);
     m->rows_bh = rows;

@@ -80,10 +80,10 @@ struct Model {
     size_t pad_cap = 0;
     CUtensorMap mapA, mapB;
     int maps_valid = 0;
-    int map_sw = 0, map_sh = 0;  // box the tensor maps were encoded for
+    int map_sw = 0, map_sh = 0, map_sd = 1, map_l2 = 256;  // box and L2 promotion of the tensor maps
     int tma_variant = 4;         // tile shape of the TMA kernel (autotuned; 4 is the default)
-    int rows_bh = 128;           // band height of the row-streaming kernel (autotuned)
-    int rows_rx = 2;             // columns per thread of the row-streaming kernel (2 or 4)
+    int rows_bh = 0;             // rows per work range of the row-streaming kernel (0: even split)
+    int rows_rx = 4;             // columns per thread of the row-streaming kernel
     int *d_status = nullptr;  // set by a device wait that gave up
     // CUDA graph of the last solve's launch sequence (replayed while its key matches)
     cudaGraphExec_t gexec = nullptr;
@@ -167,7 +167,10 @@ struct TmaBuffers {
     double *partials = nullptr;
     int *status = nullptr;
 };
-mfmc_status encode_map(CUtensorMap *map, float *base, int P, size_t cap, int sw, int sh);
+// Tensor map of padded fields [cap][P][P] FP32 with a box of sw x sh x sd (x, y, sample) and
+// L2 promotion of l2promo bytes (256, 128 or 0).
+mfmc_status encode_map(CUtensorMap *map, float *base, int P, size_t cap, int sw, int sh, int sd = 1,
+                       int l2promo = 256);
 int tma_tiles(const Model &m, int variant, int *tiles_x);
 // stream-ordered allocation on alloc_st (cudaMallocAsync) and release (cudaFreeAsync)
 mfmc_status tma_alloc_buffers(const Model &m, int variant, size_t ns, TmaBuffers *b, cudaStream_t alloc_st);
@@ -182,8 +185,8 @@ mfmc_status run_resident_steps(const Model &m, const StepCoef *coef, const float
 mfmc_status launch_finalize(const double *partials, int tiles, size_t ns, int n, double *ubar, double *ooi,
                             cudaStream_t st);
 mfmc_status launch_pad(const float *u0, float *padded, int n, int G, size_t ns, cudaStream_t st);
-// Row-streaming kernel: geometry, buffers and solve with band height bh.
-void rows_geometry(const Model &m, int *nbox, int *bw);
+// Warp-strip row-streaming kernel: buffers and solve; bh = rows per work range (0: the batch's
+// rows split evenly over the resident warps), rx = columns per thread (4).
 mfmc_status rows_alloc_buffers(const Model &m, int bh, size_t ns, TmaBuffers *b, cudaStream_t alloc_st);
 mfmc_status run_solve_rows_core(const Model &m, int bh, int rx, const StepCoef *coef, const float *u0, size_t ns,
                                 int nsteps, const int *steps_ps, float *uT, double *ubar, double *ooi,

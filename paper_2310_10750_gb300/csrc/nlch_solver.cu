@@ -341,7 +341,7 @@ bool algo_supported(const Model &m, int algo) {
         case MFMC_ALGO_PREFIX: return constant && tile_launcher(m.R) != nullptr;
         case MFMC_ALGO_PREFIX_KAHAN:
         case MFMC_ALGO_PREFIX_TMA: return constant && tma_launcher(m.R) != nullptr;
-        case MFMC_ALGO_ROWS: return constant && (rows_supported(m, 2) || rows_supported(m, 4));
+        case MFMC_ALGO_ROWS: return constant && rows_supported(m, 4);
         case MFMC_ALGO_RESIDENT: {
             if (!constant || resident_launcher(m.R) == nullptr) return false;
             const int nt = resident_threads(m.d.n);
@@ -420,21 +420,24 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-mfmc_status encode_map(CUtensorMap *map, float *base, int P, size_t cap, int sw, int sh) {
+mfmc_status encode_map(CUtensorMap *map, float *base, int P, size_t cap, int sw, int sh, int sd, int l2promo) {
     auto enc = tensor_map_encoder();
     if (!enc) return fail(MFMC_ECUDA, "cuTensorMapEncodeTiled is unavailable");
     const cuuint64_t dims[3] = {(cuuint64_t)P, (cuuint64_t)P, (cuuint64_t)cap};
     const cuuint64_t strides[2] = {(cuuint64_t)P * sizeof(float), (cuuint64_t)P * P * sizeof(float)};
-    const cuuint32_t box[3] = {(cuuint32_t)sw, (cuuint32_t)sh, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)sw, (cuuint32_t)sh, (cuuint32_t)sd};
     const cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     l2promo >= 256 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B
+                                    : (l2promo >= 128 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B
+                                                      : CU_TENSOR_MAP_L2_PROMOTION_NONE),
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(MFMC_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return MFMC_OK;
 }
 
-static mfmc_status ensure_pad_scratch(Model &m, size_t ns, int box_w, int box_h) {
+static mfmc_status ensure_pad_scratch(Model &m, size_t ns, int box_w, int box_h, int box_d = 1, int l2promo = 256) {
     const int G = (m.R + 3) & ~3, P = m.d.n + 2 * G;
     if (!m.d_status) {
         MFMC_CUDA(cudaMalloc((void **)&m.d_status, sizeof(int)));
@@ -451,13 +454,17 @@ static mfmc_status ensure_pad_scratch(Model &m, size_t ns, int box_w, int box_h)
         MFMC_CUDA(cudaMalloc((void **)&m.padB, bytes));
         m.pad_cap = ns;
     }
-    if (m.maps_valid && m.map_sw == box_w && m.map_sh == box_h) return MFMC_OK;
+    if (box_w == 0) return MFMC_OK;  // buffers only (the caller encodes its own maps)
+    if (m.maps_valid && m.map_sw == box_w && m.map_sh == box_h && m.map_sd == box_d && m.map_l2 == l2promo)
+        return MFMC_OK;
     m.maps_valid = 0;
-    mfmc_status s = encode_map(&m.mapA, m.padA, P, m.pad_cap, box_w, box_h);
-    if (s == MFMC_OK) s = encode_map(&m.mapB, m.padB, P, m.pad_cap, box_w, box_h);
+    mfmc_status s = encode_map(&m.mapA, m.padA, P, m.pad_cap, box_w, box_h, box_d, l2promo);
+    if (s == MFMC_OK) s = encode_map(&m.mapB, m.padB, P, m.pad_cap, box_w, box_h, box_d, l2promo);
     if (s != MFMC_OK) return s;
     m.map_sw = box_w;
     m.map_sh = box_h;
+    m.map_sd = box_d;
+    m.map_l2 = l2promo;
     m.maps_valid = 1;
     return MFMC_OK;
 }
@@ -591,91 +598,166 @@ mfmc_status run_solve_tma(Model &m, int kahan, int variant, const StepCoef *coef
 }
 
 // ----------------------------------------------------------------------------- row streaming
-void rows_geometry(const Model &m, int *nbox, int *bw) {
-    const int G = (m.R + 3) & ~3, P = m.d.n + 2 * G;
-    *nbox = (P + 255) / 256;
-    *bw = ((P + *nbox - 1) / *nbox + 3) & ~3;
+// Partials of the row-streaming kernel: one FP64 row sum per (sample, strip, row).
+static int rows_partials_per_sample(const Model &m) { return (m.d.n / 128) * m.d.n; }
+
+__global__ void rows_ooi_kernel(const float *plain, const float *padA, const float *padB, const int *steps_ps,
+                                int nsteps, int n, int P, int G, int strips, size_t ns, double *partials) {
+    const int lane = threadIdx.x & 31;
+    const long long total = (long long)ns * strips * n;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < total; r += warps) {
+        const long long col = r / n;
+        const int y = (int)(r - col * n);
+        const int sample = (int)(col / strips), strip = (int)(col - (long long)sample * strips);
+        const int ks = steps_ps ? steps_ps[sample] : nsteps;
+        const float *src = plain ? plain + (size_t)sample * n * n + (size_t)y * n + 128 * strip + 4 * lane
+                                 : ((ks & 1) ? padA : padB) + (size_t)sample * P * P + (size_t)(G + y) * P + G +
+                                       128 * strip + 4 * lane;
+        const float4 v = *reinterpret_cast<const float4 *>(src);
+        double rs = ((double)v.x + (double)v.y) + ((double)v.z + (double)v.w);
+        for (int off = 16; off > 0; off >>= 1) rs += __shfl_down_sync(0xffffffffu, rs, off);
+        if (lane == 0) partials[r] = rs;
+    }
+}
+
+// Geometry of the row-streaming kernel: 16 warps per CTA at most, n / 128 warps per sample, a
+// padded row of P floats read through a 4-D view (k pieces of P / k <= 256 floats, P / k a
+// multiple of 4 so each piece is a whole number of 16-byte units).
+static bool rows_geom(const Model &m, RowsGeom *g) {
+    const int n = m.d.n, G = (m.R + 3) & ~3, P = n + 2 * G;
+    if (n % 128 != 0 || n > 2048) return false;
+    g->strips = n / 128;
+    g->gs = 16 / g->strips;
+    g->warps = g->gs * g->strips;
+    g->P = P;
+    g->k = 0;
+    for (int k = 1; k <= 64; ++k)
+        if (P % k == 0 && P / k <= 256 && (P / k) % 4 == 0) {
+            g->k = k;
+            break;
+        }
+    if (g->k == 0) return false;
+    const RowsLauncher *L = rows_launcher(m.R);
+    if (!L) return false;
+    g->stage_floats = g->gs * L->ch * P;
+    g->smem = (size_t)L->nstg * g->stage_floats * sizeof(float) + 128;
+    return g->smem <= 227 * 1024;
+}
+
+// Tensor map of the padded fields [cap][P][P] as (P / k, k, P, cap): a box of (P / k, k, CH, gs)
+// is CH whole rows of gs samples.
+static mfmc_status encode_rows_map(CUtensorMap *map, float *base, const RowsGeom &g, size_t cap, int ch) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return fail(MFMC_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+    const int P = g.P, w = P / g.k;
+    const cuuint64_t dims[4] = {(cuuint64_t)w, (cuuint64_t)g.k, (cuuint64_t)P, (cuuint64_t)cap};
+    const cuuint64_t strides[3] = {(cuuint64_t)w * sizeof(float), (cuuint64_t)P * sizeof(float),
+                                   (cuuint64_t)P * P * sizeof(float)};
+    const cuuint32_t box[4] = {(cuuint32_t)w, (cuuint32_t)g.k, (cuuint32_t)ch, (cuuint32_t)g.gs};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(MFMC_ECUDA, "cuTensorMapEncodeTiled (rows) failed (%d)", (int)r);
+    return MFMC_OK;
 }
 
 mfmc_status rows_alloc_buffers(const Model &m, int bh, size_t ns, TmaBuffers *b, cudaStream_t alloc_st) {
     const RowsLauncher *L = rows_launcher(m.R);
-    if (!L) return fail(MFMC_EINVAL, "no row-streaming kernel for R = %d", m.R);
-    if (bh < 8) return fail(MFMC_EINVAL, "band height %d < 8", bh);
-    const int G = (m.R + 3) & ~3, P = m.d.n + 2 * G;
-    int nbox = 0, bw = 0;
-    rows_geometry(m, &nbox, &bw);
-    const int bands = (m.d.n + bh - 1) / bh;
-    const size_t bytes = ns * (size_t)P * P * sizeof(float);
+    RowsGeom g;
+    if (!L || !rows_geom(m, &g)) return fail(MFMC_EINVAL, "no row-streaming kernel for n = %d, R = %d", m.d.n, m.R);
+    if (bh != 0 && bh < 8) return fail(MFMC_EINVAL, "band height %d < 8", bh);
+    const size_t bytes = ns * (size_t)g.P * g.P * sizeof(float);
     MFMC_CUDA(cudaMallocAsync((void **)&b->padA, bytes, alloc_st));
     MFMC_CUDA(cudaMallocAsync((void **)&b->padB, bytes, alloc_st));
-    MFMC_CUDA(cudaMallocAsync((void **)&b->partials, ns * (size_t)bands * sizeof(double), alloc_st));
+    MFMC_CUDA(cudaMallocAsync((void **)&b->partials, ns * (size_t)rows_partials_per_sample(m) * sizeof(double),
+                              alloc_st));
     MFMC_CUDA(cudaMallocAsync((void **)&b->status, sizeof(int), alloc_st));
     MFMC_CUDA(cudaMemsetAsync(b->status, 0, sizeof(int), alloc_st));
     b->cap = ns;
-    mfmc_status s = encode_map(&b->mapA, b->padA, P, ns, bw, L->ch);
-    if (s == MFMC_OK) s = encode_map(&b->mapB, b->padB, P, ns, bw, L->ch);
+    mfmc_status s = encode_rows_map(&b->mapA, b->padA, g, ns, L->ch);
+    if (s == MFMC_OK) s = encode_rows_map(&b->mapB, b->padB, g, ns, L->ch);
     return s;
 }
 
-// threads = n / rx must be a whole number of warps and at most 512
+// The row-streaming kernel: constant kernel, integer R <= 8, 128-column strips (n % 128 == 0,
+// n <= 2048), four columns per thread.
 bool rows_supported(const Model &m, int rx) {
-    return m.d.kernel == MFMC_KERNEL_CONSTANT && rows_launcher(m.R) != nullptr && (rx == 2 || rx == 4) &&
-           m.d.n % (32 * rx) == 0 && m.d.n / rx <= 512;
+    RowsGeom g;
+    return m.d.kernel == MFMC_KERNEL_CONSTANT && m.integer_R && rx == 4 && rows_launcher(m.R) != nullptr &&
+           rows_geom(m, &g);
 }
 
 mfmc_status run_solve_rows_core(const Model &m, int bh, int rx, const StepCoef *coef, const float *u0, size_t ns,
                                 int nsteps, const int *steps_ps, float *uT, double *ubar, double *ooi,
                                 const TmaBuffers &b, cudaStream_t st) {
-    if (!rows_supported(m, rx)) return fail(MFMC_EINVAL, "row-streaming kernel unsupported (n = %d, %d columns)", m.d.n, rx);
+    if (!rows_supported(m, rx)) return fail(MFMC_EINVAL, "row-streaming kernel unsupported (n = %d, R = %d, %d columns)", m.d.n, m.R, rx);
     const RowsLauncher *L = rows_launcher(m.R);
-    if (!L) return fail(MFMC_EINVAL, "no row-streaming kernel for R = %d", m.R);
-    if (bh < 8) return fail(MFMC_EINVAL, "band height %d < 8", bh);
-    const int n = m.d.n, G = (m.R + 3) & ~3, P = n + 2 * G;
-    int nbox = 0, bw = 0;
-    rows_geometry(m, &nbox, &bw);
-    const int bands = (n + bh - 1) / bh;
+    RowsGeom g;
+    rows_geom(m, &g);
+    if (bh != 0 && bh < 8) return fail(MFMC_EINVAL, "band height %d < 8", bh);
+    const int n = m.d.n, G = (m.R + 3) & ~3, P = g.P;
     {
         const size_t total = ns * (size_t)P * (P / 4);
         const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 32);
-        pad_fields_kernel<<<blocks, 256, 0, st>>>(u0, b.padB, n, G, ns, 0, 0.f);
+        const int collar = m.d.bc == MFMC_BC_COLLAR;
+        pad_fields_kernel<<<blocks, 256, 0, st>>>(u0, b.padB, n, G, ns, collar, (float)m.d.bc_value);
+        if (collar) pad_fields_kernel<<<blocks, 256, 0, st>>>(u0, b.padA, n, G, ns, collar, (float)m.d.bc_value);
         MFMC_LAUNCHED("nlch_solver launch 6");
     }
-    const int ri = rx == 4 ? 0 : 1;
-    const int threads = n / rx;
-    const size_t smem = (size_t)4 * L->ch * bw * nbox * sizeof(float) + 1024;
     int dev = 0, sms = 0;
     MFMC_CUDA(cudaGetDevice(&dev));
     MFMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const long long total = (long long)ns * bands;
-    if (total > (1ll << 30)) return fail(MFMC_EINVAL, "too many bands in one solve");
-    if (total == 0) return MFMC_OK;
-    const int grid = (int)std::min<long long>(total, (long long)sms * L->blocks_per_sm[ri](threads, smem));
+    const long long rows = (long long)((ns + g.gs - 1) / g.gs) * n;  // (sample group, row) order
+    if (rows == 0) return MFMC_OK;
+    // one range per CTA (at least 4R + 8 rows each, so the halo rows stay a minor share), or
+    // bands taken in turn by the resident CTAs
+    const int threads = 32 * g.warps;
+    const long long ctas = bh > 0 ? (rows + bh - 1) / bh : rows / (4 * m.R + 8) + 1;
+    const int grid =
+        (int)std::max<long long>(1, std::min<long long>((long long)sms * L->blocks_per_sm(threads, g.smem), ctas));
     const CUtensorMap *src = &b.mapB;
     float *dstbuf = b.padA;
     for (int k = 1; k <= nsteps; ++k) {
         const bool last = k == nsteps;
         RowsArgs a;
-        a.dst = (last && !steps_ps) ? nullptr : dstbuf;
-        a.dst_plain = (last && !steps_ps) ? uT : nullptr;
-        a.coef = coef;
-        a.partials = b.partials;
-        a.status = b.status;
-        a.steps_ps = steps_ps;
-        a.step = k;
-        a.n = n;
-        a.P = P;
-        a.BW = bw;
-        a.nbox = nbox;
-        a.BH = bh;
-        a.bands = bands;
-        a.total = (int)total;
-        a.last = (last && !steps_ps) ? 1 : 0;
-        mfmc_status s = L->fn[ri](*src, a, grid, threads, smem, st);
+        // the last step stores to the caller's field when asked, else to the scratch buffer,
+        // from which rows_ooi_kernel reduces the OoI
+        a.t.dst = (last && !steps_ps && uT) ? nullptr : dstbuf;
+        a.t.dst_plain = (last && !steps_ps) ? uT : nullptr;
+        a.t.coef = coef;
+        a.t.partials = b.partials;
+        a.t.status = b.status;
+        a.t.steps_ps = steps_ps;
+        a.t.step = k;
+        a.t.n = n;
+        a.t.P = P;
+        a.t.tiles_x = g.strips;
+        a.t.tiles = g.strips * n;
+        a.t.total = 0;
+        a.t.last = 0;
+        a.t.periodic = m.d.bc == MFMC_BC_PERIODIC;
+        a.t.wsq = nullptr;
+        a.ns = (int)ns;
+        a.gs = g.gs;
+        a.strips = g.strips;
+        a.rows = rows;
+        a.band = bh;
+        a.stage_floats = g.stage_floats;
+        mfmc_status s = L->fn(*src, a, grid, threads, g.smem, st);
         if (s != MFMC_OK) return s;
         src = (dstbuf == b.padA) ? &b.mapA : &b.mapB;
         dstbuf = (dstbuf == b.padA) ? b.padB : b.padA;
     }
-    finalize_ooi_kernel<<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(b.partials, bands, ns,
+    {
+        const long long warps = std::min<long long>((long long)ns * g.strips * n, (long long)sms * 64);
+        const unsigned blocks = (unsigned)std::max<long long>(1, (warps + 7) / 8);
+        rows_ooi_kernel<<<blocks, 256, 0, st>>>((uT && !steps_ps) ? uT : nullptr, b.padA, b.padB, steps_ps, nsteps,
+                                                n, P, G, g.strips, ns, b.partials);
+        MFMC_LAUNCHED("nlch_solver launch 7a");
+    }
+    finalize_ooi_kernel<<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(b.partials, g.strips * n, ns,
                                                                        1.0 / ((double)n * n), ubar, ooi);
     MFMC_LAUNCHED("nlch_solver launch 7");
     return MFMC_OK;
@@ -684,22 +766,22 @@ mfmc_status run_solve_rows_core(const Model &m, int bh, int rx, const StepCoef *
 mfmc_status run_solve_rows(Model &m, int bh, int rx, const StepCoef *coef, const float *u0, size_t ns, int nsteps,
                            float *uT, double *ubar, double *ooi, cudaStream_t st) {
     const RowsLauncher *L = rows_launcher(m.R);
-    if (!L) return fail(MFMC_EINVAL, "no row-streaming kernel for R = %d", m.R);
-    if (bh < 8) return fail(MFMC_EINVAL, "band height %d < 8", bh);
-    int nbox = 0, bw = 0;
-    rows_geometry(m, &nbox, &bw);
-    const int bands = (m.d.n + bh - 1) / bh;
-    mfmc_status s = ensure_pad_scratch(m, ns, bw, L->ch);
-    if (s == MFMC_OK) s = grow_buffer(&m.partials, &m.partials_cap, ns * (size_t)bands);
+    RowsGeom g;
+    if (!L || !rows_geom(m, &g)) return fail(MFMC_EINVAL, "no row-streaming kernel for n = %d, R = %d", m.d.n, m.R);
+    if (bh != 0 && bh < 8) return fail(MFMC_EINVAL, "band height %d < 8", bh);
+    // the padded buffers of the model, with tensor maps of the row view
+    mfmc_status s = ensure_pad_scratch(m, ns, 0, 0);
+    if (s == MFMC_OK) s = grow_buffer(&m.partials, &m.partials_cap, ns * (size_t)rows_partials_per_sample(m));
     if (s != MFMC_OK) return s;
     TmaBuffers b;
     b.padA = m.padA;
     b.padB = m.padB;
-    b.mapA = m.mapA;
-    b.mapB = m.mapB;
     b.cap = m.pad_cap;
     b.partials = m.partials;
     b.status = m.d_status;
+    s = encode_rows_map(&b.mapA, b.padA, g, b.cap, L->ch);
+    if (s == MFMC_OK) s = encode_rows_map(&b.mapB, b.padB, g, b.cap, L->ch);
+    if (s != MFMC_OK) return s;
     return run_solve_rows_core(m, bh, rx, coef, u0, ns, nsteps, nullptr, uT, ubar, ooi, b, st);
 }
 
@@ -741,10 +823,7 @@ mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0,
     if (algo == MFMC_ALGO_PREFIX_TMA)
         return run_solve_tma(m, 0, m.tma_variant, coef, u0, ns, nsteps, uT, ubar, ooi, st);
     if (algo == MFMC_ALGO_PREFIX_KAHAN) return run_solve_tma(m, 1, 0, coef, u0, ns, nsteps, uT, ubar, ooi, st);
-    if (algo == MFMC_ALGO_ROWS) {
-        const int rx = rows_supported(m, m.rows_rx) ? m.rows_rx : 6 - m.rows_rx;
-        return run_solve_rows(m, m.rows_bh, rx, coef, u0, ns, nsteps, uT, ubar, ooi, st);
-    }
+    if (algo == MFMC_ALGO_ROWS) return run_solve_rows(m, m.rows_bh, 4, coef, u0, ns, nsteps, uT, ubar, ooi, st);
     if (algo == MFMC_ALGO_RESIDENT) return run_resident_steps(m, coef, u0, ns, nsteps, nullptr, uT, ubar, ooi, st);
     int tiles_x = 0;
     const int tiles = tiles_for(m, algo, &tiles_x);

@@ -1,264 +1,367 @@
-// Row-streaming step kernel (constant kernel, R <= 12).
+// Row-streaming step kernel (constant kernel, R <= 8, n % 128 == 0, n <= 2048).
 //
-// A work item is a band of BH lattice rows of one sample, across the full width: thread t
-// owns the four columns 4t .. 4t+3 (n/4 threads) and walks down the band's BH + 2R input
-// rows once.  Each input row is loaded (float4) from a ring of shared-memory chunks that
-// TMA fills from the ghost-framed field (chunks of CH >= R rows, NCH stages, the copy of a
-// chunk two ahead in flight while the current one is read).  From the row the thread
-// forms an in-register prefix sum, one segment sum per distinct disc-row half-width, and
-// adds each to the 2R+1 outputs that row touches; the accumulators form a ring of 2R+1
-// slots, so after row q the output q - 2R is complete and is finished (update, projection,
-// store with ghost images, OoI partial at the last step).  Unrolling the row loop by the
-// ring period 2R+1 keeps every slot index static.  Every halo row is summed once per band
-// instead of once per output block, which is what makes this cheaper than the tile
-// kernels: about 2R+1 + (4+2R+4 w)/4 * (BH+2R)/BH + 5 FP32 instructions per point,
-// w = number of distinct half-widths.
+// A CTA of 16 warps (fewer when 16 is no multiple of n / 128) streams whole rows of GS
+// consecutive samples down a range of rows: warp w takes the 128-column strip w % (n / 128) of
+// sample w / (n / 128) of its group, lane l the strip's columns 4l .. 4l+3.  The batch's rows,
+// ordered by (sample group, row), are split evenly over the CTAs (or into fixed bands taken in
+// turn); a CTA's range is cut into segments at group boundaries, and each segment's rows are
+// walked downwards together with an R-row halo above and below (always downwards: each output's
+// disc rows are then summed top to bottom whatever the split, so results do not depend on it).
+// The rows arrive through a ring of shared-memory
+// chunks: one TMA box per chunk carries CH whole ghost-framed rows (P = n + 2 R4 floats, read
+// through a four-dimensional view that splits a row into k pieces of at most 256 floats) of
+// all GS samples, so every byte of a field is fetched once; the copy of the next chunk is
+// issued when a chunk is entered.  All warps run the same instructions on the same rows.
+//
+// From each staged row a lane forms its window's centre sums and one segment sum per distinct
+// disc-row half-width, and adds each to the 2R + 1 output rows that the row touches; the
+// accumulators (packed FP32 pairs) form a ring of 2R + 1 slots, so every staged row is summed
+// once per segment.  After staged row q the output row q - 2R is complete and is finished at
+// once (update, projection, store with ghost images).  The row loop is unrolled by the ring
+// period 2R + 1, which keeps every slot index static.  The OoI is reduced afterwards from the
+// final fields (rows_ooi_kernel), so it does not depend on how the rows were split.
 #pragma once
 
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "tma_step.cuh"
 
 namespace mfmc {
 
 struct RowsArgs {
-    float *dst;            // padded destination (nullptr: no field output)
-    float *dst_plain;      // unpadded destination at the last step, or nullptr
-    const StepCoef *coef;
-    double *partials;      // [ns][bands]
-    int *status;
-    const int *steps_ps;   // per-sample step counts, or nullptr
-    int step;
-    int n, P, BW, nbox, BH, bands, total, last;
+    TmaArgs t;             // outputs, coefficients, status, step counts, step, n, P, periodic
+    int ns;                // samples
+    int gs;                // samples per CTA
+    int strips;            // n / 128: warps per sample
+    long long rows;        // groups * n: the batch's rows in (group, row) order
+    int band;              // rows per work range; 0: rows / CTAs, one range per CTA
+    int stage_floats;      // gs * CH * P
 };
 
-template <int R, int RX>
+template <int R>
 struct RowsCfg {
     static constexpr int R4 = (R + 3) & ~3;
-    static constexpr int CH = R < 8 ? 8 : R;  // chunk rows; >= R so a chunk two back is free
-    static constexpr int NCH = 4;              // ring stages
-    static constexpr int PER = 2 * R + 1;      // accumulator ring period
-    static constexpr int WIN = RX + 2 * R4;    // floats a thread reads per row
+    static constexpr int CH = 8;                         // rows per chunk
+    // a stage is refilled (with the chunk after the next) once no row of it is read again: the
+    // oldest row still read is the centre row R rows back, so 2 + ceil(R / CH) stages suffice
+    static constexpr int NSTG = 2 + (R + CH - 1) / CH;
+    // accumulator ring slots: the 2R + 1 output rows a staged row touches (larger rings that
+    // are multiples of CH would make chunk boundaries static but spill registers)
+    static constexpr int S = 2 * R + 1;
+    static constexpr int MAXW = 16;                      // warps per CTA at most
 };
 
-// RX consecutive floats (RX = 2 or 4) from shared memory.
-template <int RX>
-__device__ __forceinline__ void load_vec(const float *p, float *out) {
-    if constexpr (RX == 4) {
-        const float4 x = *reinterpret_cast<const float4 *>(p);
-        out[0] = x.x;
-        out[1] = x.y;
-        out[2] = x.z;
-        out[3] = x.w;
-    } else {
-        const float2 x = *reinterpret_cast<const float2 *>(p);
-        out[0] = x.x;
-        out[1] = x.y;
-    }
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1, int c2,
+                                            int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
+        "[%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
 }
 
-template <int RX>
-__device__ __forceinline__ void store_vec(float *p, const float *v) {
-    if constexpr (RX == 4) {
-        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    } else {
-        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+// A segment of the walk: sample group, first row and rows (len = 0: end of the walk).
+struct RowsSegInfo {
+    int group, y0, len;
+};
+
+// The CTA's walk over its row ranges (thread 0 only; results go through shared memory).
+struct RowsSegIter {
+    long long q, qend;     // the part of the current range still to walk
+    long long range;       // index of the current range
+    long long nct;
+    __device__ void set_range(const RowsArgs &a) {
+        if (a.band > 0) {
+            q = range * a.band;
+            qend = q + a.band < a.rows ? q + a.band : a.rows;
+        } else {
+            const long long base = a.rows / nct, rem = a.rows % nct;
+            q = base * range + (range < rem ? range : rem);
+            qend = q + base + (range < rem ? 1 : 0);
+        }
+        if (q > a.rows) q = qend = a.rows;
     }
+    __device__ void init(const RowsArgs &a) {
+        nct = gridDim.x;
+        range = blockIdx.x;
+        set_range(a);
+    }
+    // The next segment with an active sample, in walk order; len = 0 at the end.
+    __device__ RowsSegInfo next(const RowsArgs &a) {
+        const int n = a.t.n;
+        RowsSegInfo s;
+        for (;;) {
+            if (q >= qend) {
+                range += nct;
+                if (a.band == 0 || range * a.band >= a.rows) {
+                    s.group = s.y0 = s.len = 0;
+                    return s;
+                }
+                set_range(a);
+                continue;
+            }
+            const long long col = q / n;
+            const long long hi = (col + 1) * n < qend ? (col + 1) * n : qend;
+            s.group = (int)col;
+            s.y0 = (int)(q - col * n);
+            s.len = (int)(hi - q);
+            q = hi;
+            bool any = false;
+            for (int w = 0; w < a.gs; ++w) {
+                const int smp = a.gs * s.group + w;
+                any = any || (smp < a.ns && (a.t.steps_ps == nullptr || a.t.step <= a.t.steps_ps[smp]));
+            }
+            if (any) return s;
+        }
+    }
+};
+
+// Shared state of a CTA: the walk, the producer's position and two segment slots (the
+// consumer's current segment and the next one).
+struct RowsShared {
+    RowsSegIter it;
+    RowsSegInfo seg[2];
+    int pslot, pc, pnch;   // producer: segment slot, next chunk in it, its chunk count
+    int pg;                // chunks issued
+};
+
+template <int R>
+__device__ __noinline__ void rows_issue(const RowsArgs &a, RowsShared &sh, const CUtensorMap *map, float *ring,
+                                        uint64_t *bar) {
+    using C = RowsCfg<R>;
+    if (sh.pc >= sh.pnch) {
+        sh.pslot ^= 1;
+        sh.pnch = sh.seg[sh.pslot].len > 0 ? (sh.seg[sh.pslot].len + 2 * R + C::CH - 1) / C::CH : 0;
+        sh.pc = 0;
+        if (sh.pnch == 0) return;
+    }
+    const RowsSegInfo &s = sh.seg[sh.pslot];
+    const int st = sh.pg % C::NSTG;
+    // lattice rows of chunk c: y0 - R + c CH + [0, CH); padded row = G + lattice row (G = R4)
+    const int ylo = s.y0 - R + sh.pc * C::CH;
+    mbar_expect_tx(&bar[st], (uint32_t)a.stage_floats * sizeof(float));
+    tma_load_4d(ring + (size_t)st * a.stage_floats, map, &bar[st], 0, 0, C::R4 + ylo, a.gs * s.group);
+    ++sh.pc;
+    ++sh.pg;
 }
 
-// RX: columns per thread (4, or 2 for twice the threads at ~12 % more adds per point).
-template <int R, int RX>
-__global__ void __launch_bounds__(512) step_rows_kernel(const __grid_constant__ CUtensorMap map, RowsArgs a) {
-    using C = RowsCfg<R, RX>;
-    constexpr int CH = C::CH, NCH = C::NCH, PER = C::PER, WIN = C::WIN, R4 = C::R4;
-    constexpr DiscRows<R> disc{};
+// Per-segment state of a warp.
+struct RowsSeg {
+    const float *win0;   // the lane's window start in its sample's first row of stage 0
+    int g0;              // stream index of the segment's first chunk
+    int nrows;           // rows walked: len + 2R
+    int sample, y0, x;   // sample, lattice row of the first output row, the lane's first column
+    bool active;
+    TmaRowCtx ctx;
+    StepCoef cf;
+};
+
+template <int R>
+struct RowsAcc {
+    float2 acc[RowsCfg<R>::S][2];  // slot j mod S: output row j (at most 2R + 1 live at a time)
+    const float *rp, *cp;          // the lane's window in the staged row, its centre R rows back
+    int cst;                       // stage of the centre row's chunk
+};
+
+__device__ __forceinline__ constexpr int rows_mod(int a, int m) { return ((a % m) + m) % m; }
+
+template <int R>
+struct RowsPlan {
+    static constexpr DiscClasses<R> cls{};
+    __host__ __device__ static constexpr bool serves(int dy, int c) { return cls.of[dy < 0 ? -dy : dy] == c; }
+};
+
+// Adds the class-c segment sums of staged row (ring position K) to every ring slot that the
+// class serves: dy with cls.of[|dy|] == c, output row q - R - dy in slot (K - R - dy) mod S.
+// The output row's first staged row (dy = -R) starts its slot.
+template <int R, int K, int c, int... D>
+__device__ __forceinline__ void rows_class(RowsAcc<R> &t, const RowWin<R> &win, std::integer_sequence<int, D...>) {
+    float h[4];
+    class_sums<R, RowsPlan<R>::cls.width[c]>(win, h);
+    const float2 h01 = make_float2(h[0], h[1]), h23 = make_float2(h[2], h[3]);
+    auto add = [&](auto dc) {
+        constexpr int dy = decltype(dc)::value - R;
+        if constexpr (RowsPlan<R>::serves(dy, c)) {
+            constexpr int slot = rows_mod(K - R - dy, RowsCfg<R>::S);
+            if constexpr (dy == -R) {
+                t.acc[slot][0] = h01;
+                t.acc[slot][1] = h23;
+            } else {
+                t.acc[slot][0] = __fadd2_rn(t.acc[slot][0], h01);
+                t.acc[slot][1] = __fadd2_rn(t.acc[slot][1], h23);
+            }
+        }
+    };
+    (add(std::integral_constant<int, D>{}), ...);
+}
+
+template <int R, int K, int... Cs>
+__device__ __forceinline__ void rows_classes(RowsAcc<R> &t, const RowWin<R> &win, std::integer_sequence<int, Cs...>) {
+    (rows_class<R, K, Cs>(t, win, std::make_integer_sequence<int, 2 * R + 1>{}), ...);
+}
+
+// Staged row q = q0 + K of the segment (q0 a multiple of S, K static: the ring position).
+// Returns false when a chunk wait ran out of its bound.
+template <int R, int K>
+__device__ __forceinline__ bool rows_row(RowsAcc<R> &t, const RowsArgs &a, const RowsSeg &sg, int q0, RowsShared &sh,
+                                         const CUtensorMap *map, float *ring, uint64_t *bar) {
+    using C = RowsCfg<R>;
+    const int q = q0 + K;
+    t.rp += a.t.P;
+    t.cp += a.t.P;
+    if (q % C::CH == 0) {
+        const int g = sg.g0 + q / C::CH;
+        const int st = g % C::NSTG;
+        t.rp = sg.win0 + st * a.stage_floats;
+        long long spins = 0;
+        bool ok = true;
+        while (!mbar_try_wait(&bar[st], (uint32_t)((g / C::NSTG) & 1)))
+            if (++spins > kWaitLimit) {
+                ok = false;
+                break;
+            }
+        // every thread is past the rows of the stage that the next copy overwrites
+        if (!__syncthreads_and(ok)) return false;
+        if (threadIdx.x == 0) rows_issue<R>(a, sh, map, ring, bar);
+    }
+    // the centre row q - R enters a new chunk: the stage after the previous centre chunk's
+    if (q >= R && (q - R) % C::CH == 0) {
+        t.cst = t.cst + 1 == C::NSTG ? 0 : t.cst + 1;
+        t.cp = sg.win0 + t.cst * a.stage_floats + C::R4;
+    }
+    RowWin<R> win;
+    row_window<R>(t.rp, win);
+    rows_classes<R, K>(t, win, std::make_integer_sequence<int, RowsPlan<R>::cls.count>{});
+    if (q >= 2 * R && (opaque_u32(sg.active) != 0)) {  // output row q - 2R is complete
+        constexpr int slot = rows_mod(K - 2 * R, C::S);
+        const float4 uc = *reinterpret_cast<const float4 *>(t.cp);  // its centre row, q - R
+        double unused = 0.0;
+        tma_emit_row<R, false, false, true>(a.t, sg.ctx, sg.cf, uc, t.acc[slot][0], t.acc[slot][1],
+                                            sg.y0 + q - 2 * R, sg.x, false, unused);
+    }
+    return true;
+}
+
+template <int R, int... Ks>
+__device__ __forceinline__ bool rows_block(RowsAcc<R> &t, const RowsArgs &a, const RowsSeg &sg, int q0,
+                                           RowsShared &sh, const CUtensorMap *map, float *ring, uint64_t *bar,
+                                           int *gfail, std::integer_sequence<int, Ks...>) {
+    using C = RowsCfg<R>;
+    bool ok = true;
+    auto one = [&](auto kc) {
+        constexpr int K = decltype(kc)::value;
+        if (ok && q0 + K < sg.nrows) {
+            ok = rows_row<R, K>(t, a, sg, q0, sh, map, ring, bar);
+            if (!ok) *gfail = sg.g0 + (q0 + K) / C::CH;
+        }
+    };
+    (one(std::integral_constant<int, Ks>{}), ...);
+    return ok;
+}
+
+template <int R>
+__global__ void __launch_bounds__(RowsCfg<R>::MAXW * 32, 1) step_rows_kernel(const __grid_constant__ CUtensorMap map,
+                                                                           RowsArgs a) {
+    using C = RowsCfg<R>;
     extern __shared__ unsigned char smem_raw[];
-    float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t full[NCH];
-    __shared__ double red[16];
-    __shared__ int abort_flag;
-
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int n = a.n, G = R4;
-    const int stage_floats = CH * a.BW * a.nbox;
-    const uint32_t chunk_bytes = (uint32_t)stage_floats * sizeof(float);
-    if (tid == 0) {
-        for (int i = 0; i < NCH; ++i) mbar_init(&full[i], 1);
+    float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    __shared__ __align__(8) uint64_t bar[C::NSTG];
+    __shared__ RowsShared sh;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sl = warp / a.strips, strip = warp - sl * a.strips;  // sample in the group, strip
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < C::NSTG; ++i) mbar_init(&bar[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        abort_flag = 0;
+        sh.it.init(a);
+        sh.seg[0] = sh.it.next(a);
+        sh.seg[1] = sh.it.next(a);
+        sh.pslot = 1;  // the first issue advances to slot 0
+        sh.pc = sh.pnch = 0;
+        sh.pg = 0;
+        rows_issue<R>(a, sh, &map, ring, bar);
     }
     __syncthreads();
-
-    // offsets (within a chunk's row 0) of this thread's WIN/RX vectors of a row: padded
-    // columns RX tid + RX q, boxes laid out one after the other, each [CH][BW]
-    int off[WIN / RX];
+    RowsAcc<R> t;
 #pragma unroll
-    for (int q = 0; q < WIN / RX; ++q) {
-        const int col = RX * tid + RX * q;
-        off[q] = (col / a.BW) * (CH * a.BW) + (col % a.BW);
+    for (int k = 0; k < C::S; ++k) t.acc[k][0] = t.acc[k][1] = make_float2(0.f, 0.f);
+
+    RowsSeg sg;
+    sg.win0 = ring + sl * C::CH * a.t.P + 128 * strip + 4 * lane;
+    sg.g0 = 0;
+    int gfail = 0;
+    bool ok = true;
+    for (int k = 0; ok; ++k) {
+        const RowsSegInfo s = sh.seg[k & 1];
+        if (s.len == 0) break;
+        sg.nrows = s.len + 2 * R;
+        // the centre row q - R enters chunk 0 at q = R (rows q < R have no centre in use): start
+        // one stage before the segment's first chunk
+        t.cst = (sg.g0 + C::NSTG - 1) % C::NSTG;
+        t.rp = t.cp = sg.win0;
+        sg.sample = a.gs * s.group + sl;
+        sg.y0 = s.y0;
+        sg.x = 128 * strip + 4 * lane;
+        sg.active = sg.sample < a.ns && (a.t.steps_ps == nullptr || a.t.step <= a.t.steps_ps[sg.sample]);
+        const int smp = sg.active ? sg.sample : 0;
+        sg.cf = a.t.coef[smp];
+        sg.ctx = tma_row_ctx<R>(a.t, smp, 128 * strip + 4 * lane, s.y0, s.len);
+        for (int q0 = 0; ok && q0 < sg.nrows; q0 += C::S)
+            ok = rows_block<R>(t, a, sg, q0, sh, &map, ring, bar, &gfail, std::make_integer_sequence<int, C::S>{});
+        sg.g0 += (sg.nrows + C::CH - 1) / C::CH;
+        __syncthreads();  // every thread has read slot k & 1
+        if (ok && threadIdx.x == 0) sh.seg[k & 1] = sh.it.next(a);
+        __syncthreads();
     }
-    const int coff = ((RX * tid + R4) / a.BW) * (CH * a.BW) + ((RX * tid + R4) % a.BW);  // centre vector
-
-    uint32_t gchunk = 0;  // chunks consumed by this CTA so far (ring position and barrier phase)
-    const int rows = a.BH + 2 * R;
-    const int nchunks = (rows + CH - 1) / CH;
-
-    for (int item = blockIdx.x; item < a.total; item += gridDim.x) {
-        const int sample = item / a.bands, band = item - sample * a.bands;
-        if (a.steps_ps != nullptr && a.step > a.steps_ps[sample]) continue;
-        const bool last = a.last || (a.steps_ps != nullptr && a.step == a.steps_ps[sample]);
-        const int y0 = band * a.BH;
-        auto issue = [&](int c) {
-            const uint32_t g = gchunk + c;
-            const int st = g % NCH;
-            float *dstc = ring + st * stage_floats;
-            mbar_expect_tx(&full[st], chunk_bytes);
-            for (int b = 0; b < a.nbox; ++b)
-                tma_load_3d(dstc + b * CH * a.BW, &map, &full[st], b * a.BW, G + y0 - R + c * CH, sample);
-        };
-        if (tid == 0)
-            for (int c = 0; c < NCH - 2 && c < nchunks; ++c) issue(c);
-
-        float acc[PER][RX];
-#pragma unroll
-        for (int k = 0; k < PER; ++k)
-#pragma unroll
-            for (int i = 0; i < RX; ++i) acc[k][i] = 0.f;
-        const StepCoef cf = a.coef[sample];
-        double part = 0.0;
-        bool aborted = false;
-
-        for (int q0 = 0; q0 < rows; q0 += PER) {
-#pragma unroll
-            for (int m = 0; m < PER; ++m) {
-                const int q = q0 + m;
-                if (q < rows) {
-                    if (q % CH == 0) {
-                        const int c = q / CH;
-                        __syncthreads();  // every thread is past chunk c-1: chunk c-2 is free
-                        if (tid == 0 && c + NCH - 2 < nchunks) issue(c + NCH - 2);
-                        const uint32_t g = gchunk + c;
-                        long long spins = 0;
-                        while (!mbar_try_wait(&full[g % NCH], (g / NCH) & 1)) {
-                            if (++spins > kWaitLimit) {
-                                abort_flag = 1;
-                                break;
-                            }
-                        }
-                        __syncthreads();
-                        if (abort_flag) {
-                            aborted = true;
-                            break;
-                        }
-                    }
-                    const float *rowp = ring + ((gchunk + q / CH) % NCH) * stage_floats + (q % CH) * a.BW;
-                    float v[WIN];
-#pragma unroll
-                    for (int t = 0; t < WIN / RX; ++t) load_vec<RX>(rowp + off[t], v + RX * t);
-                    float p[RX + 2 * R + 1];
-                    p[0] = 0.f;
-#pragma unroll
-                    for (int k = 0; k < RX + 2 * R; ++k) p[k + 1] = p[k] + v[R4 - R + k];
-                    // row q adds to outputs q - 2R + kk, kk = 0..2R, with dy = R - kk
-#pragma unroll
-                    for (int kk = 0; kk < PER; ++kk) {
-                        const int dyy = R - kk;
-                        const int w = disc.w[dyy < 0 ? -dyy : dyy];
-                        const int slot = (m + kk + 1) % PER;
-#pragma unroll
-                        for (int i = 0; i < RX; ++i) acc[slot][i] += p[i + R + w + 1] - p[i + R - w];
-                    }
-                    // output o = q - 2R is complete
-                    const int o = q - 2 * R;
-                    const int slot0 = (m + 1) % PER;
-                    if (o >= 0) {
-                        const int qc = o + R;  // its centre row
-                        float uc[RX];
-                        load_vec<RX>(ring + ((gchunk + qc / CH) % NCH) * stage_floats + (qc % CH) * a.BW + coff, uc);
-                        float out[RX];
-#pragma unroll
-                        for (int i = 0; i < RX; ++i) {
-                            const float sd = fmaf(-cf.c0, uc[i], acc[slot0][i]);
-                            const float vv = uc[i] + fmaf(cf.c1, sd, cf.c2 * uc[i]);
-                            out[i] = fminf(1.f, fmaxf(-1.f, vv));
-                        }
-                        const int y = y0 + o, x = RX * tid;
-                        if (y < n) {
-                            if (a.dst_plain) {
-                                store_vec<RX>(a.dst_plain + (size_t)sample * n * n + (size_t)y * n + x, out);
-                            } else if (a.dst) {
-                                float *d = a.dst + (size_t)sample * a.P * a.P;
-                                const int rws[3] = {G + y, y < G ? G + y + n : -1, y >= n - G ? G + y - n : -1};
-                                const int cls[3] = {G + x, x < G ? G + x + n : -1, x >= n - G ? G + x - n : -1};
-#pragma unroll
-                                for (int r2 = 0; r2 < 3; ++r2) {
-                                    if (rws[r2] < 0) continue;
-#pragma unroll
-                                    for (int c2 = 0; c2 < 3; ++c2) {
-                                        if (cls[c2] < 0) continue;
-                                        store_vec<RX>(d + (size_t)rws[r2] * a.P + cls[c2], out);
-                                    }
-                                }
-                            }
-                            if (last) {
-                                if constexpr (RX == 4)
-                                    part += ((double)out[0] + (double)out[1]) + ((double)out[2] + (double)out[3]);
-                                else
-                                    part += (double)out[0] + (double)out[1];
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int i = 0; i < RX; ++i) acc[slot0][i] = 0.f;
-                }
-            }
-            if (aborted) break;
-        }
-        if (aborted) {
-            if (tid == 0) atomicExch(a.status, 1);
-            break;
-        }
-        gchunk += nchunks;
-        if (last) {
-            for (int off2 = 16; off2 > 0; off2 >>= 1) part += __shfl_down_sync(0xffffffffu, part, off2);
-            if ((tid & 31) == 0) red[tid >> 5] = part;
-            __syncthreads();
-            if (tid == 0) {
-                double t = 0.0;
-                for (int i = 0; i < (nt + 31) / 32; ++i) t += red[i];
-                a.partials[(size_t)sample * a.bands + band] = t;
+    if (!ok && threadIdx.x == 0) {
+        // A chunk wait ran out of its bound (only a copy that never lands can cause it): report,
+        // then wait, again bounded, for each copy issued and not consumed, so that none still
+        // targets the ring when the CTA exits unless that wait runs out as well.
+        atomicExch(a.t.status, 1);
+        for (int g = gfail; g < sh.pg; ++g) {
+            long long spins = 0;
+            while (!mbar_try_wait(&bar[g % C::NSTG], (uint32_t)((g / C::NSTG) & 1)) && ++spins < kWaitLimit) {
             }
         }
-        __syncthreads();  // the ring is reused by the next item
     }
 }
 
-struct RowsLauncher {
-    int ch;  // chunk rows (TMA box height)
-    // [0]: 4 columns per thread, [1]: 2 columns per thread
-    mfmc_status (*fn[2])(const CUtensorMap &, const RowsArgs &, int grid, int threads, size_t smem, cudaStream_t);
-    int (*blocks_per_sm[2])(int threads, size_t smem);
+// FP64 sum of every (sample, strip, row) of the final fields into partials[ns][strips][n] (lane
+// sums of four values, then a fixed shuffle tree), read from the unpadded fields `plain` when
+// given, else from the ghost-framed buffer that holds each sample's last step: A after an odd
+// number of steps, B after an even one (steps_ps: per-sample step counts, or nsteps for all).
+__global__ void rows_ooi_kernel(const float *plain, const float *padA, const float *padB, const int *steps_ps,
+                                int nsteps, int n, int P, int G, int strips, size_t ns, double *partials);
+
+// Geometry of the row-streaming kernel for a lattice: samples per CTA, warps, the split of a
+// padded row into k pieces for the tensor map, and the dynamic shared memory.
+struct RowsGeom {
+    int strips, gs, warps, k, P, stage_floats;
+    size_t smem;
 };
 
-template <int R, int RX>
+struct RowsLauncher {
+    int ch, nstg;
+    mfmc_status (*fn)(const CUtensorMap &, const RowsArgs &, int grid, int threads, size_t smem, cudaStream_t);
+    int (*blocks_per_sm)(int threads, size_t smem);
+};
+
+template <int R>
 mfmc_status launch_rows(const CUtensorMap &map, const RowsArgs &a, int grid, int threads, size_t smem,
                         cudaStream_t st) {
-    auto kern = step_rows_kernel<R, RX>;
-    static size_t attr = 0;
-    if (smem > attr) {
-        MFMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = smem;
-    }
+    auto kern = step_rows_kernel<R>;
+    MFMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, threads, smem, st>>>(map, a);
     MFMC_LAUNCHED("rows_step launch");
     return MFMC_OK;
 }
 
-template <int R, int RX>
+template <int R>
 int rows_blocks_per_sm(int threads, size_t smem) {
-    auto kern = step_rows_kernel<R, RX>;
+    auto kern = step_rows_kernel<R>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem);
@@ -269,15 +372,14 @@ int rows_blocks_per_sm(int threads, size_t smem) {
 template <int R>
 RowsLauncher make_rows_launcher() {
     RowsLauncher L;
-    L.ch = RowsCfg<R, 4>::CH;
-    L.fn[0] = &launch_rows<R, 4>;
-    L.fn[1] = &launch_rows<R, 2>;
-    L.blocks_per_sm[0] = &rows_blocks_per_sm<R, 4>;
-    L.blocks_per_sm[1] = &rows_blocks_per_sm<R, 2>;
+    L.ch = RowsCfg<R>::CH;
+    L.nstg = RowsCfg<R>::NSTG;
+    L.fn = &launch_rows<R>;
+    L.blocks_per_sm = &rows_blocks_per_sm<R>;
     return L;
 }
 
-// Defined in the per-R translation units (R <= 12).
+// Defined in the per-R translation units (R <= 8).
 const RowsLauncher *rows_launcher(int R);
 
 }  // namespace mfmc

@@ -38,6 +38,23 @@ struct DiscRows {
     }
 };
 
+// Classes of disc rows by half-width.  The half-widths do not increase with |dy|, so rows
+// of equal half-width are consecutive; a class's row segment sum is the same for every
+// output row that a staged row serves through that class.
+template <int R>
+struct DiscClasses {
+    int count;       // number of distinct half-widths
+    int width[R + 1];  // half-width of class c (decreasing in c)
+    int of[R + 1];     // class of |dy|
+    constexpr DiscClasses() : count(0), width(), of() {
+        const DiscRows<R> d{};
+        for (int a = 0; a <= R; ++a) {
+            if (a == 0 || d.w[a] != d.w[a - 1]) width[count++] = d.w[a];
+            of[a] = count - 1;
+        }
+    }
+};
+
 struct TileArgs {
     const float *src;
     float *dst;

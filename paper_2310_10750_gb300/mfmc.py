@@ -188,7 +188,7 @@ class Model:
     def set_tile_variant(self, variant: int):
         _check(_L.mfmc_model_set_tile_variant(self.handle, variant))
 
-    def set_band_height(self, rows: int, columns_per_thread: int = 2):
+    def set_band_height(self, rows: int, columns_per_thread: int = 4):
         _check(_L.mfmc_model_set_band_height(self.handle, rows, columns_per_thread))
 
     def info(self) -> mfmc_model_info:

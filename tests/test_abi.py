@@ -97,18 +97,20 @@ def test_host_setters_and_version(lib):
     _, mfmc = lib
     assert mfmc.mfmc_version()
     m = mfmc.Model(n=256, delta=8 / 256, eps=0.02)
-    for v in range(8):
+    for v in range(11):
         m.set_tile_variant(v)
         assert m.info().tile_variant == v
-    for v in (-1, 8):
+    for v in (-1, 11):
         with pytest.raises(mfmc.MfmcError) as e:
             m.set_tile_variant(v)
         assert e.value.status == mfmc.MFMC_EINVAL
-    assert m.info().tile_variant == 7            # a rejected call changes nothing
+    assert m.info().tile_variant == 10           # a rejected call changes nothing
     m.set_band_height(64, 4)
     assert (m.info().band_height, m.info().columns_per_thread) == (64, 4)
-    for rows, cols in ((7, 2), (16385, 2), (64, 3)):
+    for rows, cols in ((7, 4), (16385, 4), (64, 2), (64, 3), (-1, 4)):
         with pytest.raises(mfmc.MfmcError) as e:
             m.set_band_height(rows, cols)
         assert e.value.status == mfmc.MFMC_EINVAL
     assert (m.info().band_height, m.info().columns_per_thread) == (64, 4)
+    m.set_band_height(0, 4)                      # 0: the batch's rows split evenly over the warps
+    assert m.info().band_height == 0

@@ -21,18 +21,21 @@ import oracle as O
 
 pytestmark = pytest.mark.gpu
 
-ALGOS = ["prefix", "direct", "kahan", "resident", "plain", "tma", "tma1", "tma2", "tma3", "tma4"]
+TMA_VARIANTS = ["tma", "tma1", "tma2", "tma3", "tma4", "tma8", "tma9", "tma10"]
+ALGOS = ["prefix", "direct", "kahan", "resident", "plain"] + TMA_VARIANTS
 
 
 def algo_id(mf, name):
     return {"prefix": mf.ALGO_PREFIX, "direct": mf.ALGO_DIRECT, "kahan": mf.ALGO_PREFIX_KAHAN,
             "resident": mf.ALGO_RESIDENT, "plain": mf.ALGO_PLAIN, "auto": mf.ALGO_AUTO,
-            "tma": mf.ALGO_PREFIX_TMA, "tma1": mf.ALGO_PREFIX_TMA, "tma2": mf.ALGO_PREFIX_TMA,
-            "tma3": mf.ALGO_PREFIX_TMA, "tma4": mf.ALGO_PREFIX_TMA, "rows": mf.ALGO_ROWS}[name]
+            "rows": mf.ALGO_ROWS}.get(name, mf.ALGO_PREFIX_TMA if name.startswith("tma") else None)
 
 
 def variant_of(name):
-    return {"tma": 0, "tma1": 1, "tma2": 2, "tma3": 3, "tma4": 4}.get(name)
+    """Tile-shape variant of the TMA kernel named "tma" (variant 0) or "tmaN" (variant N)."""
+    if not name.startswith("tma"):
+        return None
+    return int(name[3:] or 0)
 
 
 def pair(mf, n, R, steps, ic=0, eps=0.03, eps_lo=0.0, eps_hi=0.0, kernel=0, delta_hf=0.0, tau=1e-3,
@@ -150,7 +153,7 @@ def test_nuclei_obstacle_active_and_bounds_exact(gpu_lib, algo):
 
 def test_ragged_tiles_and_many_tiles(gpu_lib):
     mf = gpu_lib
-    for (n, R), algo in itertools.product(((68, 3), (132, 5), (200, 8)), ("prefix", "tma", "tma1", "tma2", "tma3", "tma4")):
+    for (n, R), algo in itertools.product(((68, 3), (132, 5), (200, 8)), ["prefix"] + TMA_VARIANTS):
         g, o = pair(mf, n, R, 20, ic=2, tau=5e-3, algo=algo)
         seeds = seeds_of(2, base=n)
         _, uT, f, _ = gpu_solve(mf, g, seeds)
@@ -175,7 +178,7 @@ def test_gaussian_kernel_generic_path(gpu_lib):
 def test_stationary_states_exact(gpu_lib):
     import torch
     mf = gpu_lib
-    for algo in ("prefix", "resident", "direct", "kahan", "tma", "tma1", "tma2", "tma3", "tma4"):
+    for algo in ["prefix", "resident", "direct", "kahan"] + TMA_VARIANTS:
         g = mf.Model(n=64, delta=4 / 64, nsteps=50, algo=algo_id(mf, algo))
         if variant_of(algo) is not None:
             g.set_tile_variant(variant_of(algo))
@@ -267,31 +270,56 @@ def test_hierarchy_levels_sampled(gpu_lib, n, R):
         assert abs(f[i] - fr) <= 1e-5 * fr
 
 
-@pytest.mark.parametrize("rx", [2, 4])
-@pytest.mark.parametrize("n,R,bh", [(128, 2, 64), (128, 4, 128), (256, 8, 64), (256, 8, 128), (256, 8, 256),
-                                    (384, 6, 256), (512, 8, 128), (192, 4, 64)])
-def test_row_streaming_kernel(gpu_lib, n, R, bh, rx):
-    # one step element by element, then a 40-step solve, including a band height that
-    # does not divide n (384 with 256-row bands) and the nuclei IC (obstacle active)
+@pytest.mark.parametrize("n,R,bh", [(128, 2, 64), (128, 4, 0), (256, 8, 0), (256, 8, 64), (256, 8, 40),
+                                    (384, 6, 0), (512, 8, 128), (384, 4, 24), (256, 6, 0)])
+def test_row_streaming_kernel(gpu_lib, n, R, bh):
+    # the warp-strip kernel: one step element by element, then a 40-step solve; bands that
+    # split the (sample, strip) columns unevenly (40, 24 rows), the even split over the
+    # resident warps (0), several strips per row (n = 384, 512) and the nuclei IC (obstacle
+    # active)
     mf = gpu_lib
     o = O.OracleModel(n=n, delta=R / n, eps=0.03, tau=5e-3, nsteps=1, ic=2)
-    if n % (32 * rx):
-        pytest.skip("n / columns is not a whole number of warps")
     g = mf.Model(n=n, delta=R / n, eps=0.03, tau=5e-3, nsteps=1, ic=2, algo=mf.ALGO_ROWS)
-    g.set_band_height(bh, rx)
+    g.set_band_height(bh, 4)
     seeds = seeds_of(3, base=n + bh)
     u0, uT, _, _ = gpu_solve(mf, g, seeds)
     for i in range(len(seeds)):
         ref = o.step(u0[i], 0.03)
         assert np.abs(uT[i] - ref).max() <= 4e-6
     g2, o2 = pair(mf, n, R, 40, ic=2, tau=5e-3, algo="rows")
-    g2.set_band_height(bh, rx)
+    g2.set_band_height(bh, 4)
     _, uT2, f2, _ = gpu_solve(mf, g2, seeds)
     for i, s in enumerate(seeds):
         fr, _, ur, _ = o2.solve_sample(int(s))
         assert abs(f2[i] - fr) <= 1e-5 * fr
         assert np.abs(uT2[i] - ur).max() <= 40 * 4e-6 * 1.3
     assert np.abs(uT2).max() <= 1.0
+
+
+def test_row_streaming_many_samples_and_stationary(gpu_lib):
+    # many samples: each warp's range crosses strip and sample boundaries; pure phases stay
+    # exactly stationary; the result does not depend on the work split (row partials)
+    import torch
+    mf = gpu_lib
+    g, o = pair(mf, 256, 8, 6, ic=1, algo="rows")
+    seeds = seeds_of(37, base=3)
+    _, uT, f, ubar = gpu_solve(mf, g, seeds)
+    for i in (0, 17, 36):
+        fr, mean, ur, _ = o.solve_sample(int(seeds[i]))
+        assert np.abs(uT[i] - ur).max() <= 6 * 4e-6 * 0.1
+        assert abs(ubar[i] - mean) <= 6 * 4e-6 * 0.1
+    g.set_band_height(24, 4)
+    _, uT_b, f_b, _ = gpu_solve(mf, g, seeds)
+    assert np.array_equal(uT_b, uT) and np.array_equal(f_b, f)
+    g3 = mf.Model(n=256, delta=8 / 256, nsteps=20, algo=mf.ALGO_ROWS)
+    for c in (1.0, -1.0, 0.0):
+        u0 = torch.full((3, 256, 256), c, dtype=torch.float32, device="cuda")
+        uT3 = torch.empty_like(u0)
+        ooi = torch.empty(3, dtype=torch.float64, device="cuda")
+        mf.mfmc_solve_fields(g3, u0, 3, uT=uT3, ooi=ooi)
+        torch.cuda.synchronize()
+        assert torch.all(uT3 == c)
+        assert np.all(ooi.cpu().numpy() == 0.5 * (1 + c))
 
 
 def test_graph_replay_matches_direct_launches(gpu_lib):
