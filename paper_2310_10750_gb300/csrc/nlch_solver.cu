@@ -745,6 +745,7 @@ mfmc_status run_solve_rows_core(const Model &m, int bh, int rx, const StepCoef *
         a.rows = rows;
         a.band = bh;
         a.stage_floats = g.stage_floats;
+        a.ng = 1;  // one lockstep group per CTA (measured faster than two or four)
         mfmc_status s = L->fn(*src, a, grid, threads, g.smem, st);
         if (s != MFMC_OK) return s;
         src = (dstbuf == b.padA) ? &b.mapA : &b.mapB;

@@ -38,8 +38,9 @@ struct RowsArgs {
     int gs;                // samples per CTA
     int strips;            // n / 128: warps per sample
     long long rows;        // groups * n: the batch's rows in (group, row) order
-    int band;              // rows per work range; 0: rows / CTAs, one range per CTA
+    int band;              // rows per work range; 0: rows / groups, one range per group
     int stage_floats;      // gs * CH * P
+    int ng;                // independent warp groups per CTA (each gs samples)
 };
 
 template <int R>
@@ -53,7 +54,24 @@ struct RowsCfg {
     // are multiples of CH would make chunk boundaries static but spill registers)
     static constexpr int S = 2 * R + 1;
     static constexpr int MAXW = 16;                      // warps per CTA at most
+    static constexpr int MAXG = 4;                       // warp groups per CTA at most
 };
+
+// Barriers of one warp group (named barrier id, nthreads threads; id 0 is the CTA's).
+__device__ __forceinline__ bool group_sync_and(int id, int nthreads, bool ok) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.and.pred p, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)ok), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void group_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
 
 __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1, int c2,
                                             int c3) {
@@ -85,9 +103,9 @@ struct RowsSegIter {
         }
         if (q > a.rows) q = qend = a.rows;
     }
-    __device__ void init(const RowsArgs &a) {
-        nct = gridDim.x;
-        range = blockIdx.x;
+    __device__ void init(const RowsArgs &a, long long id, long long count) {
+        nct = count;
+        range = id;
         set_range(a);
     }
     // The next segment with an active sample, in walk order; len = 0 at the end.
@@ -152,13 +170,43 @@ __device__ __noinline__ void rows_issue(const RowsArgs &a, RowsShared &sh, const
 // Per-segment state of a warp.
 struct RowsSeg {
     const float *win0;   // the lane's window start in its sample's first row of stage 0
+    int bid, bthreads;   // the warp group's named barrier and its threads
+    bool leader;         // the group's first thread: issues the copies and walks the segments
     int g0;              // stream index of the segment's first chunk
     int nrows;           // rows walked: len + 2R
-    int sample, y0, x;   // sample, lattice row of the first output row, the lane's first column
-    bool active;
-    TmaRowCtx ctx;
-    StepCoef cf;
+    int sample;
+    // outputs: the next output row's four values go to out (advanced by ostride per row), its
+    // ghost column image to out + gdelta, and for lattice rows yr < G or yr >= n - G also to
+    // the ghost row image (out +- n P); flags say which of these exist
+    float *out;
+    long long gdelta;
+    int ostride, yr;
+    unsigned flags;
+    float2 nc0, c1, c2;  // step coefficients (-c0, c1, c2) in both halves of a pair
 };
+
+enum : unsigned { kRowsActive = 1u, kRowsGhostCol = 2u, kRowsGhostRows = 4u };
+
+// The update and projection of one output row of a lane (four columns) from its disc sums
+// (s01, s23) and centre values uc, and its stores (Eq. nonl_CH_nm with beta2 = 0 and the
+// projection of Eq. potential_obstacle): sd = fma(-c0, u, S), v = u + fma(c1, sd, c2 u),
+// u_new = min(1, max(-1, v)), each packed FP32 pair rounding exactly like the scalar operations.
+template <int R>
+__device__ __forceinline__ void rows_emit(RowsSeg &sg, unsigned fl, float4 uc, float2 s01, float2 s23, int n, int P) {
+    constexpr int G = (R + 3) & ~3;
+    const float2 u01 = make_float2(uc.x, uc.y), u23 = make_float2(uc.z, uc.w);
+    const float2 v01 = __fadd2_rn(u01, __ffma2_rn(sg.c1, __ffma2_rn(sg.nc0, u01, s01), __fmul2_rn(sg.c2, u01)));
+    const float2 v23 = __fadd2_rn(u23, __ffma2_rn(sg.c1, __ffma2_rn(sg.nc0, u23, s23), __fmul2_rn(sg.c2, u23)));
+    const float4 val = make_float4(fminf(1.f, fmaxf(-1.f, v01.x)), fminf(1.f, fmaxf(-1.f, v01.y)),
+                                   fminf(1.f, fmaxf(-1.f, v23.x)), fminf(1.f, fmaxf(-1.f, v23.y)));
+    *reinterpret_cast<float4 *>(sg.out) = val;
+    if (fl & kRowsGhostCol) *reinterpret_cast<float4 *>(sg.out + sg.gdelta) = val;
+    if ((fl & kRowsGhostRows) && (unsigned)(sg.yr - G) >= (unsigned)(n - 2 * G)) {
+        const long long off = (long long)(sg.yr < G ? n : -n) * P;  // the row's periodic image
+        *reinterpret_cast<float4 *>(sg.out + off) = val;
+        if (fl & kRowsGhostCol) *reinterpret_cast<float4 *>(sg.out + off + sg.gdelta) = val;
+    }
+}
 
 template <int R>
 struct RowsAcc {
@@ -207,7 +255,7 @@ __device__ __forceinline__ void rows_classes(RowsAcc<R> &t, const RowWin<R> &win
 // Staged row q = q0 + K of the segment (q0 a multiple of S, K static: the ring position).
 // Returns false when a chunk wait ran out of its bound.
 template <int R, int K>
-__device__ __forceinline__ bool rows_row(RowsAcc<R> &t, const RowsArgs &a, const RowsSeg &sg, int q0, RowsShared &sh,
+__device__ __forceinline__ bool rows_row(RowsAcc<R> &t, const RowsArgs &a, RowsSeg &sg, int q0, RowsShared &sh,
                                          const CUtensorMap *map, float *ring, uint64_t *bar) {
     using C = RowsCfg<R>;
     const int q = q0 + K;
@@ -224,30 +272,33 @@ __device__ __forceinline__ bool rows_row(RowsAcc<R> &t, const RowsArgs &a, const
                 ok = false;
                 break;
             }
-        // every thread is past the rows of the stage that the next copy overwrites
-        if (!__syncthreads_and(ok)) return false;
-        if (threadIdx.x == 0) rows_issue<R>(a, sh, map, ring, bar);
+        // every thread of the group is past the rows of the stage that the next copy overwrites
+        if (!group_sync_and(sg.bid, sg.bthreads, ok)) return false;
+        if (sg.leader) rows_issue<R>(a, sh, map, ring, bar);
     }
     // the centre row q - R enters a new chunk: the stage after the previous centre chunk's
-    if (q >= R && (q - R) % C::CH == 0) {
+    if ((R % C::CH == 0 ? q % C::CH == 0 : (q - R) % C::CH == 0) && q >= R) {
         t.cst = t.cst + 1 == C::NSTG ? 0 : t.cst + 1;
         t.cp = sg.win0 + t.cst * a.stage_floats + C::R4;
     }
     RowWin<R> win;
     row_window<R>(t.rp, win);
     rows_classes<R, K>(t, win, std::make_integer_sequence<int, RowsPlan<R>::cls.count>{});
-    if (q >= 2 * R && (opaque_u32(sg.active) != 0)) {  // output row q - 2R is complete
-        constexpr int slot = rows_mod(K - 2 * R, C::S);
-        const float4 uc = *reinterpret_cast<const float4 *>(t.cp);  // its centre row, q - R
-        double unused = 0.0;
-        tma_emit_row<R, false, false, true>(a.t, sg.ctx, sg.cf, uc, t.acc[slot][0], t.acc[slot][1],
-                                            sg.y0 + q - 2 * R, sg.x, false, unused);
+    if (q >= 2 * R) {  // output row q - 2R is complete
+        const unsigned fl = opaque_u32(sg.flags);
+        if (fl & kRowsActive) {
+            constexpr int slot = rows_mod(K - 2 * R, C::S);
+            const float4 uc = *reinterpret_cast<const float4 *>(t.cp);  // its centre row, q - R
+            rows_emit<R>(sg, fl, uc, t.acc[slot][0], t.acc[slot][1], a.t.n, a.t.P);
+        }
+        sg.out += sg.ostride;
+        ++sg.yr;
     }
     return true;
 }
 
 template <int R, int... Ks>
-__device__ __forceinline__ bool rows_block(RowsAcc<R> &t, const RowsArgs &a, const RowsSeg &sg, int q0,
+__device__ __forceinline__ bool rows_block(RowsAcc<R> &t, const RowsArgs &a, RowsSeg &sg, int q0,
                                            RowsShared &sh, const CUtensorMap *map, float *ring, uint64_t *bar,
                                            int *gfail, std::integer_sequence<int, Ks...>) {
     using C = RowsCfg<R>;
@@ -268,15 +319,21 @@ __global__ void __launch_bounds__(RowsCfg<R>::MAXW * 32, 1) step_rows_kernel(con
                                                                            RowsArgs a) {
     using C = RowsCfg<R>;
     extern __shared__ unsigned char smem_raw[];
-    float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    __shared__ __align__(8) uint64_t bar[C::NSTG];
-    __shared__ RowsShared sh;
+    __shared__ __align__(8) uint64_t bars[C::MAXG][C::NSTG];
+    __shared__ RowsShared shs[C::MAXG];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int sl = warp / a.strips, strip = warp - sl * a.strips;  // sample in the group, strip
-    if (threadIdx.x == 0) {
+    // warp groups: a.gs samples x a.strips strips each, independent rings and barriers
+    const int gw = a.gs * a.strips, gid = warp / gw, wig = warp - gid * gw;
+    const int sl = wig / a.strips, strip = wig - sl * a.strips;  // sample in the group, strip
+    float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127)) +
+                  (size_t)gid * C::NSTG * a.stage_floats;
+    uint64_t *bar = bars[gid];
+    RowsShared &sh = shs[gid];
+    const bool leader = (threadIdx.x - 32 * gw * gid) == 0;
+    if (leader) {
         for (int i = 0; i < C::NSTG; ++i) mbar_init(&bar[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        sh.it.init(a);
+        sh.it.init(a, (long long)blockIdx.x * a.ng + gid, (long long)gridDim.x * a.ng);
         sh.seg[0] = sh.it.next(a);
         sh.seg[1] = sh.it.next(a);
         sh.pslot = 1;  // the first issue advances to slot 0
@@ -291,6 +348,9 @@ __global__ void __launch_bounds__(RowsCfg<R>::MAXW * 32, 1) step_rows_kernel(con
 
     RowsSeg sg;
     sg.win0 = ring + sl * C::CH * a.t.P + 128 * strip + 4 * lane;
+    sg.bid = 1 + gid;
+    sg.bthreads = 32 * gw;
+    sg.leader = leader;
     sg.g0 = 0;
     int gfail = 0;
     bool ok = true;
@@ -303,20 +363,43 @@ __global__ void __launch_bounds__(RowsCfg<R>::MAXW * 32, 1) step_rows_kernel(con
         t.cst = (sg.g0 + C::NSTG - 1) % C::NSTG;
         t.rp = t.cp = sg.win0;
         sg.sample = a.gs * s.group + sl;
-        sg.y0 = s.y0;
-        sg.x = 128 * strip + 4 * lane;
-        sg.active = sg.sample < a.ns && (a.t.steps_ps == nullptr || a.t.step <= a.t.steps_ps[sg.sample]);
-        const int smp = sg.active ? sg.sample : 0;
-        sg.cf = a.t.coef[smp];
-        sg.ctx = tma_row_ctx<R>(a.t, smp, 128 * strip + 4 * lane, s.y0, s.len);
+        {
+            const int n = a.t.n, P = a.t.P, x = 128 * strip + 4 * lane;
+            const bool active =
+                sg.sample < a.ns && (a.t.steps_ps == nullptr || a.t.step <= a.t.steps_ps[sg.sample]);
+            const int smp = active ? sg.sample : 0;
+            const StepCoef cf = a.t.coef[smp];
+            sg.nc0 = make_float2(-cf.c0, -cf.c0);
+            sg.c1 = make_float2(cf.c1, cf.c1);
+            sg.c2 = make_float2(cf.c2, cf.c2);
+            sg.yr = s.y0;
+            sg.flags = active ? kRowsActive : 0u;
+            sg.gdelta = 0;
+            if (a.t.dst_plain) {  // the caller's unpadded field (last step): no ghost images
+                sg.out = a.t.dst_plain + (size_t)smp * n * n + (size_t)s.y0 * n + x;
+                sg.ostride = n;
+            } else {
+                sg.out = a.t.dst + (size_t)smp * P * P + (size_t)(C::R4 + s.y0) * P + C::R4 + x;
+                sg.ostride = P;
+                if (a.t.periodic) {
+                    // the lane's columns have a periodic image in the frame, n columns to the right
+                    // when x < G and n columns to the left when x >= n - G
+                    if (x < C::R4 || x >= n - C::R4) {
+                        sg.flags |= kRowsGhostCol;
+                        sg.gdelta = x < C::R4 ? n : -n;
+                    }
+                    sg.flags |= kRowsGhostRows;
+                }
+            }
+        }
         for (int q0 = 0; ok && q0 < sg.nrows; q0 += C::S)
             ok = rows_block<R>(t, a, sg, q0, sh, &map, ring, bar, &gfail, std::make_integer_sequence<int, C::S>{});
         sg.g0 += (sg.nrows + C::CH - 1) / C::CH;
-        __syncthreads();  // every thread has read slot k & 1
-        if (ok && threadIdx.x == 0) sh.seg[k & 1] = sh.it.next(a);
-        __syncthreads();
+        group_sync(sg.bid, sg.bthreads);  // every thread of the group has read slot k & 1
+        if (ok && leader) sh.seg[k & 1] = sh.it.next(a);
+        group_sync(sg.bid, sg.bthreads);
     }
-    if (!ok && threadIdx.x == 0) {
+    if (!ok && leader) {
         // A chunk wait ran out of its bound (only a copy that never lands can cause it): report,
         // then wait, again bounded, for each copy issued and not consumed, so that none still
         // targets the ring when the CTA exits unless that wait runs out as well.

@@ -296,6 +296,34 @@ def test_row_streaming_kernel(gpu_lib, n, R, bh):
     assert np.abs(uT2).max() <= 1.0
 
 
+@pytest.mark.parametrize("n,R", [(256, 8), (128, 4), (384, 6)])
+def test_row_streaming_noise_ic_multistep(gpu_lib, n, R):
+    # smoothed-noise fields are nonzero at every edge, so every ghost image (rows and columns,
+    # both sides) is exercised: 6 steps element by element against the oracle
+    mf = gpu_lib
+    g, o = pair(mf, n, R, 6, ic=1, eps=0.02, algo="rows")
+    seeds = seeds_of(5, base=7 * n)
+    _, uT, f, _ = gpu_solve(mf, g, seeds)
+    for i, s in enumerate(seeds):
+        fr, mean, ur, _ = o.solve_sample(int(s))
+        assert np.abs(uT[i] - ur).max() <= 6 * 4e-6 * 0.1
+        assert abs(f[i] - fr) <= 1e-7
+
+
+def test_row_streaming_matches_tile_kernel_bitwise(gpu_lib):
+    # the row-streaming and the TMA tile kernels form the same class segment sums in the same
+    # row order and the same epilogue, so their fields agree bit for bit (256^2, R = 8, 37
+    # samples: ranges cross sample groups; 5 steps of the smoothed-noise IC)
+    mf = gpu_lib
+    seeds = seeds_of(37, base=11)
+    out = {}
+    for algo in ("rows", "tma4"):
+        g, _ = pair(mf, 256, 8, 5, ic=1, eps=0.02, algo=algo)
+        out[algo] = gpu_solve(mf, g, seeds)
+    assert np.array_equal(out["rows"][1], out["tma4"][1])
+    assert np.array_equal(out["rows"][2], out["tma4"][2])
+
+
 def test_row_streaming_many_samples_and_stationary(gpu_lib):
     # many samples: each warp's range crosses strip and sample boundaries; pure phases stay
     # exactly stationary; the result does not depend on the work split (row partials)
