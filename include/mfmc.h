@@ -48,8 +48,6 @@ typedef enum {
  *             with the same second moment and the paper's c_gamma ~ 36 eps^2/delta^2. */
 typedef enum { MFMC_KERNEL_CONSTANT = 0, MFMC_KERNEL_GAUSSIAN = 1 } mfmc_kernel;
 
-/* Boundary: the periodic unit torus (the interaction collar of Section 2 is not
- * modelled). */
 /* Boundary of the lattice Omega.  PERIODIC: the unit torus.  COLLAR: the volume-constrained
  * form of Section 2 -- the operator of Eq. (nonl_operator) integrates over Omega together
  * with the interaction collar Omega_I of width delta around it, and the collar holds the
@@ -193,6 +191,14 @@ mfmc_status mfmc_model_query(const mfmc_model *model, mfmc_model_info *out);
  * NULL. */
 mfmc_status mfmc_model_solver_stats(const mfmc_model *model, uint64_t *newton_iters, uint64_t *cg_iters);
 
+/* Iteration bounds of the beta2 > 0 solver (MFMC_ALGO_ACTIVE_SET; the paper states no solver for
+ * its obstacle step, so the bounds are this library's): newton_max = semismooth Newton passes
+ * per time step (default 60), cg_max = FP32 CG iterations per Newton correction (default 500);
+ * 0 restores a default.  A step that reaches the Newton bound stops the sample's solve and sets
+ * the model's status flag, so mfmc_solve_batch returns MFMC_ETIMEOUT; the device stays usable
+ * and the next call starts with the flag cleared.  MFMC_EINVAL for values outside [0, 100000]. */
+mfmc_status mfmc_model_set_iteration_limits(mfmc_model *model, int newton_max, int cg_max);
+
 /* Pin the tile shape (0..10) of the TMA kernel instead of letting the autotuner choose
  * (for measurements and tests).  MFMC_EINVAL for an unknown variant. */
 mfmc_status mfmc_model_set_tile_variant(mfmc_model *model, int variant);
@@ -249,9 +255,11 @@ mfmc_status mfmc_solve_fields_algo(const mfmc_model *model, int algo, const doub
  * 256 x 256, 1006 fields of 64 x 64), ns * tiles <= 65536; larger batches return
  * MFMC_EINVAL with the limits in the message.  Constant kernel and R in
  * {1,2,3,4,5,6,8,11,12,16,22,24,32} only.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress), so make it before any stream capture.
- * All calls share the one array and it keeps the last call's contents; calls whose work
- * overlaps on the GPU (other streams, other threads) race on it. */
+ * array's device address (cudaGetSymbolAddress) and keeps it for the life of the process,
+ * so make it before any stream capture, and do not use this call after cudaDeviceReset on
+ * that device (the kept address would then be stale).  All calls share the one array and
+ * it keeps the last call's contents; calls whose work overlaps on the GPU (other streams,
+ * other threads) race on it. */
 mfmc_status mfmc_solve_fields_noalloc(const mfmc_model *model, const double *eps, const float *u0,
                                       size_t ns, float *uT, double *ubar, double *ooi,
                                       void *stream);

@@ -38,8 +38,6 @@
 namespace mfmc {
 
 constexpr int AS_NT = 512;
-constexpr int AS_MAX_NEWTON = 60;
-constexpr int AS_MAX_CG = 500;        // FP32 CG iterations per Newton correction
 constexpr float AS_CG_RTOL = 1e-5f;   // max |J d + F| / max |F| that ends a correction
 constexpr int AS_VEC64 = 3;           // u, g, w
 constexpr int AS_VEC32 = 7;           // d, r, p, q, inactive mask, z, t
@@ -102,6 +100,7 @@ struct ActiveSetArgs {
     const double *wtab;  // Gaussian: FP64 weight / eps^2 by r^2; nullptr: constant kernel
     int widths[kMaxR + 1];
     int n, R, nsteps;
+    int newton_max, cg_max;  // iteration bounds: Newton passes per step, CG iterations per correction
     int load;     // read u0 into the FP64 field first
     int g_given;  // the disc sums of u are in g already (spectral form): no direct sum
     int finish;   // write uT, ubar and the OoI after the last step
@@ -376,7 +375,7 @@ __global__ void __launch_bounds__(AS_NT) active_set_kernel(ActiveSetArgs a) {
             fmax = as_block_max(fmax, red64);
             changed = as_block_max(changed, red64);
             if (it > 1 && changed == 0.0 && fmax <= 1e-11) break;
-            if (it > AS_MAX_NEWTON) {
+            if (it > a.newton_max) {
                 failed = true;
                 break;
             }
@@ -422,7 +421,7 @@ __global__ void __launch_bounds__(AS_NT) active_set_kernel(ActiveSetArgs a) {
                            rmax = rmax > fabsf(v.y) ? rmax : fabsf(v.y);
                        });
                 rmax = as_block_max(rmax, red32);
-                if (rmax <= AS_CG_RTOL || !(pq > 0.0f) || !(rz > 0.0f) || k >= AS_MAX_CG) {
+                if (rmax <= AS_CG_RTOL || !(pq > 0.0f) || !(rz > 0.0f) || k >= a.cg_max) {
                     n_cg += k;
                     break;
                 }
@@ -492,6 +491,8 @@ mfmc_status run_solve_active_set(Model &m, const double *eps_dev, const float *u
     for (int d = 0; d <= kMaxR; ++d) a.widths[d] = d <= m.R ? m.widths[d] : 0;
     a.n = m.d.n;
     a.R = m.R;
+    a.newton_max = m.as_newton_max;
+    a.cg_max = m.as_cg_max;
     a.ahat = m.ahat;
     a.chat = m.chat64;
     a.tau = m.d.tau;

@@ -223,6 +223,16 @@ mfmc_status mfmc_model_create(const mfmc_model_desc *desc, mfmc_model **out) {
 
 void mfmc_model_destroy(mfmc_model *model) { delete model; }
 
+mfmc_status mfmc_model_set_iteration_limits(mfmc_model *m, int newton_max, int cg_max) {
+    if (!m) return fail(MFMC_EINVAL, "NULL model");
+    if (newton_max < 0 || newton_max > 100000 || cg_max < 0 || cg_max > 100000)
+        return fail(MFMC_EINVAL, "iteration limits outside [0, 100000]");
+    std::lock_guard<std::mutex> lk(m->mu);
+    m->as_newton_max = newton_max > 0 ? newton_max : kAsNewtonMax;
+    m->as_cg_max = cg_max > 0 ? cg_max : kAsCgMax;
+    return MFMC_OK;
+}
+
 mfmc_status mfmc_model_solver_stats(const mfmc_model *m, uint64_t *newton_iters, uint64_t *cg_iters) {
     if (!m) return fail(MFMC_EINVAL, "NULL model");
     unsigned long long it[2] = {0, 0};
@@ -418,6 +428,8 @@ mfmc_status mfmc_solve_batch(mfmc_model *const *models, const mfmc_sample_params
             std::lock_guard<std::mutex> lk(m->mu);
             if (!m->stream) MFMC_CUDA(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking));
             MFMC_CUDA(cudaStreamSynchronize(m->stream));
+            // a flag left by an earlier solve whose results nobody waited for is not this call's
+            if (m->d_status) MFMC_CUDA(cudaMemset(m->d_status, 0, sizeof(int)));
             mfmc_status s = grow_buffer(&m->u0buf, &m->u0_cap, k * nn);
             if (s == MFMC_OK) s = grow_buffer(&m->eps_tmp, &m->eps_cap, k);
             if (s == MFMC_OK) s = grow_buffer(&m->resbuf, &m->res_cap, 2 * k);
@@ -451,7 +463,11 @@ mfmc_status mfmc_solve_batch(mfmc_model *const *models, const mfmc_sample_params
         if (m->d_status) {
             int flag = 0;
             MFMC_CUDA(cudaMemcpy(&flag, m->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-            if (flag) return fail(MFMC_ETIMEOUT, "a device-side wait gave up");
+            if (flag) {
+                // reported once: the next call starts with the flag cleared
+                MFMC_CUDA(cudaMemset(m->d_status, 0, sizeof(int)));
+                return fail(MFMC_ETIMEOUT, "a device-side wait or an iteration bound gave up");
+            }
         }
         const std::vector<size_t> &idx = groups[order[g]];
         const size_t k = idx.size();

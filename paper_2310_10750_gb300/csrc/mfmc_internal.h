@@ -15,6 +15,10 @@ namespace mfmc {
 
 constexpr int kMaxR = 32;
 constexpr int kMaxNs = 1 << 24;
+// default iteration bounds of the beta2 > 0 solver: Newton passes per step, FP32 CG iterations
+// per Newton correction (mfmc_model_set_iteration_limits changes them per model)
+constexpr int kAsNewtonMax = 60;
+constexpr int kAsCgMax = 500;
 
 // Step coefficients of one sample.  With S = sum_z what_z u_{i+z} (what_z = 1 for the
 // constant kernel, the Gaussian weight / eps^2 otherwise) the update is
@@ -92,6 +96,8 @@ struct Model {
     FftState *fft = nullptr;  // created by the first FFT-path solve
     Fft64State *fft64 = nullptr;  // created by the first spectral beta2 > 0 solve
     unsigned long long *d_as_iters = nullptr;  // Newton and CG iterations of the last beta2 > 0 solve
+    int as_newton_max = kAsNewtonMax;           // iteration bounds of the beta2 > 0 solver
+    int as_cg_max = kAsCgMax;
     ~Model();
 };
 

@@ -67,7 +67,16 @@ __device__ __forceinline__ bool mixed_item(const CUtensorMap &map, const TmaArgs
             ok = false;
             break;
         }
-    if (!__syncthreads_and(ok)) return false;
+    if (!__syncthreads_and(ok)) {
+        // the copy did not land within the bound: wait for it once more (bounded) so that it
+        // does not target the stage after the CTA has gone
+        if (threadIdx.x == 0) {
+            long long w = 0;
+            while (!mbar_try_wait(bar, parity) && ++w < kWaitLimit) {
+            }
+        }
+        return false;
+    }
     const bool last = a.last || (a.steps_ps != nullptr && a.step == a.steps_ps[sample]);
     tma_tile_compute<R, S::RY, S::TXT, S::TYT, 1>(stage, a, sample, tile, x0, y0, last, red);
     __syncthreads();  // the stage is free again
@@ -333,12 +342,8 @@ extern "C" mfmc_status mfmc_solve_batch_mixed(mfmc_model *const *models, const m
         if (!(W.gexec && W.gkey == key)) {
             if (W.gexec) cudaGraphExecDestroy(W.gexec);
             W.gexec = nullptr;
-            static bool attr = false;
-            if (!attr) {
-                MFMC_CUDA(cudaFuncSetAttribute(mixed_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)kMixSmem));
-                attr = true;
-            }
+            MFMC_CUDA(cudaFuncSetAttribute(mixed_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kMixSmem));
             int dev = 0, sms = 0, per = 0;
             MFMC_CUDA(cudaGetDevice(&dev));
             MFMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

@@ -369,12 +369,8 @@ static int tiles_for(const Model &m, int algo, int *tiles_x) {
 static mfmc_status launch_generic(const Model &m, const GenericArgs &base, size_t s0, size_t cnt,
                                   cudaStream_t st) {
     const size_t smem = generic_smem(m.R);
-    static bool attr_done = false;
-    if (!attr_done) {
-        MFMC_CUDA(cudaFuncSetAttribute(step_generic_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       96 * 1024));
-        attr_done = true;
-    }
+    // set before every launch: the attribute is per device, and the call is cheap
+    MFMC_CUDA(cudaFuncSetAttribute(step_generic_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
     for (size_t o = 0; o < cnt; o += 65535) {
         GenericArgs a = base;
         a.sample0 = (int)(s0 + o);

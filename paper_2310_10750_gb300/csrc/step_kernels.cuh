@@ -373,11 +373,8 @@ mfmc_status launch_tile(const TileArgs &base, size_t ns, cudaStream_t st) {
     using C = TileCfg<R>;
     auto kern = step_tile_kernel<R, C::RY, C::TXT, C::TYT, ALGO>;
     constexpr size_t smem = tile_smem_bytes<R, C::RY, C::TXT, C::TYT>();
-    static bool attr_done = false;
-    if (!attr_done) {
-        MFMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_done = true;
-    }
+    // set before every launch: the attribute is per device, and the call is cheap
+    MFMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (size_t s0 = 0; s0 < ns; s0 += 65535) {
         TileArgs a = base;
         a.sample0 = (int)s0;
@@ -421,11 +418,7 @@ template <int R>
 mfmc_status launch_resident(const ResidentArgs &a, cudaStream_t st) {
     auto kern = resident_kernel<R, RES_RY>;
     const size_t smem = resident_smem(a.n, R);
-    static size_t attr_max = 0;
-    if (smem > attr_max) {
-        MFMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_max = smem;
-    }
+    MFMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int nt = resident_threads(a.n);
     int per_sm = 0;
     MFMC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem));

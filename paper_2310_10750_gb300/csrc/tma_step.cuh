@@ -573,14 +573,21 @@ __device__ __forceinline__ void tma_step_body(const CUtensorMap &src_map, const 
     };
 
     int k = 0;
+    int issued = 0;  // copies issued by thread 0 (item k's copy is copy number k)
     const int stride = gridDim.x;
     const int first = next_active(a, blockIdx.x, stride);
-    if (tid == 0 && first < a.total) issue(first, 0);
+    if (tid == 0 && first < a.total) {
+        issue(first, 0);
+        issued = 1;
+    }
     for (int item = first, nxt; item < a.total; item = nxt, ++k) {
         nxt = next_active(a, item + stride, stride);
         const int stage = STAGES == 2 ? (k & 1) : 0;
         const uint32_t parity = STAGES == 2 ? (uint32_t)((k >> 1) & 1) : (uint32_t)(k & 1);
-        if (STAGES == 2 && tid == 0 && nxt < a.total) issue(nxt, stage ^ 1);
+        if (STAGES == 2 && tid == 0 && nxt < a.total) {
+            issue(nxt, stage ^ 1);
+            ++issued;
+        }
         // bounded wait for this stage's copy
         long long spins = 0;
         while (!mbar_try_wait(&bars[stage], parity)) {
@@ -591,7 +598,20 @@ __device__ __forceinline__ void tma_step_body(const CUtensorMap &src_map, const 
         }
         __syncthreads();
         if (abort_flag) {
-            if (tid == 0) atomicExch(a.status, 1);
+            // A copy did not land within the bound (only a copy that never completes can cause
+            // it).  Report, then wait, again bounded, for every copy issued and not consumed
+            // (items k .. issued - 1), so that none still targets this CTA's shared memory when
+            // it exits unless that wait runs out as well.
+            if (tid == 0) {
+                atomicExch(a.status, 1);
+                for (int j = k; j < issued; ++j) {
+                    const int sj = STAGES == 2 ? (j & 1) : 0;
+                    const uint32_t pj = STAGES == 2 ? (uint32_t)((j >> 1) & 1) : (uint32_t)(j & 1);
+                    long long w = 0;
+                    while (!mbar_try_wait(&bars[sj], pj) && ++w < kWaitLimit) {
+                    }
+                }
+            }
             break;
         }
         const float *s = base + stage * C::STAGE_FLOATS;
@@ -604,7 +624,10 @@ __device__ __forceinline__ void tma_step_body(const CUtensorMap &src_map, const 
         else
             tma_tile_compute<R, RY, TXT, TYT, ALGO>(s, a, sample, tile, x0, y0, last, red);
         __syncthreads();  // every thread is done with this stage before it is refilled
-        if (STAGES == 1 && tid == 0 && nxt < a.total) issue(nxt, 0);
+        if (STAGES == 1 && tid == 0 && nxt < a.total) {
+            issue(nxt, 0);
+            ++issued;
+        }
     }
 }
 
@@ -721,11 +744,8 @@ mfmc_status launch_tma(const CUtensorMap &map, const TmaArgs &a, int grid, cudaS
     using C = TmaCfg<R, T::RY, T::TXT, T::TYT, T::STAGES>;
     auto kern = tma_kernel_ptr<R, T::RY, T::TXT, T::TYT, ALGO, T::STAGES, T::MINB>();
     constexpr size_t smem = C::SMEM + (ALGO == 3 ? (size_t)(R + 1) * (R + 1) * sizeof(float) : 0);
-    static bool attr_done = false;
-    if (!attr_done) {
-        MFMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_done = true;
-    }
+    // set before every launch: the attribute is per device, and the call is cheap
+    MFMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<grid, T::TXT * T::TYT, smem, st>>>(map, a);
     MFMC_LAUNCHED("tma_step launch 1");
     return MFMC_OK;

@@ -97,6 +97,7 @@ _sig("mfmc_model_destroy", None, [_vp])
 _sig("mfmc_model_query", _st, [_vp, ctypes.POINTER(mfmc_model_info)])
 _sig("mfmc_model_set_tile_variant", _st, [_vp, ctypes.c_int])
 _sig("mfmc_model_solver_stats", _st, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)])
+_sig("mfmc_model_set_iteration_limits", _st, [_vp, ctypes.c_int, ctypes.c_int])
 _sig("mfmc_model_set_band_height", _st, [_vp, ctypes.c_int, ctypes.c_int])
 _sig("mfmc_sample_eps", _st, [_vp, _vp, _vp, ctypes.c_size_t, _vp])
 _sig("mfmc_init_fields", _st, [_vp, _vp, _vp, ctypes.c_size_t, _vp, _vp])
@@ -191,6 +192,9 @@ class Model:
     def set_band_height(self, rows: int, columns_per_thread: int = 4):
         _check(_L.mfmc_model_set_band_height(self.handle, rows, columns_per_thread))
 
+    def set_iteration_limits(self, newton_max: int = 0, cg_max: int = 0):
+        _check(_L.mfmc_model_set_iteration_limits(self.handle, newton_max, cg_max))
+
     def info(self) -> mfmc_model_info:
         out = mfmc_model_info()
         _check(_L.mfmc_model_query(self.handle, ctypes.byref(out)))
@@ -203,6 +207,10 @@ def mfmc_model_create(**kw) -> Model:
 
 def mfmc_model_set_tile_variant(model: Model, variant: int):
     model.set_tile_variant(variant)
+
+
+def mfmc_model_set_iteration_limits(model: Model, newton_max: int = 0, cg_max: int = 0):
+    model.set_iteration_limits(newton_max, cg_max)
 
 
 def mfmc_model_solver_stats(model: Model):

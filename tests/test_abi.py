@@ -60,6 +60,14 @@ def test_model_validation_on_host(lib):
     assert mfmc.mfmc_model_solver_stats(b2) == (0, 0)
     assert mfmc.mfmc_model_solver_stats(m) == (0, 0)
     assert mfmc._L.mfmc_model_solver_stats(None, None, None) == mfmc.MFMC_EINVAL
+    # iteration bounds of the beta2 > 0 solver: host-side validation
+    b2.set_iteration_limits(3, 7)
+    b2.set_iteration_limits()
+    for bad in ((-1, 0), (0, -1), (100001, 0)):
+        with pytest.raises(mfmc.MfmcError) as e:
+            b2.set_iteration_limits(*bad)
+        assert e.value.status == mfmc.MFMC_EINVAL
+    assert mfmc._L.mfmc_model_set_iteration_limits(None, 1, 1) == mfmc.MFMC_EINVAL
     # a non-integer delta/h: the disc is { |z| <= 4.5 } and only the generic kernel serves it
     g = mfmc.Model(n=64, delta=4.5 / 64, eps=0.03)
     assert g.info().R == 4

@@ -133,3 +133,33 @@ def test_active_set_direct_and_spectral_disc_sums(gpu_lib, case):
     u0, u1, _, _ = gpu_solve(mf, one, seeds[:1])
     ref, _, _ = B2.step(o, u0[0], 0.04219, 0.05)
     assert np.abs(u1[0] - ref).max() <= 1e-7
+
+
+def test_newton_bound_reports_timeout_and_the_model_recovers(gpu_lib):
+    # Failure detection in its safe form: an iteration bound set low by the host.  Every step
+    # of these nuclei fields needs several Newton passes, so a bound of one pass is reached; the
+    # kernel stops the sample and returns normally, the batch call reports MFMC_ETIMEOUT, and the
+    # next call on the same model (default bounds again) runs on a usable context and matches
+    # the oracle.
+    mf = gpu_lib
+    kw = dict(n=32, delta=3 / 32, eps=0.03, tau=0.01, nsteps=5, ic=2, beta2=0.05)
+    g = mf.Model(**kw)
+    seeds = np.arange(3, dtype=np.uint64) + 640
+    g.set_iteration_limits(newton_max=1)
+    with pytest.raises(mf.MfmcError) as e:
+        mf.mfmc_solve_batch([g] * 3, seeds)
+    assert e.value.status == mf.MFMC_ETIMEOUT
+    with pytest.raises(mf.MfmcError) as e:
+        g.set_iteration_limits(newton_max=-1)
+    assert e.value.status == mf.MFMC_EINVAL
+    g.set_iteration_limits()                  # 0, 0: the defaults
+    f, _ = mf.mfmc_solve_batch([g] * 3, seeds)
+    o = O.OracleModel(**{k: v for k, v in kw.items() if k != "beta2"})
+    for i, s in enumerate(seeds):
+        fr, _, _, _ = B2.solve_sample(o, int(s), 0.05, 5)
+        assert abs(f[i] - fr) <= 1e-8 * fr
+    # a CG bound of one iteration only makes each correction coarser: the Newton passes still
+    # converge to the same tolerance within their default bound
+    g.set_iteration_limits(cg_max=1)
+    f1, _ = mf.mfmc_solve_batch([g] * 3, seeds)
+    assert np.abs(f1 - f).max() <= 1e-8
