@@ -129,7 +129,8 @@ def dist_env():
 
 def cpu_baseline(seconds=12.0):
     """The FP64 oracle on the host cores on a bounded sample of the workload: samples 0, 1, ...
-    of the 512, each for as many of its 1000 steps as fit, until about `seconds` of CPU work."""
+    of the 512, each for as many of its 1000 steps as fit, until about `seconds` of CPU work.
+    Returns the baseline record and the oracle's solutions (seed, steps, f, mean, u(T))."""
     import oracle
     o = oracle.OracleModel(n=N_LATTICE, delta=R_CELLS / N_LATTICE, eps=EPS, eps_lo=EPS_LO, eps_hi=EPS_HI,
                            tau=TAU, nsteps=NSTEPS, ic=1, ic_amp=SIGMA, bc=BC, bc_value=BC_VALUE)
@@ -140,17 +141,52 @@ def cpu_baseline(seconds=12.0):
     o.solve(u0, eps, nsteps=10)
     dt10 = time.perf_counter() - t
     steps = int(max(10, min(NSTEPS, 10 * seconds / max(dt10, 1e-6))))
-    pts, dt, done = 0, 0.0, 0
+    pts, dt, done, sols = 0, 0.0, 0, []
     while done < 64 and (dt < seconds or done == 0):
         s = SEED_BASE + done
         eps, u0 = o.sample_eps(s), o.initial_field(s)
         t = time.perf_counter()
-        o.solve(u0, eps, nsteps=steps)
+        uT, mean = o.solve(u0, eps, nsteps=steps)
         dt += time.perf_counter() - t
         pts += N_LATTICE * N_LATTICE * steps
+        sols.append((s, steps, 0.5 * (1.0 + mean), mean, uT))
         done += 1
-    return {"value": pts / dt, "unit": METRIC, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{done} sample(s) of 256x256, {steps} of 1000 steps each, FP64 direct disc sum ({dt:.1f} s)"}
+    return ({"value": pts / dt, "unit": METRIC, "cores": oracle.num_threads(), "kind": "oracle",
+             "sample": f"{done} sample(s) of 256x256, {steps} of 1000 steps each, FP64 direct disc sum ({dt:.1f} s)"},
+            sols)
+
+
+def oracle_check(mfmc, sols, algo_req):
+    """The GPU path (the benchmark's algorithm, one batch) on the samples the CPU baseline solved,
+    against the FP64 oracle's solutions: OoI (relative), mean of u and the field (absolute), and
+    the bounds [-1, 1]."""
+    import numpy as np
+    import torch
+    if not sols:
+        return None
+    steps = sols[0][1]
+    g = mfmc.Model(n=N_LATTICE, delta=R_CELLS / N_LATTICE, eps=EPS, eps_lo=EPS_LO, eps_hi=EPS_HI, tau=TAU,
+                   nsteps=steps, ic=mfmc.IC_SMOOTHED_GAUSS, ic_amp=SIGMA, algo=algo_req, bc=BC, bc_value=BC_VALUE)
+    seeds = np.array([s for s, _, _, _, _ in sols], dtype=np.uint64)
+    k = len(seeds)
+    u0 = torch.empty((k, N_LATTICE, N_LATTICE), dtype=torch.float32, device="cuda")
+    uT = torch.empty_like(u0)
+    f = torch.empty(k, dtype=torch.float64, device="cuda")
+    ubar = torch.empty(k, dtype=torch.float64, device="cuda")
+    eps = torch.tensor(mfmc.mfmc_sample_eps(g, seeds), dtype=torch.float64, device="cuda")
+    mfmc.mfmc_init_fields(g, seeds, u0)
+    mfmc.mfmc_solve_fields(g, u0, k, eps=eps, uT=uT, ubar=ubar, ooi=f)
+    torch.cuda.synchronize()
+    uT, f, ubar = uT.cpu().numpy().astype(np.float64), f.cpu().numpy(), ubar.cpu().numpy()
+    rel, dm, du = 0.0, 0.0, 0.0
+    for i, (_, _, fr, mr, ur) in enumerate(sols):
+        rel = max(rel, abs(f[i] - fr) / abs(fr))
+        dm = max(dm, abs(ubar[i] - mr))
+        du = max(du, float(np.abs(uT[i] - ur).max()))
+    return {"samples": k, "steps": steps, "max_rel_ooi_err": rel, "max_abs_ubar_err": dm,
+            "max_abs_field_err": du, "bounds_exact": bool(np.abs(uT).max() <= 1.0),
+            "target_rel_ooi_err": 1e-5, "algo": g.info().algo,
+            "what": "GPU (FP32 fields) vs FP64 CPU oracle, the first samples of the timed batch's seeds"}
 
 
 def run_reference(args):
@@ -283,7 +319,9 @@ def run_ours(args):
     batched_sps = ws * ns / (ms_step * 1e-3)
 
     peak_gbs, sm_max, peak_kind = load_peaks()
-    launches_per_solve = NSTEPS + 2
+    # step kernels, then padding, coefficients and the OoI finalisation (and for the row-streaming
+    # kernel its field reduction)
+    launches_per_solve = NSTEPS + (4 if algo.startswith("row-stream") else 3)
     kernel_ms = ms_step / NSTEPS  # average step-kernel launch (upper bound: includes launch gaps)
     bytes_launch = 8.0 * ns * N_LATTICE * N_LATTICE
     achieved = bytes_launch / (kernel_ms * 1e-3) / 1e9
@@ -292,7 +330,7 @@ def run_ours(args):
     if os.path.exists(tpath):
         try:
             tr = json.load(open(tpath))
-            key = f"{N_LATTICE}_{R_CELLS}_{algo}" + ("_collar" if BC == 1 else "")
+            key = f"{N_LATTICE}_{R_CELLS}_{algo.split(' (')[0]}" + ("_collar" if BC == 1 else "")
             if key in tr:
                 traffic = tr[key]
         except Exception:
@@ -324,7 +362,10 @@ def run_ours(args):
                 "gpu_launches": args.steps * launches_per_solve,
                 "clocks": clocks}
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"], sols = cpu_baseline()
+            line["oracle_check"] = oracle_check(mfmc, sols, algo_req)
+        if not args.no_extras and ws == 1:
+            line.update(extra_metrics(mfmc, model, algo_req, ns, ms_step, args))
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
@@ -357,17 +398,15 @@ def _batched_cost(mfmc, model, ns, seed_base):
     return e0.elapsed_time(e1) * 1e-3 / ns
 
 
-def run_hierarchy(args):
+def hierarchy_metrics(mfmc, n_val, budgets=(10.0, 30.0, 100.0, 300.0), reps=10, plain=True):
     """MFMC hierarchy with a fixed physical horizon delta = 1/32 (512^2/R=16, 256^2/8,
     128^2/4, 64^2/2), 1000 steps, the four-nuclei initial condition of Eq. (ic) whose
     theta is the shared random input, eps = 0.02 U[0.8, 1.2].  Pilot of 64 samples,
-    costs measured as batched GPU seconds per sample, 10 replicate MC and MFMC estimates
-    per budget, MSE against a validation mean of HF samples."""
+    costs measured as batched GPU seconds per sample, `reps` replicate MC and MFMC estimates
+    per budget B = b C_1, MSE against a validation mean of n_val HF samples (Section 3,
+    Eqs. mse_error and error_theory)."""
     import numpy as np
     import torch
-    from paper_2310_10750_gb300 import build as pkg_build
-    pkg_build.build()
-    from paper_2310_10750_gb300 import mfmc
     base = 20231016 + 1000003 * 2
     levels = [(512, 16), (256, 8), (128, 4), (64, 2)]
     common = dict(eps=0.02, eps_lo=0.016, eps_hi=0.024, tau=1e-3, nsteps=1000, ic=mfmc.IC_NUCLEI)
@@ -376,7 +415,7 @@ def run_hierarchy(args):
     names = {1: "direct", 2: "prefix", 4: "resident", 6: "prefix-tma", 7: "row-stream"}
     algos = [names.get(m.info().algo, str(m.info().algo)) for m in models]
     plain_cost = None
-    if not args.no_plain:
+    if plain:
         m0 = models[0]
         u0 = torch.empty((1, 512, 512), dtype=torch.float32, device="cuda")
         mfmc.mfmc_init_fields(m0, _seeds(base, 1), u0)
@@ -391,7 +430,6 @@ def run_hierarchy(args):
     n_pilot = 64
     pilot = np.stack([mfmc.mfmc_solve_batch([m] * n_pilot, _seeds(base, n_pilot))[0] for m in models])
     # validation mean of the high-fidelity OoI
-    n_val = args.validation
     t = time.perf_counter()
     chunk = 4096                                         # bounded device memory per call
     fval = np.concatenate([mfmc.mfmc_solve_batch([models[0]] * min(chunk, n_val - o),
@@ -399,7 +437,6 @@ def run_hierarchy(args):
                            for o in range(0, n_val, chunk)])
     q_val = float(np.mean(fval))
     t_val = time.perf_counter() - t
-    reps = 10
     rows = []
     next_seed = [base + 10 ** 5]
 
@@ -408,11 +445,12 @@ def run_hierarchy(args):
         next_seed[0] += count
         return s0
 
-    for b in (10.0, 30.0, 100.0, 300.0):
+    plan = None
+    for b in budgets:
         B = b * cost[0]
         plan = mfmc.mfmc_plan(pilot, cost, B, 0)
         p = plan.as_dict()
-        est_mfmc, est_mc, gpu_s = [], [], 0.0
+        est_mfmc, est_mc = [], []
         for r in range(reps):
             s0 = take(p["m"][-1])
             lists = []
@@ -429,32 +467,39 @@ def run_hierarchy(args):
         sig1 = p["sigma_all"][0]
         row = {"budget_gpu_s": B, "budget_over_C1": b, "subset": p["idx"], "m": p["m"],
                "below_min_budget": p["below_min_budget"], "mse_mfmc": mse_mfmc, "mse_mc": mse_mc,
+               "mse_mfmc_per_gpu_s": mse_mfmc * B, "mse_mc_per_gpu_s": mse_mc * B,
                "mse_mfmc_theory": p["mse_theory"], "mse_mc_theory": sig1 ** 2 / max(1, int(B // cost[0])),
-               "mse_ratio_mc_over_mfmc": mse_mc / mse_mfmc if mse_mfmc > 0 else None}
+               "mse_ratio_mc_over_mfmc": mse_mc / mse_mfmc if mse_mfmc > 0 else None,
+               "validation_mse_floor": float(np.var(fval, ddof=1)) / n_val}
         if plain_cost:
             row["mse_mc_plain_loop_theory"] = sig1 ** 2 / max(1e-9, B / plain_cost)
         rows.append(row)
-    line = {"metric": "MFMC MSE per GPU-s (hierarchy)", "value": rows[2]["mse_mfmc"], "unit": "MSE at B = 100 C_1",
-            "higher_is_better": False, "data": "synthetic",
-            "config": {"workload": "MFMC hierarchy delta=1/32: 512^2/R16, 256^2/R8, 128^2/R4, 64^2/R2, 1000 steps,"
-                                   " nuclei IC (Eq. ic), pilot 64, 10 replicates per budget",
-                       "algos": algos},
-            "cost_gpu_s_per_sample": cost, "samples_per_s_per_fidelity": [1.0 / c for c in cost],
+    return {"workload": "MFMC hierarchy delta=1/32: 512^2/R16, 256^2/R8, 128^2/R4, 64^2/R2, 1000 steps, nuclei IC "
+                        f"(Eq. ic), pilot 64, {reps} replicates per budget, validation mean of {n_val} HF samples",
+            "algos": algos, "cost_gpu_s_per_sample": cost, "samples_per_s_per_fidelity": [1.0 / c for c in cost],
             "plain_loop_cost_gpu_s_per_hf_sample": plain_cost,
             "pilot_rho": plan.as_dict()["rho_all"], "pilot_sigma": plan.as_dict()["sigma_all"],
             "q_validation": q_val, "n_validation": n_val, "validation_s": t_val, "budgets": rows}
+
+
+def run_hierarchy(args):
+    from paper_2310_10750_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2310_10750_gb300 import mfmc
+    h = hierarchy_metrics(mfmc, args.validation, plain=not args.no_plain)
+    rows = h["budgets"]
+    line = {"metric": "MFMC MSE per GPU-s (hierarchy)", "value": rows[2]["mse_mfmc"], "unit": "MSE at B = 100 C_1",
+            "higher_is_better": False, "data": "synthetic", "config": {"workload": h["workload"], "algos": h["algos"]}}
+    line.update({k: v for k, v in h.items() if k not in ("workload", "algos")})
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_serving(args):
+def serving_metrics(mfmc, total):
     """Poisson stream of solve requests of mixed fidelity (64^2 .. 1024^2 in 40/30/20/8/2 %,
-    delta = 1/32, 500-2000 steps each) through the continuous-batching server."""
+    delta = 1/32, 500-2000 steps each) through the continuous-batching server: the capacity
+    (2000 requests submitted at once), then `total` requests at 0.8 x that capacity."""
     import numpy as np
-    import torch
-    from paper_2310_10750_gb300 import build as pkg_build
-    pkg_build.build()
-    from paper_2310_10750_gb300 import mfmc
     rng = np.random.default_rng(20231016 + 1000003 * 3)
     sizes = [64, 128, 256, 512, 1024]
     probs = [0.40, 0.30, 0.20, 0.08, 0.02]
@@ -462,7 +507,6 @@ def run_serving(args):
                             nsteps=1000, ic=mfmc.IC_SMOOTHED_GAUSS, ic_amp=0.05) for n in sizes}
     for n, m in models.items():                           # tune each fidelity before serving
         mfmc.mfmc_solve_batch([m] * 8, _seeds(1, 8))
-    total = args.requests
     kinds = rng.choice(sizes, size=total, p=probs)
     steps = rng.integers(500, 2001, size=total)
 
@@ -493,16 +537,82 @@ def run_serving(args):
     st_cap, wall_cap = run_stream(cap_n, 0.0)              # all at once: capacity
     capacity = cap_n / wall_cap
     st, wall = run_stream(total, 0.8 * capacity)
-    line = {"metric": "p50/p99 solve latency (serving)", "value": st["p99_latency_s"], "unit": "s (p99)",
-            "higher_is_better": False, "data": "synthetic",
-            "config": {"workload": f"{total} requests, Poisson at 0.8 x measured capacity, n in 64..1024 "
-                                   "(40/30/20/8/2 %), R = n/32, 500-2000 steps, 120 GB budget"},
+    return {"workload": f"{total} requests, Poisson at 0.8 x measured capacity, n in 64..1024 (40/30/20/8/2 %), "
+                        "R = n/32, 500-2000 steps, 120 GB budget",
             "p50_latency_s": st["p50_latency_s"], "p99_latency_s": st["p99_latency_s"],
             "mean_latency_s": st["mean_latency_s"], "samples_per_s": st["samples_per_s"],
             "capacity_samples_per_s": capacity, "arrival_rate": 0.8 * capacity, "wall_s": wall,
             "completed": st["completed"], "peak_inflight": st["peak_inflight"], "peak_bytes": st["peak_bytes"]}
+
+
+def run_serving(args):
+    from paper_2310_10750_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2310_10750_gb300 import mfmc
+    sv = serving_metrics(mfmc, args.requests)
+    line = {"metric": "p50/p99 solve latency (serving)", "value": sv["p99_latency_s"], "unit": "s (p99)",
+            "higher_is_better": False, "data": "synthetic", "config": {"workload": sv["workload"]}}
+    line.update({k: v for k, v in sv.items() if k != "workload"})
     print(json.dumps(line), flush=True)
     return 0
+
+
+def fidelity_rates(mfmc):
+    """Batched samples/s of each fidelity of the serving mix (delta = 1/32: n = 64 .. 1024,
+    R = n/32, 1000 steps, smoothed-noise IC), each batch large enough to fill the GPU."""
+    base = 20231016 + 1000003 * 6
+    out = {}
+    for n, bs in ((64, 4096), (128, 2048), (256, 512), (512, 128), (1024, 64)):
+        m = mfmc.Model(n=n, delta=(n // 32) / n, eps=0.02, eps_lo=0.016, eps_hi=0.024, tau=1e-3, nsteps=1000,
+                       ic=mfmc.IC_SMOOTHED_GAUSS, ic_amp=0.05)
+        c = _batched_cost(mfmc, m, bs, base)
+        out[f"{n}x{n}_R{n // 32}"] = {"samples_per_s": 1.0 / c, "batch": bs, "algo": m.info().algo,
+                                      "grid_pt_updates_per_s": n * n * 1000 / c}
+    return out
+
+
+def extra_metrics(mfmc, model, algo_req, ns, ms_step, args):
+    """The metric's other parts, measured after the headline timing so that they cannot
+    perturb it: the plain form on the benchmark's own kernel, samples/s per fidelity, serving
+    latency (the full request stream) and MFMC MSE per GPU-second at B = 100 C_1."""
+    import numpy as np
+    import torch
+    out = {}
+    # one sample per launch, one launch per step, with the kernel the batched path uses
+    k = 4
+    algo = model.info().algo
+    seeds = np.arange(k, dtype=np.uint64) + np.uint64(SEED_BASE)
+    u0 = torch.empty((k, N_LATTICE, N_LATTICE), dtype=torch.float32, device="cuda")
+    ooi = torch.empty(k, dtype=torch.float64, device="cuda")
+    eps = torch.tensor(mfmc.mfmc_sample_eps(model, seeds), dtype=torch.float64, device="cuda")
+    mfmc.mfmc_init_fields(model, seeds, u0)
+    mfmc.mfmc_solve_fields_algo(model, algo, u0[:1], 1, eps=eps[:1], ooi=ooi[:1])  # warm (graph capture)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(k):
+        mfmc.mfmc_solve_fields_algo(model, algo, u0[i:i + 1], 1, eps=eps[i:i + 1], ooi=ooi[i:i + 1])
+    e1.record()
+    torch.cuda.synchronize()
+    plain_sps = k / (e0.elapsed_time(e1) * 1e-3)
+    batched_sps = ns / (ms_step * 1e-3)
+    out["plain_form_same_kernel"] = {"samples_per_s": plain_sps, "speedup_batched_vs_plain": batched_sps / plain_sps,
+                                     "algo": algo, "what": "the batched path's own kernel, one sample per launch, "
+                                                           "one launch per step (4 samples)"}
+    t = time.perf_counter()
+    out["samples_per_s_per_fidelity"] = fidelity_rates(mfmc)
+    out["serving"] = serving_metrics(mfmc, args.requests)
+    h = hierarchy_metrics(mfmc, args.validation, budgets=(100.0,), reps=10, plain=False)
+    r = h["budgets"][0]
+    out["mfmc"] = {"workload": h["workload"], "budget_over_C1": 100.0, "budget_gpu_s": r["budget_gpu_s"],
+                   "mse_mfmc": r["mse_mfmc"], "mse_mc": r["mse_mc"], "mse_mfmc_per_gpu_s": r["mse_mfmc_per_gpu_s"],
+                   "mse_mc_per_gpu_s": r["mse_mc_per_gpu_s"], "mse_ratio_mc_over_mfmc": r["mse_ratio_mc_over_mfmc"],
+                   "mse_mfmc_theory": r["mse_mfmc_theory"], "mse_mc_theory": r["mse_mc_theory"],
+                   "validation_mse_floor": r["validation_mse_floor"], "n_validation": h["n_validation"],
+                   "subset": r["subset"], "m": r["m"], "cost_gpu_s_per_sample": h["cost_gpu_s_per_sample"],
+                   "algos": h["algos"]}
+    out["extras_wall_s"] = time.perf_counter() - t
+    return out
 
 
 def run_large(args):
@@ -676,7 +786,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="single", choices=["single", "hierarchy", "serving", "large", "mixed", "paper"],
                     help="single (the headline, default), or one of the other measured configurations")
-    ap.add_argument("--validation", type=int, default=2048, help="hierarchy: HF samples of the validation mean")
+    ap.add_argument("--validation", type=int, default=16384, help="hierarchy: HF samples of the validation mean")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline only: skip the serving, per-fidelity and MFMC measurements")
     ap.add_argument("--requests", type=int, default=20000, help="serving: requests in the stream")
     ap.add_argument("--beta2", type=float, default=0.0, help="paper: beta2 of the nine models (the paper's 0.05)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
