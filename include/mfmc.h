@@ -392,6 +392,14 @@ mfmc_status mfmc_submit(mfmc_server *srv, const mfmc_model *model,
  * queued or running, MFMC_ENOTFOUND for an unknown ticket. */
 mfmc_status mfmc_poll(mfmc_server *srv, uint64_t ticket, double *ooi, double *latency_s);
 
+/* When a finished request was submitted, admitted (its cohort queued on the GPU) and found
+ * complete, in seconds since the server was created (host outputs, each may be NULL).  Kept
+ * after mfmc_poll, until mfmc_server_destroy.  MFMC_EBUSY while the request runs,
+ * MFMC_ENOTFOUND for a ticket the server never issued.  Serving is not in the paper: this
+ * shows which requests ran on the device at the same time. */
+mfmc_status mfmc_request_times(mfmc_server *srv, uint64_t ticket, double *submit_s, double *admit_s,
+                               double *done_s);
+
 /* Block until every submitted request has completed. */
 mfmc_status mfmc_server_drain(mfmc_server *srv);
 

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -38,6 +39,7 @@ struct ServerReq {
     uint64_t seed;
     int nsteps;
     double t_submit;
+    double t_admit = -1.0;
 };
 
 struct Cohort {
@@ -95,6 +97,9 @@ struct mfmc_server {
     std::deque<ServerReq> pending;
     std::vector<Cohort *> running;
     std::unordered_map<uint64_t, std::pair<double, double>> results;
+    // submit, admit and completion times of every finished request (kept until destroy)
+    std::unordered_map<uint64_t, std::array<double, 3>> times;
+    double t0 = 0;  // server creation
     std::unordered_set<uint64_t> open;  // submitted, result not yet polled
     uint64_t next_ticket = 1;
     size_t bytes_in_use = 0, peak_bytes = 0;
@@ -208,6 +213,7 @@ static void server_loop(mfmc_server *S) {
                     c->variant = r.model->tma_variant;
                     fresh.push_back(c);
                 }
+                r.t_admit = now_s();
                 c->reqs.push_back(r);
                 c->slots.push_back(S->free_slots.back());
                 S->free_slots.pop_back();
@@ -263,6 +269,7 @@ static void server_loop(mfmc_server *S) {
                     const ServerReq &r = c->reqs[q];
                     const double lat = t - r.t_submit;
                     S->results[r.ticket] = {S->res_host[2 * c->slots[q]], lat};
+                    S->times[r.ticket] = {r.t_submit - S->t0, r.t_admit - S->t0, t - S->t0};
                     S->free_slots.push_back(c->slots[q]);
                     S->latencies.push_back(lat);
                     S->completed++;
@@ -292,6 +299,7 @@ mfmc_status mfmc_server_create(size_t hbm_budget_bytes, int max_slots, mfmc_serv
     if (!S) return fail(MFMC_ENOMEM, "host allocation failed");
     S->budget = hbm_budget_bytes;
     S->max_slots = max_slots;
+    S->t0 = now_s();
     cudaError_t e = cudaGetDevice(&S->device);
     if (e == cudaSuccess)
         e = cudaHostAlloc((void **)&S->res_host, 2 * (size_t)max_slots * sizeof(double), cudaHostAllocMapped);
@@ -335,6 +343,20 @@ mfmc_status mfmc_submit(mfmc_server *S, const mfmc_model *model, const mfmc_samp
     }
     S->cv.notify_all();
     *ticket = r.ticket;
+    return MFMC_OK;
+}
+
+mfmc_status mfmc_request_times(mfmc_server *S, uint64_t ticket, double *submit_s, double *admit_s, double *done_s) {
+    if (!S) return fail(MFMC_EINVAL, "NULL server");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->times.find(ticket);
+    if (it == S->times.end()) {
+        if (S->open.count(ticket)) return MFMC_EBUSY;
+        return fail(MFMC_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    }
+    if (submit_s) *submit_s = it->second[0];
+    if (admit_s) *admit_s = it->second[1];
+    if (done_s) *done_s = it->second[2];
     return MFMC_OK;
 }
 

@@ -126,6 +126,7 @@ class mfmc_server_stats(ctypes.Structure):
 _sig("mfmc_server_create", _st, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(_vp)])
 _sig("mfmc_submit", _st, [_vp, _vp, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)])
 _sig("mfmc_poll", _st, [_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)])
+_sig("mfmc_request_times", _st, [_vp, ctypes.c_uint64] + [ctypes.POINTER(ctypes.c_double)] * 3)
 _sig("mfmc_server_drain", _st, [_vp])
 _sig("mfmc_server_get_stats", _st, [_vp, ctypes.POINTER(mfmc_server_stats)])
 _sig("mfmc_server_destroy", None, [_vp])
@@ -372,6 +373,16 @@ class Server:
             return None
         _check(st)
         return f.value, lat.value
+
+    def times(self, ticket: int):
+        """(submit_s, admit_s, done_s) of a finished request, seconds since the server started;
+        None while it runs."""
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        st = _L.mfmc_request_times(self.handle, ticket, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+        if st == MFMC_EBUSY:
+            return None
+        _check(st)
+        return a.value, b.value, c.value
 
     def drain(self):
         _check(_L.mfmc_server_drain(self.handle))

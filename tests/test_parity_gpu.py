@@ -133,7 +133,9 @@ def test_plain_mc_config_64_R4(gpu_lib, algo):
         assert abs(f[i] - fr) <= 1e-5 * fr
         tol = 200 * 4e-6 * 0.05 * growth
         assert np.abs(uT[i] - ur).max() <= tol
-        assert abs(ubar[i] - mean) <= 2 * tol
+        # the mean of u is O(1e-4) here: its error is the average of per-point rounding errors of
+        # both signs (measured near 1e-10), bounded relative to |mean| rather than to f
+        assert abs(ubar[i] - mean) <= 1e-5 * abs(mean) + 1e-9
 
 
 @pytest.mark.parametrize("algo", ["prefix", "resident", "direct", "tma"])
@@ -236,8 +238,8 @@ def _gpu_batch_of_config(mf, n, R, steps, ns, algo="auto", ic=1, base=0):
 @pytest.mark.slow
 def test_single_fidelity_256_R8_full_size_sampled(gpu_lib):
     # 256 x 256, delta = 8h, 1000 steps, 512 samples in one launch configuration (the one
-    # the benchmark times); the oracle checks samples 0 and 511 element by element and every
-    # sample is checked by the exact linear-regime identity of the mean.
+    # the benchmark times); the oracle checks every 64th sample and the last element by element
+    # and every sample is checked by the exact linear-regime identity of the mean.
     mf = gpu_lib
     n, R, steps, ns = 256, 8, 1000, 512
     g, o = _gpu_batch_of_config(mf, n, R, steps, ns)
@@ -251,9 +253,10 @@ def test_single_fidelity_256_R8_full_size_sampled(gpu_lib):
         c2 = 1e-3 / (1 + 1e-3 * cg)
         pred = (1 + c2) ** steps * u0[i].mean()
         assert abs(ubar[i] - pred) <= 1e-6 * np.abs(u0[i]).max() + 1e-9
-    for i in (0, ns - 1):
+    for i in list(range(0, ns, 64)) + [ns - 1]:
         fr, mean, ur, _ = o.solve_sample(int(seeds[i]))
         assert abs(f[i] - fr) <= 1e-5 * fr
+        assert abs(ubar[i] - mean) <= 1e-5 * abs(mean) + 1e-9
         assert np.abs(uT[i] - ur).max() <= steps * 4e-6 * 0.05 * math.e
 
 
@@ -268,6 +271,8 @@ def test_hierarchy_levels_sampled(gpu_lib, n, R):
     for i in (0, 15):
         fr, mean, ur, _ = o.solve_sample(int(seeds[i]))
         assert abs(f[i] - fr) <= 1e-5 * fr
+        assert abs(ubar[i] - mean) <= 1e-5 * abs(mean) + 1e-9
+        assert np.abs(uT[i] - ur).max() <= (1000 if n < 512 else 200) * 4e-6 * math.e
 
 
 @pytest.mark.parametrize("n,R,bh", [(128, 2, 64), (128, 4, 0), (256, 8, 0), (256, 8, 64), (256, 8, 40),

@@ -46,6 +46,8 @@ def test_alone_and_in_the_mix_are_identical(gpu_lib):
     srv = mf.Server(8 << 30, 256)
     rng = np.random.default_rng(0)
     tickets = {}
+    # a long request first (6000 steps): every later request is admitted while it runs
+    long_t = srv.submit(ms[256], 4242, params=mf.make_params(1, nsteps=[6000])[0])
     for i in range(120):
         n = int(rng.choice([64, 128, 256], p=[0.5, 0.3, 0.2]))
         tickets[srv.submit(ms[n], 5000 + i)] = (n, 5000 + i)
@@ -54,14 +56,28 @@ def test_alone_and_in_the_mix_are_identical(gpu_lib):
                 tickets[srv.submit(ms[pn], ps)] = (pn, ps)
         if i % 20 == 0:
             time.sleep(0.002)   # later requests arrive while earlier ones run
-    res = wait(srv, list(tickets))
+    res = wait(srv, list(tickets) + [long_t])
     st = srv.stats()
+    times = {t: srv.times(t) for t in list(tickets) + [long_t]}
     srv.close()
+    # a sample's arithmetic does not depend on the cohort it runs in (per-sample tiles or rows
+    # summed in a fixed order, the OoI from fixed-order partials): identical OoIs
     for t, (n, seed) in tickets.items():
         if (n, seed) in alone:
-            f = res[t][0]
-            assert abs(f - alone[(n, seed)]) <= 1e-5 * alone[(n, seed)]
-    assert st["completed"] == len(tickets)
+            assert res[t][0] == alone[(n, seed)], (n, seed)
+    assert st["completed"] == len(tickets) + 1
+    # continuous batching, not a queue: requests of different cohorts ran on the device at the
+    # same time, and every probe in the mix was admitted while some other request was in flight
+    assert st["peak_inflight"] > 1
+    for t, (n, seed) in tickets.items():
+        if (n, seed) in alone:
+            _, a0, d0 = times[t]
+            assert any(u != t and a1 < a0 < d1 for u, (_, a1, d1) in times.items()), (n, seed)
+    _, a_long, d_long = times[long_t]
+    assert sum(1 for t, (_, a, d) in times.items() if t != long_t and a_long < a < d_long) >= 100
+    with pytest.raises(mf.MfmcError) as e:
+        mf.Server(1 << 20, 2).times(12345)
+    assert e.value.status == mf.MFMC_ENOTFOUND
     assert st["p99_latency_s"] >= st["p50_latency_s"] > 0
     # spot check against the oracle
     for t, (n, seed) in list(tickets.items())[:3]:
