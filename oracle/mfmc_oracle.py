@@ -14,7 +14,7 @@ Follows the paper's steps in its order and notation:
   the telescoping estimator                       (Eq. MFMC_estimator)
   empirical and theoretical MSE                   (Eqs. mse_error, error_theory)
 
-Readings where the paper is silent (each listed in the design notes):
+Readings where the paper is silent (the choices this oracle makes):
   * ties in rho^2 are broken by model index (stable sort);
   * a zero denominator in Eq. (conditionb) makes the subset infeasible;
   * variances use the n-1 convention (rho and alpha do not depend on it);

@@ -34,3 +34,42 @@ def test_large_hf_fp32_kahan_and_fft_against_oracle(gpu_lib):
         f = float(ooi.cpu()[0])
         assert abs(f - fr) <= 1e-9 * fr, algo
         assert np.abs(uT.cpu().numpy()[0].astype(np.float64) - ur).max() <= tol, algo
+
+
+def _fixture():
+    from tests.conftest import read_golden
+    rows = read_golden("large_hf_1024_R32_100steps.txt")
+    return [(int(r[1]), float(r[2]), float(r[3]), np.array([float(v) for v in r[4:]])) for r in rows]
+
+
+@pytest.mark.slow
+def test_large_hf_samples_0_to_3_100_steps_fp32_and_kahan(gpu_lib):
+    # samples 0..3 of the large configuration, 100 steps, against the FP64 oracle's solutions
+    # stored by tests/golden/make_large_hf_fixture.py (OoI, mean and u at 512 fixed points):
+    # the plain FP32 sums of the autotuned kernel and the compensated ones.  Bound on the field:
+    # 100 x 4e-6 x max|u| e^{c_F T} with max|u| <= 0.05 e^{0.1}.
+    import torch
+    mf = gpu_lib
+    n, R, steps = 1024, 32, 100
+    kw = dict(n=n, delta=R / n, eps=0.02, eps_lo=0.016, eps_hi=0.024, tau=1e-3, nsteps=steps, ic=1, ic_amp=0.05)
+    ref = _fixture()
+    assert len(ref) == 4
+    seeds = np.array([r[0] for r in ref], dtype=np.uint64)
+    pts = np.random.default_rng(1024).integers(0, n, size=(512, 2))
+    tol = steps * 4e-6 * 0.05 * math.exp(0.1) * math.exp(0.1)
+    for algo in (mf.ALGO_AUTO, mf.ALGO_PREFIX_KAHAN):
+        g = mf.Model(algo=algo, **kw)
+        u0 = torch.empty((4, n, n), dtype=torch.float32, device="cuda")
+        uT = torch.empty_like(u0)
+        ooi = torch.empty(4, dtype=torch.float64, device="cuda")
+        ubar = torch.empty(4, dtype=torch.float64, device="cuda")
+        eps = torch.tensor(mf.mfmc_sample_eps(g, seeds), dtype=torch.float64, device="cuda")
+        mf.mfmc_init_fields(g, seeds, u0)
+        mf.mfmc_solve_fields(g, u0, 4, eps=eps, uT=uT, ooi=ooi, ubar=ubar)
+        torch.cuda.synchronize()
+        f, m, u = ooi.cpu().numpy(), ubar.cpu().numpy(), uT.cpu().numpy().astype(np.float64)
+        for i, (_, fr, mr, ur) in enumerate(ref):
+            assert abs(f[i] - fr) <= 1e-9 * fr, (algo, i)
+            assert abs(m[i] - mr) <= 1e-5 * abs(mr) + 1e-9, (algo, i)
+            assert np.abs(u[i][pts[:, 0], pts[:, 1]] - ur).max() <= tol, (algo, i)
+        assert np.abs(u).max() <= 1.0
