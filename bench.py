@@ -319,9 +319,9 @@ def run_ours(args):
     batched_sps = ws * ns / (ms_step * 1e-3)
 
     peak_gbs, sm_max, peak_kind = load_peaks()
-    # step kernels, then padding, coefficients and the OoI finalisation (and for the row-streaming
-    # kernel its field reduction)
-    launches_per_solve = NSTEPS + (4 if algo.startswith("row-stream") else 3)
+    # step kernels, then coefficients and the OoI finalisation, and either the padding kernel (tile
+    # kernels) or the field reduction (row-streaming kernel, whose initial copy is a memcpy)
+    launches_per_solve = NSTEPS + 3
     kernel_ms = ms_step / NSTEPS  # average step-kernel launch (upper bound: includes launch gaps)
     bytes_launch = 8.0 * ns * N_LATTICE * N_LATTICE
     achieved = bytes_launch / (kernel_ms * 1e-3) / 1e9

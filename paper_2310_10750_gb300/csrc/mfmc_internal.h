@@ -169,6 +169,7 @@ mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0,
 struct TmaBuffers {
     float *padA = nullptr, *padB = nullptr;
     CUtensorMap mapA, mapB;
+    CUtensorMap mapA1, mapB1;  // the row-streaming kernel's one-row boxes
     size_t cap = 0;
     double *partials = nullptr;
     int *status = nullptr;

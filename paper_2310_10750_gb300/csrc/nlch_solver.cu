@@ -597,8 +597,8 @@ mfmc_status run_solve_tma(Model &m, int kahan, int variant, const StepCoef *coef
 // Partials of the row-streaming kernel: one FP64 row sum per (sample, strip, row).
 static int rows_partials_per_sample(const Model &m) { return (m.d.n / 128) * m.d.n; }
 
-__global__ void rows_ooi_kernel(const float *plain, const float *padA, const float *padB, const int *steps_ps,
-                                int nsteps, int n, int P, int G, int strips, size_t ns, double *partials) {
+__global__ void rows_ooi_kernel(const float *plain, const float *fieldA, const float *fieldB, const int *steps_ps,
+                                int nsteps, int n, int strips, size_t ns, double *partials) {
     const int lane = threadIdx.x & 31;
     const long long total = (long long)ns * strips * n;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
@@ -607,10 +607,9 @@ __global__ void rows_ooi_kernel(const float *plain, const float *padA, const flo
         const int y = (int)(r - col * n);
         const int sample = (int)(col / strips), strip = (int)(col - (long long)sample * strips);
         const int ks = steps_ps ? steps_ps[sample] : nsteps;
-        const float *src = plain ? plain + (size_t)sample * n * n + (size_t)y * n + 128 * strip + 4 * lane
-                                 : ((ks & 1) ? padA : padB) + (size_t)sample * P * P + (size_t)(G + y) * P + G +
-                                       128 * strip + 4 * lane;
-        const float4 v = *reinterpret_cast<const float4 *>(src);
+        const float *f = plain ? plain : ((ks & 1) ? fieldA : fieldB);
+        const float4 v = *reinterpret_cast<const float4 *>(f + (size_t)sample * n * n + (size_t)y * n + 128 * strip +
+                                                           4 * lane);
         double rs = ((double)v.x + (double)v.y) + ((double)v.z + (double)v.w);
         for (int off = 16; off > 0; off >>= 1) rs += __shfl_down_sync(0xffffffffu, rs, off);
         if (lane == 0) partials[r] = rs;
@@ -618,39 +617,39 @@ __global__ void rows_ooi_kernel(const float *plain, const float *padA, const flo
 }
 
 // Geometry of the row-streaming kernel: 16 warps per CTA at most, n / 128 warps per sample, a
-// padded row of P floats read through a 4-D view (k pieces of P / k <= 256 floats, P / k a
-// multiple of 4 so each piece is a whole number of 16-byte units).
+// row of n floats read through a 4-D view (k pieces of n / k <= 256 floats, n / k a multiple of
+// 4 so each piece is a whole number of 16-byte units).
 static bool rows_geom(const Model &m, RowsGeom *g) {
-    const int n = m.d.n, G = (m.R + 3) & ~3, P = n + 2 * G;
+    const int n = m.d.n;
     if (n % 128 != 0 || n > 2048) return false;
     g->strips = n / 128;
     g->gs = 16 / g->strips;
     g->warps = g->gs * g->strips;
-    g->P = P;
     g->k = 0;
     for (int k = 1; k <= 64; ++k)
-        if (P % k == 0 && P / k <= 256 && (P / k) % 4 == 0) {
+        if (n % k == 0 && n / k <= 256 && (n / k) % 4 == 0) {
             g->k = k;
             break;
         }
     if (g->k == 0) return false;
     const RowsLauncher *L = rows_launcher(m.R);
     if (!L) return false;
-    g->stage_floats = g->gs * L->ch * P;
+    g->stage_floats = g->gs * L->ch * n;
     g->smem = (size_t)L->nstg * g->stage_floats * sizeof(float) + 128;
     return g->smem <= 227 * 1024;
 }
 
-// Tensor map of the padded fields [cap][P][P] as (P / k, k, P, cap): a box of (P / k, k, CH, gs)
-// is CH whole rows of gs samples.
-static mfmc_status encode_rows_map(CUtensorMap *map, float *base, const RowsGeom &g, size_t cap, int ch) {
+// Tensor map of the fields [cap][n][n] as (n / k, k, cap, n): a box of (n / k, k, gs, rows) is
+// `rows` whole rows of gs samples, stored in shared memory as [row][sample][n].
+static mfmc_status encode_rows_map(CUtensorMap *map, float *base, const Model &m, const RowsGeom &g, size_t cap,
+                                   int rows) {
     auto enc = tensor_map_encoder();
     if (!enc) return fail(MFMC_ECUDA, "cuTensorMapEncodeTiled is unavailable");
-    const int P = g.P, w = P / g.k;
-    const cuuint64_t dims[4] = {(cuuint64_t)w, (cuuint64_t)g.k, (cuuint64_t)P, (cuuint64_t)cap};
-    const cuuint64_t strides[3] = {(cuuint64_t)w * sizeof(float), (cuuint64_t)P * sizeof(float),
-                                   (cuuint64_t)P * P * sizeof(float)};
-    const cuuint32_t box[4] = {(cuuint32_t)w, (cuuint32_t)g.k, (cuuint32_t)ch, (cuuint32_t)g.gs};
+    const int n = m.d.n, w = n / g.k;
+    const cuuint64_t dims[4] = {(cuuint64_t)w, (cuuint64_t)g.k, (cuuint64_t)cap, (cuuint64_t)n};
+    const cuuint64_t strides[3] = {(cuuint64_t)w * sizeof(float), (cuuint64_t)n * n * sizeof(float),
+                                   (cuuint64_t)n * sizeof(float)};
+    const cuuint32_t box[4] = {(cuuint32_t)w, (cuuint32_t)g.k, (cuuint32_t)g.gs, (cuuint32_t)rows};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -659,12 +658,20 @@ static mfmc_status encode_rows_map(CUtensorMap *map, float *base, const RowsGeom
     return MFMC_OK;
 }
 
+static mfmc_status encode_rows_maps(TmaBuffers *b, const Model &m, const RowsGeom &g, int ch) {
+    mfmc_status s = encode_rows_map(&b->mapA, b->padA, m, g, b->cap, ch);
+    if (s == MFMC_OK) s = encode_rows_map(&b->mapA1, b->padA, m, g, b->cap, 1);
+    if (s == MFMC_OK) s = encode_rows_map(&b->mapB, b->padB, m, g, b->cap, ch);
+    if (s == MFMC_OK) s = encode_rows_map(&b->mapB1, b->padB, m, g, b->cap, 1);
+    return s;
+}
+
 mfmc_status rows_alloc_buffers(const Model &m, int bh, size_t ns, TmaBuffers *b, cudaStream_t alloc_st) {
     const RowsLauncher *L = rows_launcher(m.R);
     RowsGeom g;
     if (!L || !rows_geom(m, &g)) return fail(MFMC_EINVAL, "no row-streaming kernel for n = %d, R = %d", m.d.n, m.R);
     if (bh != 0 && bh < 8) return fail(MFMC_EINVAL, "band height %d < 8", bh);
-    const size_t bytes = ns * (size_t)g.P * g.P * sizeof(float);
+    const size_t bytes = ns * (size_t)m.d.n * m.d.n * sizeof(float);
     MFMC_CUDA(cudaMallocAsync((void **)&b->padA, bytes, alloc_st));
     MFMC_CUDA(cudaMallocAsync((void **)&b->padB, bytes, alloc_st));
     MFMC_CUDA(cudaMallocAsync((void **)&b->partials, ns * (size_t)rows_partials_per_sample(m) * sizeof(double),
@@ -672,17 +679,15 @@ mfmc_status rows_alloc_buffers(const Model &m, int bh, size_t ns, TmaBuffers *b,
     MFMC_CUDA(cudaMallocAsync((void **)&b->status, sizeof(int), alloc_st));
     MFMC_CUDA(cudaMemsetAsync(b->status, 0, sizeof(int), alloc_st));
     b->cap = ns;
-    mfmc_status s = encode_rows_map(&b->mapA, b->padA, g, ns, L->ch);
-    if (s == MFMC_OK) s = encode_rows_map(&b->mapB, b->padB, g, ns, L->ch);
-    return s;
+    return encode_rows_maps(b, m, g, L->ch);
 }
 
-// The row-streaming kernel: constant kernel, integer R <= 8, 128-column strips (n % 128 == 0,
-// n <= 2048), four columns per thread.
+// The row-streaming kernel: constant kernel, periodic lattice, integer R <= 8, 128-column strips
+// (n % 128 == 0, n <= 2048), four columns per thread.
 bool rows_supported(const Model &m, int rx) {
     RowsGeom g;
-    return m.d.kernel == MFMC_KERNEL_CONSTANT && m.integer_R && rx == 4 && rows_launcher(m.R) != nullptr &&
-           rows_geom(m, &g);
+    return m.d.kernel == MFMC_KERNEL_CONSTANT && m.d.bc == MFMC_BC_PERIODIC && m.integer_R && rx == 4 &&
+           rows_launcher(m.R) != nullptr && rows_geom(m, &g);
 }
 
 mfmc_status run_solve_rows_core(const Model &m, int bh, int rx, const StepCoef *coef, const float *u0, size_t ns,
@@ -693,15 +698,9 @@ mfmc_status run_solve_rows_core(const Model &m, int bh, int rx, const StepCoef *
     RowsGeom g;
     rows_geom(m, &g);
     if (bh != 0 && bh < 8) return fail(MFMC_EINVAL, "band height %d < 8", bh);
-    const int n = m.d.n, G = (m.R + 3) & ~3, P = g.P;
-    {
-        const size_t total = ns * (size_t)P * (P / 4);
-        const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 32);
-        const int collar = m.d.bc == MFMC_BC_COLLAR;
-        pad_fields_kernel<<<blocks, 256, 0, st>>>(u0, b.padB, n, G, ns, collar, (float)m.d.bc_value);
-        if (collar) pad_fields_kernel<<<blocks, 256, 0, st>>>(u0, b.padA, n, G, ns, collar, (float)m.d.bc_value);
-        MFMC_LAUNCHED("nlch_solver launch 6");
-    }
+    const int n = m.d.n;
+    // B holds the fields after an even number of steps: step 0 is the initial field
+    MFMC_CUDA(cudaMemcpyAsync(b.padB, u0, ns * (size_t)n * n * sizeof(float), cudaMemcpyDeviceToDevice, st));
     int dev = 0, sms = 0;
     MFMC_CUDA(cudaGetDevice(&dev));
     MFMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -713,45 +712,48 @@ mfmc_status run_solve_rows_core(const Model &m, int bh, int rx, const StepCoef *
     const long long ctas = bh > 0 ? (rows + bh - 1) / bh : rows / (4 * m.R + 8) + 1;
     const int grid =
         (int)std::max<long long>(1, std::min<long long>((long long)sms * L->blocks_per_sm(threads, g.smem), ctas));
-    const CUtensorMap *src = &b.mapB;
+    bool fromB = true;
     float *dstbuf = b.padA;
     for (int k = 1; k <= nsteps; ++k) {
         const bool last = k == nsteps;
         RowsArgs a;
-        // the last step stores to the caller's field when asked, else to the scratch buffer,
-        // from which rows_ooi_kernel reduces the OoI
-        a.t.dst = (last && !steps_ps && uT) ? nullptr : dstbuf;
-        a.t.dst_plain = (last && !steps_ps) ? uT : nullptr;
+        // the last step stores to the caller's field when asked, else to the scratch field, from
+        // which rows_ooi_kernel reduces the OoI
+        a.t.dst = (last && !steps_ps && uT) ? uT : dstbuf;
+        a.t.dst_plain = nullptr;
         a.t.coef = coef;
         a.t.partials = b.partials;
         a.t.status = b.status;
         a.t.steps_ps = steps_ps;
         a.t.step = k;
         a.t.n = n;
-        a.t.P = P;
+        a.t.P = n;
         a.t.tiles_x = g.strips;
         a.t.tiles = g.strips * n;
         a.t.total = 0;
         a.t.last = 0;
-        a.t.periodic = m.d.bc == MFMC_BC_PERIODIC;
+        a.t.periodic = 1;
         a.t.wsq = nullptr;
         a.ns = (int)ns;
         a.gs = g.gs;
         a.strips = g.strips;
         a.rows = rows;
         a.band = bh;
+        a.halo = 2 * m.R;
         a.stage_floats = g.stage_floats;
+        a.pitch = g.gs * n;
         a.ng = 1;  // one lockstep group per CTA (measured faster than two or four)
-        mfmc_status s = L->fn(*src, a, grid, threads, g.smem, st);
+        // steps after the first follow a step: programmatic dependents of it
+        mfmc_status s = L->fn(fromB ? b.mapB : b.mapA, fromB ? b.mapB1 : b.mapA1, a, grid, threads, g.smem, k > 1, st);
         if (s != MFMC_OK) return s;
-        src = (dstbuf == b.padA) ? &b.mapA : &b.mapB;
+        fromB = !fromB;
         dstbuf = (dstbuf == b.padA) ? b.padB : b.padA;
     }
     {
         const long long warps = std::min<long long>((long long)ns * g.strips * n, (long long)sms * 64);
         const unsigned blocks = (unsigned)std::max<long long>(1, (warps + 7) / 8);
         rows_ooi_kernel<<<blocks, 256, 0, st>>>((uT && !steps_ps) ? uT : nullptr, b.padA, b.padB, steps_ps, nsteps,
-                                                n, P, G, g.strips, ns, b.partials);
+                                                n, g.strips, ns, b.partials);
         MFMC_LAUNCHED("nlch_solver launch 7a");
     }
     finalize_ooi_kernel<<<(unsigned)((ns + 127) / 128), 128, 0, st>>>(b.partials, g.strips * n, ns,
@@ -766,7 +768,8 @@ mfmc_status run_solve_rows(Model &m, int bh, int rx, const StepCoef *coef, const
     RowsGeom g;
     if (!L || !rows_geom(m, &g)) return fail(MFMC_EINVAL, "no row-streaming kernel for n = %d, R = %d", m.d.n, m.R);
     if (bh != 0 && bh < 8) return fail(MFMC_EINVAL, "band height %d < 8", bh);
-    // the padded buffers of the model, with tensor maps of the row view
+    // the model's scratch buffers (sized for ghost-framed fields; used here as plain fields),
+    // with tensor maps of the row view
     mfmc_status s = ensure_pad_scratch(m, ns, 0, 0);
     if (s == MFMC_OK) s = grow_buffer(&m.partials, &m.partials_cap, ns * (size_t)rows_partials_per_sample(m));
     if (s != MFMC_OK) return s;
@@ -776,8 +779,7 @@ mfmc_status run_solve_rows(Model &m, int bh, int rx, const StepCoef *coef, const
     b.cap = m.pad_cap;
     b.partials = m.partials;
     b.status = m.d_status;
-    s = encode_rows_map(&b.mapA, b.padA, g, b.cap, L->ch);
-    if (s == MFMC_OK) s = encode_rows_map(&b.mapB, b.padB, g, b.cap, L->ch);
+    s = encode_rows_maps(&b, m, g, L->ch);
     if (s != MFMC_OK) return s;
     return run_solve_rows_core(m, bh, rx, coef, u0, ns, nsteps, nullptr, uT, ubar, ooi, b, st);
 }

@@ -1,25 +1,35 @@
-// Row-streaming step kernel (constant kernel, R <= 8, n % 128 == 0, n <= 2048).
+// Row-streaming step kernel (constant kernel, periodic lattice, R <= 8, n % 128 == 0, n <= 2048).
 //
 // A CTA of 16 warps (fewer when 16 is no multiple of n / 128) streams whole rows of GS
 // consecutive samples down a range of rows: warp w takes the 128-column strip w % (n / 128) of
 // sample w / (n / 128) of its group, lane l the strip's columns 4l .. 4l+3.  The batch's rows,
-// ordered by (sample group, row), are split evenly over the CTAs (or into fixed bands taken in
-// turn); a CTA's range is cut into segments at group boundaries, and each segment's rows are
-// walked downwards together with an R-row halo above and below (always downwards: each output's
-// disc rows are then summed top to bottom whatever the split, so results do not depend on it).
-// The rows arrive through a ring of shared-memory
-// chunks: one TMA box per chunk carries CH whole ghost-framed rows (P = n + 2 R4 floats, read
-// through a four-dimensional view that splits a row into k pieces of at most 256 floats) of
-// all GS samples, so every byte of a field is fetched once; the copy of the next chunk is
-// issued when a chunk is entered.  All warps run the same instructions on the same rows.
+// ordered by (sample group, row), are split over the CTAs so that every CTA walks about as many
+// rows, its halo rows included (or into fixed bands taken in turn); a CTA's range is cut into
+// segments at group boundaries, and each segment's rows are walked downwards together with an
+// R-row halo above and below (always downwards: each output's disc rows are then summed top to
+// bottom whatever the split, so results do not depend on it).
+//
+// The fields are plain [sample][n][n] arrays: no ghost frame.  The rows arrive through a ring
+// of shared-memory chunks, one TMA box per chunk carrying CH whole rows of all GS samples
+// (stored [row][sample][n]; a four-dimensional view splits a row into k pieces of at most 256
+// floats), so every byte of a field is fetched once.  The periodic images are taken on the fly:
+// a chunk's lattice rows wrap modulo n in the copy's row coordinate (a chunk that straddles row
+// 0 or row n is fetched row by row through a second view), and the lanes whose window crosses
+// column 0 or column n read those float4s n columns away in the same staged row.  The copy of
+// the next chunk is issued when a chunk is entered.  All warps run the same instructions on
+// the same rows.
 //
 // From each staged row a lane forms its window's centre sums and one segment sum per distinct
 // disc-row half-width, and adds each to the 2R + 1 output rows that the row touches; the
 // accumulators (packed FP32 pairs) form a ring of 2R + 1 slots, so every staged row is summed
 // once per segment.  After staged row q the output row q - 2R is complete and is finished at
-// once (update, projection, store with ghost images).  The row loop is unrolled by the ring
-// period 2R + 1, which keeps every slot index static.  The OoI is reduced afterwards from the
-// final fields (rows_ooi_kernel), so it does not depend on how the rows were split.
+// once (update, projection, store).  The row loop is unrolled by the ring period 2R + 1, which
+// keeps every slot index static.  The OoI is reduced afterwards from the final fields
+// (rows_ooi_kernel), so it does not depend on how the rows were split.
+//
+// Consecutive steps are launched as programmatic dependents: a step's CTAs set up their
+// barriers and walk while the previous step drains, and wait for its completion
+// (griddepcontrol.wait) before the first copy.
 #pragma once
 
 #include <cuda.h>
@@ -33,13 +43,15 @@
 namespace mfmc {
 
 struct RowsArgs {
-    TmaArgs t;             // outputs, coefficients, status, step counts, step, n, P, periodic
+    TmaArgs t;             // destination (t.dst, plain fields), coefficients, status, step counts, step, n
     int ns;                // samples
     int gs;                // samples per CTA
     int strips;            // n / 128: warps per sample
     long long rows;        // groups * n: the batch's rows in (group, row) order
-    int band;              // rows per work range; 0: rows / groups, one range per group
-    int stage_floats;      // gs * CH * P
+    int band;              // rows per work range; 0: an even split of rows and halos over the CTAs
+    int halo;              // 2R: the rows a segment reads beyond its outputs
+    int stage_floats;      // CH * gs * n
+    int pitch;             // gs * n: floats from one staged row of a sample to its next
     int ng;                // independent warp groups per CTA (each gs samples)
 };
 
@@ -92,14 +104,24 @@ struct RowsSegIter {
     long long q, qend;     // the part of the current range still to walk
     long long range;       // index of the current range
     long long nct;
+    // Without bands the split is even in a walk-cost space where each group counts n + 2R
+    // rows: its 2R halo rows of the group's first segment, then its n rows.  A range that
+    // starts a new segment inside the group (at a cut or a group boundary) therefore walks 2R
+    // rows more than it outputs and every range walks at most its share + 2R rows.
+    __device__ static long long walk_to_row(const RowsArgs &a, long long v) {
+        const long long V = a.t.n + a.halo, g = v / V, o = v - g * V - a.halo;
+        return g * a.t.n + (o > 0 ? o : 0);
+    }
     __device__ void set_range(const RowsArgs &a) {
         if (a.band > 0) {
             q = range * a.band;
             qend = q + a.band < a.rows ? q + a.band : a.rows;
         } else {
-            const long long base = a.rows / nct, rem = a.rows % nct;
-            q = base * range + (range < rem ? range : rem);
-            qend = q + base + (range < rem ? 1 : 0);
+            const long long total = a.rows / a.t.n * (a.t.n + a.halo);
+            const long long base = total / nct, rem = total % nct;
+            const long long vb = base * range + (range < rem ? range : rem);
+            q = walk_to_row(a, vb);
+            qend = walk_to_row(a, vb + base + (range < rem ? 1 : 0));
         }
         if (q > a.rows) q = qend = a.rows;
     }
@@ -147,9 +169,11 @@ struct RowsShared {
     int pg;                // chunks issued
 };
 
+// Issues the copy of the next chunk of the walk (thread 0).  map: boxes of CH rows; map1: boxes
+// of one row, for the chunks that straddle row 0 or row n.
 template <int R>
-__device__ __noinline__ void rows_issue(const RowsArgs &a, RowsShared &sh, const CUtensorMap *map, float *ring,
-                                        uint64_t *bar) {
+__device__ __noinline__ void rows_issue(const RowsArgs &a, RowsShared &sh, const CUtensorMap *map,
+                                        const CUtensorMap *map1, float *ring, uint64_t *bar) {
     using C = RowsCfg<R>;
     if (sh.pc >= sh.pnch) {
         sh.pslot ^= 1;
@@ -158,54 +182,68 @@ __device__ __noinline__ void rows_issue(const RowsArgs &a, RowsShared &sh, const
         if (sh.pnch == 0) return;
     }
     const RowsSegInfo &s = sh.seg[sh.pslot];
-    const int st = sh.pg % C::NSTG;
-    // lattice rows of chunk c: y0 - R + c CH + [0, CH); padded row = G + lattice row (G = R4)
+    const int st = sh.pg % C::NSTG, n = a.t.n;
+    // lattice rows of chunk c: y0 - R + c CH + [0, CH), taken modulo n (-R <= y < n + R + CH)
     const int ylo = s.y0 - R + sh.pc * C::CH;
+    float *dst = ring + (size_t)st * a.stage_floats;
     mbar_expect_tx(&bar[st], (uint32_t)a.stage_floats * sizeof(float));
-    tma_load_4d(ring + (size_t)st * a.stage_floats, map, &bar[st], 0, 0, C::R4 + ylo, a.gs * s.group);
+    if ((ylo < 0 && ylo + C::CH > 0) || (ylo < n && ylo + C::CH > n)) {
+        for (int r = 0; r < C::CH; ++r) {  // the chunk straddles a periodic seam: row by row
+            const int y = ylo + r;
+            tma_load_4d(dst + (size_t)r * a.pitch, map1, &bar[st], 0, 0, a.gs * s.group, y < 0 ? y + n : (y >= n ? y - n : y));
+        }
+    } else {
+        tma_load_4d(dst, map, &bar[st], 0, 0, a.gs * s.group, ylo < 0 ? ylo + n : (ylo >= n ? ylo - n : ylo));
+    }
     ++sh.pc;
     ++sh.pg;
 }
 
 // Per-segment state of a warp.
+template <int R>
 struct RowsSeg {
-    const float *win0;   // the lane's window start in its sample's first row of stage 0
+    static constexpr int NQ = RowWin<R>::WIN / 4, QC = RowWin<R>::R4 / 4;
+    const float *win0;   // the lane's window start (column x - R4, unwrapped) in its sample's first row of stage 0
+    int wd[NQ];          // per float4 of the window: 0, or +-n where it crosses column 0 or n (never at QC)
     int bid, bthreads;   // the warp group's named barrier and its threads
     bool leader;         // the group's first thread: issues the copies and walks the segments
     int g0;              // stream index of the segment's first chunk
     int nrows;           // rows walked: len + 2R
-    int sample;
-    // outputs: the next output row's four values go to out (advanced by ostride per row), its
-    // ghost column image to out + gdelta, and for lattice rows yr < G or yr >= n - G also to
-    // the ghost row image (out +- n P); flags say which of these exist
-    float *out;
-    long long gdelta;
-    int ostride, yr;
+    float *out;          // the next output row's four values (rows advance by n)
     unsigned flags;
     float2 nc0, c1, c2;  // step coefficients (-c0, c1, c2) in both halves of a pair
 };
 
-enum : unsigned { kRowsActive = 1u, kRowsGhostCol = 2u, kRowsGhostRows = 4u };
+enum : unsigned { kRowsActive = 1u };
+
+// The window of a lane in a staged row: WIN values from rowp, the float4s that cross a periodic
+// seam taken n columns away in the same row, then the centre sums.
+template <int R>
+__device__ __forceinline__ void rows_window(const float *rowp, const RowsSeg<R> &sg, RowWin<R> &w) {
+    using S = RowsSeg<R>;
+#pragma unroll
+    for (int q = 0; q < S::NQ; ++q) {
+        const float4 x = *reinterpret_cast<const float4 *>(rowp + 4 * q + (q == S::QC ? 0 : sg.wd[q]));
+        w.v[4 * q + 0] = x.x;
+        w.v[4 * q + 1] = x.y;
+        w.v[4 * q + 2] = x.z;
+        w.v[4 * q + 3] = x.w;
+    }
+    row_prefix<R>(w);
+}
 
 // The update and projection of one output row of a lane (four columns) from its disc sums
-// (s01, s23) and centre values uc, and its stores (Eq. nonl_CH_nm with beta2 = 0 and the
+// (s01, s23) and centre values uc, and its store (Eq. nonl_CH_nm with beta2 = 0 and the
 // projection of Eq. potential_obstacle): sd = fma(-c0, u, S), v = u + fma(c1, sd, c2 u),
 // u_new = min(1, max(-1, v)), each packed FP32 pair rounding exactly like the scalar operations.
 template <int R>
-__device__ __forceinline__ void rows_emit(RowsSeg &sg, unsigned fl, float4 uc, float2 s01, float2 s23, int n, int P) {
-    constexpr int G = (R + 3) & ~3;
+__device__ __forceinline__ void rows_emit(const RowsSeg<R> &sg, float4 uc, float2 s01, float2 s23) {
     const float2 u01 = make_float2(uc.x, uc.y), u23 = make_float2(uc.z, uc.w);
     const float2 v01 = __fadd2_rn(u01, __ffma2_rn(sg.c1, __ffma2_rn(sg.nc0, u01, s01), __fmul2_rn(sg.c2, u01)));
     const float2 v23 = __fadd2_rn(u23, __ffma2_rn(sg.c1, __ffma2_rn(sg.nc0, u23, s23), __fmul2_rn(sg.c2, u23)));
-    const float4 val = make_float4(fminf(1.f, fmaxf(-1.f, v01.x)), fminf(1.f, fmaxf(-1.f, v01.y)),
-                                   fminf(1.f, fmaxf(-1.f, v23.x)), fminf(1.f, fmaxf(-1.f, v23.y)));
-    *reinterpret_cast<float4 *>(sg.out) = val;
-    if (fl & kRowsGhostCol) *reinterpret_cast<float4 *>(sg.out + sg.gdelta) = val;
-    if ((fl & kRowsGhostRows) && (unsigned)(sg.yr - G) >= (unsigned)(n - 2 * G)) {
-        const long long off = (long long)(sg.yr < G ? n : -n) * P;  // the row's periodic image
-        *reinterpret_cast<float4 *>(sg.out + off) = val;
-        if (fl & kRowsGhostCol) *reinterpret_cast<float4 *>(sg.out + off + sg.gdelta) = val;
-    }
+    *reinterpret_cast<float4 *>(sg.out) =
+        make_float4(fminf(1.f, fmaxf(-1.f, v01.x)), fminf(1.f, fmaxf(-1.f, v01.y)), fminf(1.f, fmaxf(-1.f, v23.x)),
+                    fminf(1.f, fmaxf(-1.f, v23.y)));
 }
 
 template <int R>
@@ -255,12 +293,13 @@ __device__ __forceinline__ void rows_classes(RowsAcc<R> &t, const RowWin<R> &win
 // Staged row q = q0 + K of the segment (q0 a multiple of S, K static: the ring position).
 // Returns false when a chunk wait ran out of its bound.
 template <int R, int K>
-__device__ __forceinline__ bool rows_row(RowsAcc<R> &t, const RowsArgs &a, RowsSeg &sg, int q0, RowsShared &sh,
-                                         const CUtensorMap *map, float *ring, uint64_t *bar) {
+__device__ __forceinline__ bool rows_row(RowsAcc<R> &t, const RowsArgs &a, RowsSeg<R> &sg, int q0, RowsShared &sh,
+                                         const CUtensorMap *map, const CUtensorMap *map1, float *ring,
+                                         uint64_t *bar) {
     using C = RowsCfg<R>;
     const int q = q0 + K;
-    t.rp += a.t.P;
-    t.cp += a.t.P;
+    t.rp += a.pitch;
+    t.cp += a.pitch;
     if (q % C::CH == 0) {
         const int g = sg.g0 + q / C::CH;
         const int st = g % C::NSTG;
@@ -274,7 +313,7 @@ __device__ __forceinline__ bool rows_row(RowsAcc<R> &t, const RowsArgs &a, RowsS
             }
         // every thread of the group is past the rows of the stage that the next copy overwrites
         if (!group_sync_and(sg.bid, sg.bthreads, ok)) return false;
-        if (sg.leader) rows_issue<R>(a, sh, map, ring, bar);
+        if (sg.leader) rows_issue<R>(a, sh, map, map1, ring, bar);
     }
     // the centre row q - R enters a new chunk: the stage after the previous centre chunk's
     if ((R % C::CH == 0 ? q % C::CH == 0 : (q - R) % C::CH == 0) && q >= R) {
@@ -282,31 +321,29 @@ __device__ __forceinline__ bool rows_row(RowsAcc<R> &t, const RowsArgs &a, RowsS
         t.cp = sg.win0 + t.cst * a.stage_floats + C::R4;
     }
     RowWin<R> win;
-    row_window<R>(t.rp, win);
+    rows_window<R>(t.rp, sg, win);
     rows_classes<R, K>(t, win, std::make_integer_sequence<int, RowsPlan<R>::cls.count>{});
     if (q >= 2 * R) {  // output row q - 2R is complete
-        const unsigned fl = opaque_u32(sg.flags);
-        if (fl & kRowsActive) {
+        if (opaque_u32(sg.flags) & kRowsActive) {
             constexpr int slot = rows_mod(K - 2 * R, C::S);
             const float4 uc = *reinterpret_cast<const float4 *>(t.cp);  // its centre row, q - R
-            rows_emit<R>(sg, fl, uc, t.acc[slot][0], t.acc[slot][1], a.t.n, a.t.P);
+            rows_emit<R>(sg, uc, t.acc[slot][0], t.acc[slot][1]);
         }
-        sg.out += sg.ostride;
-        ++sg.yr;
+        sg.out += a.t.n;
     }
     return true;
 }
 
 template <int R, int... Ks>
-__device__ __forceinline__ bool rows_block(RowsAcc<R> &t, const RowsArgs &a, RowsSeg &sg, int q0,
-                                           RowsShared &sh, const CUtensorMap *map, float *ring, uint64_t *bar,
-                                           int *gfail, std::integer_sequence<int, Ks...>) {
+__device__ __forceinline__ bool rows_block(RowsAcc<R> &t, const RowsArgs &a, RowsSeg<R> &sg, int q0,
+                                           RowsShared &sh, const CUtensorMap *map, const CUtensorMap *map1,
+                                           float *ring, uint64_t *bar, int *gfail, std::integer_sequence<int, Ks...>) {
     using C = RowsCfg<R>;
     bool ok = true;
     auto one = [&](auto kc) {
         constexpr int K = decltype(kc)::value;
         if (ok && q0 + K < sg.nrows) {
-            ok = rows_row<R, K>(t, a, sg, q0, sh, map, ring, bar);
+            ok = rows_row<R, K>(t, a, sg, q0, sh, map, map1, ring, bar);
             if (!ok) *gfail = sg.g0 + (q0 + K) / C::CH;
         }
     };
@@ -315,12 +352,14 @@ __device__ __forceinline__ bool rows_block(RowsAcc<R> &t, const RowsArgs &a, Row
 }
 
 template <int R>
-__global__ void __launch_bounds__(RowsCfg<R>::MAXW * 32, 1) step_rows_kernel(const __grid_constant__ CUtensorMap map,
-                                                                           RowsArgs a) {
+__global__ void __launch_bounds__(RowsCfg<R>::MAXW * 32, 1)
+    step_rows_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap map1, RowsArgs a) {
     using C = RowsCfg<R>;
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bars[C::MAXG][C::NSTG];
     __shared__ RowsShared shs[C::MAXG];
+    // the next step may be scheduled now; its CTAs take SMs as this step's CTAs leave them
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // warp groups: a.gs samples x a.strips strips each, independent rings and barriers
     const int gw = a.gs * a.strips, gid = warp / gw, wig = warp - gid * gw;
@@ -339,15 +378,24 @@ __global__ void __launch_bounds__(RowsCfg<R>::MAXW * 32, 1) step_rows_kernel(con
         sh.pslot = 1;  // the first issue advances to slot 0
         sh.pc = sh.pnch = 0;
         sh.pg = 0;
-        rows_issue<R>(a, sh, &map, ring, bar);
     }
+    // the previous step (the producer of the rows read here and the reader of the rows written
+    // here) has completed and its stores are visible
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (leader) rows_issue<R>(a, sh, &map, &map1, ring, bar);
     __syncthreads();
     RowsAcc<R> t;
 #pragma unroll
     for (int k = 0; k < C::S; ++k) t.acc[k][0] = t.acc[k][1] = make_float2(0.f, 0.f);
 
-    RowsSeg sg;
-    sg.win0 = ring + sl * C::CH * a.t.P + 128 * strip + 4 * lane;
+    const int n = a.t.n, x = 128 * strip + 4 * lane;
+    RowsSeg<R> sg;
+    sg.win0 = ring + sl * n + x - C::R4;
+#pragma unroll
+    for (int q = 0; q < RowsSeg<R>::NQ; ++q) {
+        const int c = x / 4 - RowsSeg<R>::QC + q;  // float4 column of the window's q-th float4
+        sg.wd[q] = c < 0 ? n : (c >= n / 4 ? -n : 0);
+    }
     sg.bid = 1 + gid;
     sg.bthreads = 32 * gw;
     sg.leader = leader;
@@ -362,38 +410,20 @@ __global__ void __launch_bounds__(RowsCfg<R>::MAXW * 32, 1) step_rows_kernel(con
         // one stage before the segment's first chunk
         t.cst = (sg.g0 + C::NSTG - 1) % C::NSTG;
         t.rp = t.cp = sg.win0;
-        sg.sample = a.gs * s.group + sl;
         {
-            const int n = a.t.n, P = a.t.P, x = 128 * strip + 4 * lane;
-            const bool active =
-                sg.sample < a.ns && (a.t.steps_ps == nullptr || a.t.step <= a.t.steps_ps[sg.sample]);
-            const int smp = active ? sg.sample : 0;
+            const int sample = a.gs * s.group + sl;
+            const bool active = sample < a.ns && (a.t.steps_ps == nullptr || a.t.step <= a.t.steps_ps[sample]);
+            const int smp = active ? sample : 0;
             const StepCoef cf = a.t.coef[smp];
             sg.nc0 = make_float2(-cf.c0, -cf.c0);
             sg.c1 = make_float2(cf.c1, cf.c1);
             sg.c2 = make_float2(cf.c2, cf.c2);
-            sg.yr = s.y0;
             sg.flags = active ? kRowsActive : 0u;
-            sg.gdelta = 0;
-            if (a.t.dst_plain) {  // the caller's unpadded field (last step): no ghost images
-                sg.out = a.t.dst_plain + (size_t)smp * n * n + (size_t)s.y0 * n + x;
-                sg.ostride = n;
-            } else {
-                sg.out = a.t.dst + (size_t)smp * P * P + (size_t)(C::R4 + s.y0) * P + C::R4 + x;
-                sg.ostride = P;
-                if (a.t.periodic) {
-                    // the lane's columns have a periodic image in the frame, n columns to the right
-                    // when x < G and n columns to the left when x >= n - G
-                    if (x < C::R4 || x >= n - C::R4) {
-                        sg.flags |= kRowsGhostCol;
-                        sg.gdelta = x < C::R4 ? n : -n;
-                    }
-                    sg.flags |= kRowsGhostRows;
-                }
-            }
+            sg.out = a.t.dst + (size_t)smp * n * n + (size_t)s.y0 * n + x;
         }
         for (int q0 = 0; ok && q0 < sg.nrows; q0 += C::S)
-            ok = rows_block<R>(t, a, sg, q0, sh, &map, ring, bar, &gfail, std::make_integer_sequence<int, C::S>{});
+            ok = rows_block<R>(t, a, sg, q0, sh, &map, &map1, ring, bar, &gfail,
+                               std::make_integer_sequence<int, C::S>{});
         sg.g0 += (sg.nrows + C::CH - 1) / C::CH;
         group_sync(sg.bid, sg.bthreads);  // every thread of the group has read slot k & 1
         if (ok && leader) sh.seg[k & 1] = sh.it.next(a);
@@ -413,31 +443,43 @@ __global__ void __launch_bounds__(RowsCfg<R>::MAXW * 32, 1) step_rows_kernel(con
 }
 
 // FP64 sum of every (sample, strip, row) of the final fields into partials[ns][strips][n] (lane
-// sums of four values, then a fixed shuffle tree), read from the unpadded fields `plain` when
-// given, else from the ghost-framed buffer that holds each sample's last step: A after an odd
-// number of steps, B after an even one (steps_ps: per-sample step counts, or nsteps for all).
-__global__ void rows_ooi_kernel(const float *plain, const float *padA, const float *padB, const int *steps_ps,
-                                int nsteps, int n, int P, int G, int strips, size_t ns, double *partials);
+// sums of four values, then a fixed shuffle tree), read from the fields `plain` when given, else
+// from the scratch field that holds each sample's last step: A after an odd number of steps, B
+// after an even one (steps_ps: per-sample step counts, or nsteps for all).
+__global__ void rows_ooi_kernel(const float *plain, const float *fieldA, const float *fieldB, const int *steps_ps,
+                                int nsteps, int n, int strips, size_t ns, double *partials);
 
 // Geometry of the row-streaming kernel for a lattice: samples per CTA, warps, the split of a
-// padded row into k pieces for the tensor map, and the dynamic shared memory.
+// row into k pieces for the tensor map, and the dynamic shared memory.
 struct RowsGeom {
-    int strips, gs, warps, k, P, stage_floats;
+    int strips, gs, warps, k, stage_floats;
     size_t smem;
 };
 
 struct RowsLauncher {
     int ch, nstg;
-    mfmc_status (*fn)(const CUtensorMap &, const RowsArgs &, int grid, int threads, size_t smem, cudaStream_t);
+    // pdl: launch as a programmatic dependent of the previous kernel in the stream (a step)
+    mfmc_status (*fn)(const CUtensorMap &map, const CUtensorMap &map1, const RowsArgs &, int grid, int threads,
+                      size_t smem, bool pdl, cudaStream_t);
     int (*blocks_per_sm)(int threads, size_t smem);
 };
 
 template <int R>
-mfmc_status launch_rows(const CUtensorMap &map, const RowsArgs &a, int grid, int threads, size_t smem,
-                        cudaStream_t st) {
+mfmc_status launch_rows(const CUtensorMap &map, const CUtensorMap &map1, const RowsArgs &a, int grid, int threads,
+                        size_t smem, bool pdl, cudaStream_t st) {
     auto kern = step_rows_kernel<R>;
     MFMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, threads, smem, st>>>(map, a);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    MFMC_CUDA(cudaLaunchKernelEx(&cfg, kern, map, map1, a));
     MFMC_LAUNCHED("rows_step launch");
     return MFMC_OK;
 }

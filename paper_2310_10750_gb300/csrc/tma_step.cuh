@@ -212,6 +212,21 @@ struct RowWin {
     float p[NP];
 };
 
+// The centre sums p of a window whose values v are loaded.
+template <int R>
+__device__ __forceinline__ void row_prefix(RowWin<R> &w) {
+    using W = RowWin<R>;
+    constexpr int M = W::M, o = W::R4 - R;
+    w.p[M] = 0.f;
+    w.p[M + 1] = w.v[o + M];
+    w.p[M - 1] = w.v[o + M - 1];
+#pragma unroll
+    for (int q = 1; q < M; ++q) {
+        w.p[M + 1 + q] = w.p[M + q] + w.v[o + M + q];
+        w.p[M - 1 - q] = w.p[M - q] + w.v[o + M - 1 - q];
+    }
+}
+
 template <int R>
 __device__ __forceinline__ void row_window(const float *rowp, RowWin<R> &w) {
     using W = RowWin<R>;
@@ -224,15 +239,7 @@ __device__ __forceinline__ void row_window(const float *rowp, RowWin<R> &w) {
         w.v[4 * q + 2] = x.z;
         w.v[4 * q + 3] = x.w;
     }
-    constexpr int M = W::M, o = W::R4 - R;
-    w.p[M] = 0.f;
-    w.p[M + 1] = w.v[o + M];
-    w.p[M - 1] = w.v[o + M - 1];
-#pragma unroll
-    for (int q = 1; q < M; ++q) {
-        w.p[M + 1 + q] = w.p[M + q] + w.v[o + M + q];
-        w.p[M - 1 - q] = w.p[M - q] + w.v[o + M - 1 - q];
-    }
+    row_prefix<R>(w);
 }
 
 // The four row-segment sums of half-width HW centred on the thread's output columns i = 0..3:

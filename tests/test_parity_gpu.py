@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerances (derived from the arithmetic; see the design notes):
+Tolerances, each derived from the FP32 arithmetic of the step:
   * initial fields: both sides build them in FP64 and round to FP32; the only
     difference is the last FP64 bit of log/cos/exp, so values agree to 1 FP32 ulp.
   * one step: u_new = u + c1 (S - c0 u) + c2 u in FP32.  The final add rounds to
@@ -303,8 +303,9 @@ def test_row_streaming_kernel(gpu_lib, n, R, bh):
 
 @pytest.mark.parametrize("n,R", [(256, 8), (128, 4), (384, 6)])
 def test_row_streaming_noise_ic_multistep(gpu_lib, n, R):
-    # smoothed-noise fields are nonzero at every edge, so every ghost image (rows and columns,
-    # both sides) is exercised: 6 steps element by element against the oracle
+    # smoothed-noise fields are nonzero at every edge, so every periodic seam (row 0 and row n,
+    # column 0 and column n, whether a chunk straddles it or not) is exercised: 6 steps element
+    # by element against the oracle
     mf = gpu_lib
     g, o = pair(mf, n, R, 6, ic=1, eps=0.02, algo="rows")
     seeds = seeds_of(5, base=7 * n)
