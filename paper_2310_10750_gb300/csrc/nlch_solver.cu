@@ -706,6 +706,8 @@ mfmc_status run_solve_rows_core(const Model &m, int bh, int rx, const StepCoef *
     MFMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const long long rows = (long long)((ns + g.gs - 1) / g.gs) * n;  // (sample group, row) order
     if (rows == 0) return MFMC_OK;
+    if (rows / n * (n + 2LL * m.R) >= (1LL << 31) || (bh > 0 && rows + bh >= (1LL << 31)))
+        return fail(MFMC_EINVAL, "batch of %zu samples too large for the row-streaming kernel", ns);
     // one range per CTA (at least 4R + 8 rows each, so the halo rows stay a minor share), or
     // bands taken in turn by the resident CTAs
     const int threads = 32 * g.warps;

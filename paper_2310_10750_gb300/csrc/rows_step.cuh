@@ -81,10 +81,6 @@ __device__ __forceinline__ bool group_sync_and(int id, int nthreads, bool ok) {
     return r != 0;
 }
 
-__device__ __forceinline__ void group_sync(int id, int nthreads) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
 __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1, int c2,
                                             int c3) {
     asm volatile(
@@ -99,33 +95,35 @@ struct RowsSegInfo {
     int group, y0, len;
 };
 
-// The CTA's walk over its row ranges (thread 0 only; results go through shared memory).
+// The CTA's walk over its row ranges (one thread at a time; results go through shared memory).
+// 32-bit arithmetic: the host keeps every walk-cost position below 2^31.
 struct RowsSegIter {
-    long long q, qend;     // the part of the current range still to walk
-    long long range;       // index of the current range
-    long long nct;
+    int q, qend;     // the part of the current range still to walk
+    int range;       // index of the current range
+    int nct;
     // Without bands the split is even in a walk-cost space where each group counts n + 2R
     // rows: its 2R halo rows of the group's first segment, then its n rows.  A range that
     // starts a new segment inside the group (at a cut or a group boundary) therefore walks 2R
     // rows more than it outputs and every range walks at most its share + 2R rows.
-    __device__ static long long walk_to_row(const RowsArgs &a, long long v) {
-        const long long V = a.t.n + a.halo, g = v / V, o = v - g * V - a.halo;
+    __device__ static int walk_to_row(const RowsArgs &a, int v) {
+        const int V = a.t.n + a.halo, g = v / V, o = v - g * V - a.halo;
         return g * a.t.n + (o > 0 ? o : 0);
     }
     __device__ void set_range(const RowsArgs &a) {
+        const int rows = (int)a.rows;
         if (a.band > 0) {
             q = range * a.band;
-            qend = q + a.band < a.rows ? q + a.band : a.rows;
+            qend = q + a.band < rows ? q + a.band : rows;
         } else {
-            const long long total = a.rows / a.t.n * (a.t.n + a.halo);
-            const long long base = total / nct, rem = total % nct;
-            const long long vb = base * range + (range < rem ? range : rem);
+            const int total = rows / a.t.n * (a.t.n + a.halo);
+            const int base = total / nct, rem = total % nct;
+            const int vb = base * range + (range < rem ? range : rem);
             q = walk_to_row(a, vb);
             qend = walk_to_row(a, vb + base + (range < rem ? 1 : 0));
         }
-        if (q > a.rows) q = qend = a.rows;
+        if (q > rows) q = qend = rows;
     }
-    __device__ void init(const RowsArgs &a, long long id, long long count) {
+    __device__ void init(const RowsArgs &a, int id, int count) {
         nct = count;
         range = id;
         set_range(a);
@@ -137,18 +135,18 @@ struct RowsSegIter {
         for (;;) {
             if (q >= qend) {
                 range += nct;
-                if (a.band == 0 || range * a.band >= a.rows) {
+                if (a.band == 0 || (long long)range * a.band >= a.rows) {
                     s.group = s.y0 = s.len = 0;
                     return s;
                 }
                 set_range(a);
                 continue;
             }
-            const long long col = q / n;
-            const long long hi = (col + 1) * n < qend ? (col + 1) * n : qend;
-            s.group = (int)col;
-            s.y0 = (int)(q - col * n);
-            s.len = (int)(hi - q);
+            const int col = q / n;
+            const int hi = (col + 1) * n < qend ? (col + 1) * n : qend;
+            s.group = col;
+            s.y0 = q - col * n;
+            s.len = hi - q;
             q = hi;
             bool any = false;
             for (int w = 0; w < a.gs; ++w) {
@@ -160,11 +158,11 @@ struct RowsSegIter {
     }
 };
 
-// Shared state of a CTA: the walk, the producer's position and two segment slots (the
-// consumer's current segment and the next one).
+// Shared state of a CTA: the walk, the producer's position and three segment slots (segment k
+// in slot k mod 3: the consumers' current one and the next two).
 struct RowsShared {
     RowsSegIter it;
-    RowsSegInfo seg[2];
+    RowsSegInfo seg[3];
     int pslot, pc, pnch;   // producer: segment slot, next chunk in it, its chunk count
     int pg;                // chunks issued
 };
@@ -176,7 +174,7 @@ __device__ __noinline__ void rows_issue(const RowsArgs &a, RowsShared &sh, const
                                         const CUtensorMap *map1, float *ring, uint64_t *bar) {
     using C = RowsCfg<R>;
     if (sh.pc >= sh.pnch) {
-        sh.pslot ^= 1;
+        sh.pslot = sh.pslot == 2 ? 0 : sh.pslot + 1;
         sh.pnch = sh.seg[sh.pslot].len > 0 ? (sh.seg[sh.pslot].len + 2 * R + C::CH - 1) / C::CH : 0;
         sh.pc = 0;
         if (sh.pnch == 0) return;
@@ -206,7 +204,9 @@ struct RowsSeg {
     const float *win0;   // the lane's window start (column x - R4, unwrapped) in its sample's first row of stage 0
     int wd[NQ];          // per float4 of the window: 0, or +-n where it crosses column 0 or n (never at QC)
     int bid, bthreads;   // the warp group's named barrier and its threads
-    bool leader;         // the group's first thread: issues the copies and walks the segments
+    bool leader;         // the group's first thread: walks the segments
+    int tig, gw;         // the thread's index in its group, the group's warps
+    int kseg;            // index of the current segment (its slot: kseg mod 3)
     int g0;              // stream index of the segment's first chunk
     int nrows;           // rows walked: len + 2R
     float *out;          // the next output row's four values (rows advance by n)
@@ -313,7 +313,14 @@ __device__ __forceinline__ bool rows_row(RowsAcc<R> &t, const RowsArgs &a, RowsS
             }
         // every thread of the group is past the rows of the stage that the next copy overwrites
         if (!group_sync_and(sg.bid, sg.bthreads, ok)) return false;
-        if (sg.leader) rows_issue<R>(a, sh, map, map1, ring, bar);
+        // the copy is issued by lane 0 of warp g mod gw of the group: each warp carries the
+        // issue's extra work once every gw chunks, so no warp lags at every barrier
+        if (sg.tig == 32 * (g % sg.gw)) {
+            // at a segment's first chunk every warp has left the segment before it: its slot
+            // takes the segment after the next
+            if (q == 0 && sg.kseg > 0) sh.seg[(sg.kseg + 2) % 3] = sh.it.next(a);
+            rows_issue<R>(a, sh, map, map1, ring, bar);
+        }
     }
     // the centre row q - R enters a new chunk: the stage after the previous centre chunk's
     if ((R % C::CH == 0 ? q % C::CH == 0 : (q - R) % C::CH == 0) && q >= R) {
@@ -353,9 +360,10 @@ __device__ __forceinline__ bool rows_block(RowsAcc<R> &t, const RowsArgs &a, Row
 
 template <int R>
 __global__ void __launch_bounds__(RowsCfg<R>::MAXW * 32, 1)
-    step_rows_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap map1, RowsArgs a) {
+    step_rows_kernel(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap map1,
+                     const __grid_constant__ RowsArgs a) {
     using C = RowsCfg<R>;
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(128) float rows_smem[];
     __shared__ __align__(8) uint64_t bars[C::MAXG][C::NSTG];
     __shared__ RowsShared shs[C::MAXG];
     // the next step may be scheduled now; its CTAs take SMs as this step's CTAs leave them
@@ -364,18 +372,17 @@ __global__ void __launch_bounds__(RowsCfg<R>::MAXW * 32, 1)
     // warp groups: a.gs samples x a.strips strips each, independent rings and barriers
     const int gw = a.gs * a.strips, gid = warp / gw, wig = warp - gid * gw;
     const int sl = wig / a.strips, strip = wig - sl * a.strips;  // sample in the group, strip
-    float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127)) +
-                  (size_t)gid * C::NSTG * a.stage_floats;
+    // (indexing the shared array itself keeps every ring access a shared-memory load)
+    float *ring = rows_smem + gid * C::NSTG * a.stage_floats;
     uint64_t *bar = bars[gid];
     RowsShared &sh = shs[gid];
     const bool leader = (threadIdx.x - 32 * gw * gid) == 0;
     if (leader) {
         for (int i = 0; i < C::NSTG; ++i) mbar_init(&bar[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        sh.it.init(a, (long long)blockIdx.x * a.ng + gid, (long long)gridDim.x * a.ng);
-        sh.seg[0] = sh.it.next(a);
-        sh.seg[1] = sh.it.next(a);
-        sh.pslot = 1;  // the first issue advances to slot 0
+        sh.it.init(a, (int)blockIdx.x * a.ng + gid, (int)gridDim.x * a.ng);
+        for (int i = 0; i < 3; ++i) sh.seg[i] = sh.it.next(a);
+        sh.pslot = 2;  // the first issue advances to slot 0
         sh.pc = sh.pnch = 0;
         sh.pg = 0;
     }
@@ -399,12 +406,16 @@ __global__ void __launch_bounds__(RowsCfg<R>::MAXW * 32, 1)
     sg.bid = 1 + gid;
     sg.bthreads = 32 * gw;
     sg.leader = leader;
+    sg.tig = threadIdx.x - 32 * gw * gid;
+    sg.gw = gw;
     sg.g0 = 0;
     int gfail = 0;
     bool ok = true;
     for (int k = 0; ok; ++k) {
-        const RowsSegInfo s = sh.seg[k & 1];
+        // segment k's slot was filled before a barrier that every warp has passed since
+        const RowsSegInfo s = sh.seg[k % 3];
         if (s.len == 0) break;
+        sg.kseg = k;
         sg.nrows = s.len + 2 * R;
         // the centre row q - R enters chunk 0 at q = R (rows q < R have no centre in use): start
         // one stage before the segment's first chunk
@@ -425,9 +436,6 @@ __global__ void __launch_bounds__(RowsCfg<R>::MAXW * 32, 1)
             ok = rows_block<R>(t, a, sg, q0, sh, &map, &map1, ring, bar, &gfail,
                                std::make_integer_sequence<int, C::S>{});
         sg.g0 += (sg.nrows + C::CH - 1) / C::CH;
-        group_sync(sg.bid, sg.bthreads);  // every thread of the group has read slot k & 1
-        if (ok && leader) sh.seg[k & 1] = sh.it.next(a);
-        group_sync(sg.bid, sg.bthreads);
     }
     if (!ok && leader) {
         // A chunk wait ran out of its bound (only a copy that never lands can cause it): report,
