@@ -623,27 +623,60 @@ def run_large(args):
     pkg_build.build()
     from paper_2310_10750_gb300 import mfmc
     n, R, steps, ns = 1024, 32, 2000, 64
+    profiling = args.nsteps > 0  # a short solve for ncu: the main model only
+    if profiling:
+        steps = args.nsteps
+    if args.samples > 0:
+        ns = args.samples
     base = 20231016 + 1000003 * 4
     kw = dict(n=n, delta=R / n, eps=0.02, eps_lo=0.016, eps_hi=0.024, tau=1e-3, ic=mfmc.IC_SMOOTHED_GAUSS,
               ic_amp=0.05)
-    model = mfmc.Model(nsteps=steps, **kw)
+    pin = {"auto": mfmc.ALGO_AUTO, "spectral": mfmc.ALGO_SPECTRAL, "fft": mfmc.ALGO_FFT,
+           "tma": mfmc.ALGO_PREFIX_TMA}.get(args.algo, mfmc.ALGO_AUTO)
+    model = mfmc.Model(nsteps=steps, algo=pin, **kw)
     c = _batched_cost(mfmc, model, ns, base)
-    names = {1: "direct", 2: "prefix", 4: "resident", 6: "prefix-tma", 7: "row-stream", 8: "fft"}
+    names = {1: "direct", 2: "prefix", 4: "resident", 6: "prefix-tma", 7: "row-stream", 8: "fft", 11: "spectral"}
     algo = names.get(model.info().algo, str(model.info().algo))
     if algo == "prefix-tma":
         algo += f" (tile variant {model.info().tile_variant})"
-    direct_c = None
-    if not args.no_plain:
+    direct_c = fft_c = spec_c = None
+    if not args.no_plain and not profiling:
         md = mfmc.Model(nsteps=20, algo=mfmc.ALGO_DIRECT, **kw)
         direct_c = _batched_cost(mfmc, md, ns, base) * steps / 20
-    mf_ = mfmc.Model(nsteps=200, algo=mfmc.ALGO_FFT, **kw)
-    fft_c = _batched_cost(mfmc, mf_, ns, base) * steps / 200
+    if not profiling:
+        mf_ = mfmc.Model(nsteps=200, algo=mfmc.ALGO_FFT, **kw)
+        fft_c = _batched_cost(mfmc, mf_, ns, base) * steps / 200
+        ms_ = mfmc.Model(nsteps=200, algo=mfmc.ALGO_SPECTRAL, **kw)
+        spec_c = _batched_cost(mfmc, ms_, ns, base) * steps / 200
     pts = ns * n * n * steps
+    peak_gbs, sm_max, peak_kind = load_peaks()
+    per_step = c / steps  # GPU seconds per sample-step
+    if algo == "spectral":
+        # per sample-step: the column pass reads and writes the half spectrum (1024 x 513 complex
+        # FP32), the row pass reads the spectrum and the field and writes both
+        spec_b, field_b = 1024 * 513 * 8, 1024 * 1024 * 4
+        bytes_ss = 4 * spec_b + 2 * field_b
+        roof = {"bound": "hbm", "kernel": "spectral_column_kernel + spectral_row_kernel",
+                "algorithmic_bytes_per_sample_step": bytes_ss, "achieved": bytes_ss / per_step / 1e9,
+                "peak": peak_gbs, "unit": "GB/s", "frac": bytes_ss / per_step / 1e9 / peak_gbs,
+                "peak_kind": peak_kind}
+    else:
+        # the disc-sum kernels: 8 B per point-step of field traffic
+        bytes_ss = 8 * n * n
+        roof = {"bound": "hbm", "kernel": algo, "algorithmic_bytes_per_sample_step": bytes_ss,
+                "achieved": bytes_ss / per_step / 1e9, "peak": peak_gbs, "unit": "GB/s",
+                "frac": bytes_ss / per_step / 1e9 / peak_gbs, "peak_kind": peak_kind}
     line = {"metric": "grid-pt updates/s (large HF)", "value": pts / (c * ns), "unit": METRIC,
+            "roofline": roof,
+            "prefix_form_alu_model": {"instr_per_point": 4 * R + 9,
+                                      "frac_of_alu_peak": (4 * R + 9) * pts / (c * ns) / (152 * 128 * sm_max * 1e6),
+                                      "what": "the throughput in units of the register-tiled prefix form's "
+                                              "instruction count (4R + 9 per point) against 152 SMs x 128 FP32 lanes"},
             "higher_is_better": True, "data": "synthetic",
-            "config": {"workload": "1024^2, delta=32h (3209-pt disc), 2000 steps, 64 samples", "algo": algo},
+            "config": {"workload": f"1024^2, delta=32h (3209-pt disc), {steps} steps, {ns} samples", "algo": algo},
             "gpu_s_per_sample": c, "direct_sum_gpu_s_per_sample": direct_c,
-            "fft_gpu_s_per_sample": fft_c,
+            "fft_gpu_s_per_sample": fft_c, "spectral_gpu_s_per_sample": spec_c,
+            "spectral_what": "own FFT kernels: column pass + fused row pass per step (200 steps scaled)",
             "fft_what": "cuFFT R2C/C2R per step + product + fused update (library comparison point, 200 steps scaled)"}
     print(json.dumps(line), flush=True)
     return 0
@@ -796,7 +829,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--nsteps", type=int, default=0, help="profiling: time steps per solve")
     ap.add_argument("--samples", type=int, default=0, help="profiling: samples per GPU")
-    ap.add_argument("--algo", default="auto", choices=["auto", "prefix", "direct", "kahan", "tma", "rows", "fft"])
+    ap.add_argument("--algo", default="auto", choices=["auto", "prefix", "direct", "kahan", "tma", "rows", "fft", "spectral"])
     ap.add_argument("--band-height", type=int, default=-1,
                     help="profiling: pin the row-streaming work split (rows per range, 0 = even split)")
     ap.add_argument("--columns", type=int, default=4, help="profiling: row-streaming columns per thread")

@@ -97,10 +97,16 @@ typedef enum {
                                   by FP32 CG preconditioned with a multigrid V-cycle; one CTA
                                   per sample; the only algorithm for beta2 > 0 (AUTO picks
                                   it), periodic only */,
-    MFMC_ALGO_WEIGHTED = 10    /* register-tiled weighted disc sum over TMA tiles: any radial
+    MFMC_ALGO_WEIGHTED = 10,   /* register-tiled weighted disc sum over TMA tiles: any radial
                                   kernel (the Gaussian's fastest own path), integer delta/h,
                                   either boundary; |D| FMAs per point without the prefix
                                   form's shortcut, so the constant kernel prefers PREFIX_TMA */
+    MFMC_ALGO_SPECTRAL = 11    /* spectral form of the disc sum on this library's own FFT
+                                  kernels: per step a column pass (FFT over y, product with the
+                                  real transform of the disc weights, inverse) and a row pass
+                                  (inverse row FFT, update, forward row FFT of the new rows);
+                                  cost independent of the horizon; n = 1024, any kernel and
+                                  radius, periodic boundary, beta2 = 0; AUTO considers it */
 } mfmc_algo;
 
 /* One fidelity of the model (Section 2, Section 4).  The lattice is n x n on the unit

@@ -41,7 +41,7 @@ mfmc_status autotune(Model &m, cudaStream_t st) {
     // candidates: (algorithm, TMA tile variant)
     std::vector<std::pair<int, int>> cands;
     for (int a : {MFMC_ALGO_RESIDENT, MFMC_ALGO_ROWS, MFMC_ALGO_PREFIX_TMA, MFMC_ALGO_PREFIX, MFMC_ALGO_DIRECT,
-                  MFMC_ALGO_WEIGHTED}) {
+                  MFMC_ALGO_WEIGHTED, MFMC_ALGO_SPECTRAL}) {
         if (!algo_supported(m, a)) continue;
         if (a == MFMC_ALGO_PREFIX_TMA) {
             for (int v = 0; v < kTmaVariants; ++v) cands.push_back({a, v});

@@ -34,6 +34,8 @@ struct StepCoef {
 struct FftState;  // spectral-convolution state of the FFT path (fft_solver.cu)
 void fft_release(FftState *f);
 bool fft_available();
+struct SpectralState;  // the own-FFT spectral path (spectral.cu)
+void spectral_release(SpectralState *s);
 struct Fft64State;  // FP64 spectral disc sums of the beta2 > 0 solver (fft_solver.cu)
 void fft64_release(Fft64State *f);
 bool fft64_available();
@@ -95,6 +97,7 @@ struct Model {
     int graphs_off = 0;
     FftState *fft = nullptr;  // created by the first FFT-path solve
     Fft64State *fft64 = nullptr;  // created by the first spectral beta2 > 0 solve
+    SpectralState *spectral = nullptr;  // created by the first own-FFT spectral solve
     unsigned long long *d_as_iters = nullptr;  // Newton and CG iterations of the last beta2 > 0 solve
     int as_newton_max = kAsNewtonMax;           // iteration bounds of the beta2 > 0 solver
     int as_cg_max = kAsCgMax;
@@ -205,6 +208,12 @@ bool rows_supported(const Model &m, int rx);
 mfmc_status run_solve_tma(Model &m, int kahan, int variant, const StepCoef *coef, const float *u0, size_t ns,
                           int nsteps, float *uT, double *ubar, double *ooi, cudaStream_t st);
 // The spectral (cuFFT) form of the disc sum, periodic lattice, any kernel and radius.
+// The own-FFT spectral path (n = 1024, periodic, beta2 = 0).
+bool spectral_supported(const Model &m);
+mfmc_status run_solve_spectral(Model &m, const StepCoef *coef, const float *u0, size_t ns, int nsteps, float *uT,
+                               double *ubar, double *ooi, cudaStream_t st);
+// Per-sample FP64 mean (ubar) and OoI of ns fields of n x n, fixed summation order.
+mfmc_status launch_field_ooi(const float *u, size_t ns, int n, double *ubar, double *ooi, cudaStream_t st);
 mfmc_status run_solve_fft(Model &m, const StepCoef *coef, const float *u0, size_t ns, int nsteps, float *uT,
                           double *ubar, double *ooi, cudaStream_t st);
 // FP64 disc sums S = sum_z w_z u_{i+z} of ns fields by cuFFT: u and S are strided per-sample

@@ -316,11 +316,22 @@ __global__ void reduce_fields_kernel(const float *u, int n, double *ubar, double
     }
 }
 
+mfmc_status launch_field_ooi(const float *u, size_t ns, int n, double *ubar, double *ooi, cudaStream_t st) {
+    const size_t nn = (size_t)n * n;
+    for (size_t o = 0; o < ns; o += 65535) {
+        const unsigned g = (unsigned)std::min<size_t>(65535, ns - o);
+        reduce_fields_kernel<<<g, 256, 0, st>>>(u + o * nn, n, ubar ? ubar + o : nullptr, ooi ? ooi + o : nullptr);
+    }
+    MFMC_LAUNCHED("nlch_solver launch 9");
+    return MFMC_OK;
+}
+
 bool algo_supported(const Model &m, int algo) {
     const bool constant = m.d.kernel == MFMC_KERNEL_CONSTANT;
     // beta2 > 0: only the active-set solver; it serves nothing else
     if (m.d.beta2 > 0.0 || algo == MFMC_ALGO_ACTIVE_SET) return m.d.beta2 > 0.0 && algo == MFMC_ALGO_ACTIVE_SET;
     if (algo == MFMC_ALGO_FFT) return m.d.bc == MFMC_BC_PERIODIC;  // any kernel, any radius
+    if (algo == MFMC_ALGO_SPECTRAL) return spectral_supported(m);   // any kernel and radius, n = 1024
     if (algo == MFMC_ALGO_WEIGHTED)  // any radial kernel, integer delta / h, either boundary
         return m.integer_R && tma_launcher(m.R) != nullptr && tma_launcher(m.R)->v[kTmaWeighted].fn[3] != nullptr;
     // a non-integer delta / h: only the generic kernel, whose disc is set at run time
@@ -820,6 +831,7 @@ mfmc_status run_solve(Model &m, int algo, const StepCoef *coef, const float *u0,
         return MFMC_OK;
     }
     if (algo == MFMC_ALGO_FFT) return run_solve_fft(m, coef, u0, ns, nsteps, uT, ubar, ooi, st);
+    if (algo == MFMC_ALGO_SPECTRAL) return run_solve_spectral(m, coef, u0, ns, nsteps, uT, ubar, ooi, st);
     if (algo == MFMC_ALGO_WEIGHTED) return run_solve_tma(m, 0, kTmaWeighted, coef, u0, ns, nsteps, uT, ubar, ooi, st);
     if (algo == MFMC_ALGO_PREFIX_TMA)
         return run_solve_tma(m, 0, m.tma_variant, coef, u0, ns, nsteps, uT, ubar, ooi, st);

@@ -27,7 +27,7 @@ BC_PERIODIC = 0
 BC_COLLAR = 1
 IC_UNIFORM, IC_SMOOTHED_GAUSS, IC_NUCLEI = 0, 1, 2
 ALGO_AUTO, ALGO_DIRECT, ALGO_PREFIX, ALGO_PREFIX_KAHAN, ALGO_RESIDENT, ALGO_PLAIN, ALGO_PREFIX_TMA, ALGO_ROWS, ALGO_FFT, \
-    ALGO_ACTIVE_SET, ALGO_WEIGHTED = range(11)
+    ALGO_ACTIVE_SET, ALGO_WEIGHTED, ALGO_SPECTRAL = range(12)
 MAX_MODELS = 16
 
 

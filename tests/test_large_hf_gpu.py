@@ -1,6 +1,7 @@
 """The large high-fidelity configuration (1024 x 1024, delta = 32h: a 3209-point disc) against
-the FP64 oracle for a bounded number of steps: the plain FP32 disc sums (autotuned kernel),
-the FP32-compensated (Kahan) sums and the spectral form.  With |D| = 3209 FP32 adds per output
+the FP64 oracle for a bounded number of steps: the autotuned path, the plain FP32 disc sums of
+the TMA tile kernel, the FP32-compensated (Kahan) sums, and the spectral forms on cuFFT and on
+the library's own FFT kernels.  With |D| = 3209 FP32 adds per output
 this is where accumulation error would show first; the per-step bound of the other parity
 tests, 4e-6 max|u|, is the target for all three."""
 import math
@@ -22,7 +23,7 @@ def test_large_hf_fp32_kahan_and_fft_against_oracle(gpu_lib):
     seeds = np.array([20231016 + 1000003 * 4], dtype=np.uint64)
     fr, _, ur, _ = o.solve_sample(int(seeds[0]))
     tol = steps * 4e-6 * 0.05 * math.e
-    for algo in (mf.ALGO_AUTO, mf.ALGO_PREFIX_KAHAN, mf.ALGO_FFT):
+    for algo in (mf.ALGO_AUTO, mf.ALGO_PREFIX_TMA, mf.ALGO_PREFIX_KAHAN, mf.ALGO_FFT, mf.ALGO_SPECTRAL):
         g = mf.Model(algo=algo, **kw)
         u0 = torch.empty((1, n, n), dtype=torch.float32, device="cuda")
         uT = torch.empty_like(u0)
@@ -46,7 +47,8 @@ def _fixture():
 def test_large_hf_samples_0_to_3_100_steps_fp32_and_kahan(gpu_lib):
     # samples 0..3 of the large configuration, 100 steps, against the FP64 oracle's solutions
     # stored by tests/golden/make_large_hf_fixture.py (OoI, mean and u at 512 fixed points):
-    # the plain FP32 sums of the autotuned kernel and the compensated ones.  Bound on the field:
+    # the autotuned path (the own-FFT spectral form at this horizon), the plain FP32 prefix sums
+    # and the compensated ones.  Bound on the field:
     # 100 x 4e-6 x max|u| e^{c_F T} with max|u| <= 0.05 e^{0.1}.
     import torch
     mf = gpu_lib
@@ -57,7 +59,7 @@ def test_large_hf_samples_0_to_3_100_steps_fp32_and_kahan(gpu_lib):
     seeds = np.array([r[0] for r in ref], dtype=np.uint64)
     pts = np.random.default_rng(1024).integers(0, n, size=(512, 2))
     tol = steps * 4e-6 * 0.05 * math.exp(0.1) * math.exp(0.1)
-    for algo in (mf.ALGO_AUTO, mf.ALGO_PREFIX_KAHAN):
+    for algo in (mf.ALGO_AUTO, mf.ALGO_PREFIX_TMA, mf.ALGO_PREFIX_KAHAN):
         g = mf.Model(algo=algo, **kw)
         u0 = torch.empty((4, n, n), dtype=torch.float32, device="cuda")
         uT = torch.empty_like(u0)

@@ -1,0 +1,97 @@
+"""The spectral step on the library's own FFT kernels (MFMC_ALGO_SPECTRAL, n = 1024) against
+the FP64 oracle's direct disc sums.
+
+Tolerance: the transforms round in FP32.  A 1024-point transform by 32 x 32 with radix-2
+stages has 10 rounded butterfly levels and FP32 twiddles, so each transform adds about
+10 x 2^-24 relative to the RMS of its input; the disc sum S (|S| <= |D| max|u|) then carries an
+absolute error of a few FP32 ulps of |D| max|u|, which the update multiplies by c1 (below 1e-2
+here), so the per-step bound of the other kernels, 4e-6 max|u|, holds with a wide margin.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+N = 1024
+
+
+def gpu_solve(mf, g, seeds, u0=None):
+    import torch
+    ns, n = len(seeds), g.n
+    if u0 is None:
+        u0 = torch.empty((ns, n, n), dtype=torch.float32, device="cuda")
+        mf.mfmc_init_fields(g, seeds, u0)
+    uT = torch.empty_like(u0)
+    ooi = torch.empty(ns, dtype=torch.float64, device="cuda")
+    ubar = torch.empty(ns, dtype=torch.float64, device="cuda")
+    eps = torch.tensor(mf.mfmc_sample_eps(g, seeds), dtype=torch.float64, device="cuda")
+    mf.mfmc_solve_fields(g, u0, ns, eps=eps, uT=uT, ooi=ooi, ubar=ubar)
+    torch.cuda.synchronize()
+    return (u0.cpu().numpy().astype(np.float64), uT.cpu().numpy().astype(np.float64), ooi.cpu().numpy(),
+            ubar.cpu().numpy())
+
+
+@pytest.mark.parametrize("R,kernel,ic", [(32, 0, 2), (8, 0, 1), (3, 0, 2), (20, 1, 2)])
+def test_spectral_one_step_elementwise(gpu_lib, R, kernel, ic):
+    # the horizon of the large configuration (3209 points), a small one, one that is not a
+    # power of two, and the Gaussian kernel; nuclei ICs have the obstacle active, the smoothed
+    # noise IC is nonzero at every row and column
+    mf = gpu_lib
+    kw = dict(n=N, delta=R / N, eps=0.02, tau=5e-3, nsteps=1, ic=ic, ic_amp=0.05)
+    if kernel == 1:
+        kw.update(kernel=1, delta_hf=R / N)
+    g = mf.Model(algo=mf.ALGO_SPECTRAL, **kw)
+    o = O.OracleModel(**kw)
+    seeds = np.arange(2, dtype=np.uint64) + 31 * R
+    u0, uT, f, ubar = gpu_solve(mf, g, seeds)
+    for i in range(len(seeds)):
+        ref = o.step(u0[i], float(mf.mfmc_sample_eps(g, seeds)[i]))
+        assert np.abs(uT[i] - ref).max() <= 4e-6 * max(1.0, np.abs(u0[i]).max()), i
+        assert abs(ubar[i] - ref.mean()) <= 1e-5 * abs(ref.mean()) + 1e-9
+    assert np.abs(uT).max() <= 1.0
+
+
+def test_spectral_20_steps_large_configuration_against_oracle(gpu_lib):
+    # 1024^2, delta = 32h, smoothed-noise IC of amplitude 0.05, eps = 0.02 U[0.8, 1.2]: the
+    # large high-fidelity configuration, 20 steps, one sample
+    mf = gpu_lib
+    steps = 20
+    kw = dict(n=N, delta=32 / N, eps=0.02, eps_lo=0.016, eps_hi=0.024, tau=1e-3, nsteps=steps, ic=1, ic_amp=0.05)
+    g = mf.Model(algo=mf.ALGO_SPECTRAL, **kw)
+    o = O.OracleModel(**kw)
+    seeds = np.array([20231016 + 1000003 * 4], dtype=np.uint64)
+    fr, mr, ur, _ = o.solve_sample(int(seeds[0]))
+    _, uT, f, ubar = gpu_solve(mf, g, seeds)
+    assert abs(f[0] - fr) <= 1e-9 * fr
+    assert abs(ubar[0] - mr) <= 1e-5 * abs(mr) + 1e-9
+    assert np.abs(uT[0] - ur).max() <= steps * 4e-6 * 0.05 * math.e
+
+
+def test_spectral_matches_the_cufft_path_and_is_deterministic(gpu_lib):
+    # the same spectral product by cuFFT's transforms and by the own kernels: the two FP32
+    # forms agree to their rounding over 50 steps; a repeated call is bitwise identical; odd
+    # batch sizes (the last row pass and column tile are partly empty) and a batch that grows
+    mf = gpu_lib
+    kw = dict(n=N, delta=16 / N, eps=0.03, tau=5e-3, nsteps=50, ic=2)
+    gs = mf.Model(algo=mf.ALGO_SPECTRAL, **kw)
+    gf = mf.Model(algo=mf.ALGO_FFT, **kw)
+    for ns in (1, 3):
+        seeds = np.arange(ns, dtype=np.uint64) + 700
+        _, us, fs, _ = gpu_solve(mf, gs, seeds)
+        _, uf, ff, _ = gpu_solve(mf, gf, seeds)
+        _, us2, fs2, _ = gpu_solve(mf, gs, seeds)
+        assert np.array_equal(us, us2) and np.array_equal(fs, fs2)
+        assert np.abs(fs - ff).max() <= 1e-6 * ff.max()
+        assert np.abs(us - uf).max() <= 50 * 4e-6 * math.exp(0.5)
+
+
+def test_spectral_rejects_unsupported_models(gpu_lib):
+    mf = gpu_lib
+    for kw in (dict(n=512, delta=8 / 512), dict(n=N, delta=8 / N, bc=mf.BC_COLLAR, bc_value=-1.0),
+               dict(n=N, delta=8 / N, beta2=0.05)):
+        with pytest.raises(Exception):
+            mf.Model(algo=mf.ALGO_SPECTRAL, nsteps=1, **kw)
