@@ -3,7 +3,7 @@ the FP64 oracle for a bounded number of steps: the autotuned path, the plain FP3
 the TMA tile kernel, the FP32-compensated (Kahan) sums, and the spectral forms on cuFFT and on
 the library's own FFT kernels.  With |D| = 3209 FP32 adds per output
 this is where accumulation error would show first; the per-step bound of the other parity
-tests, 4e-6 max|u|, is the target for all three."""
+tests, 4e-6 max|u|, is the target for each of them."""
 import math
 
 import numpy as np
