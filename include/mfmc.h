@@ -105,8 +105,10 @@ typedef enum {
                                   kernels: per step a column pass (FFT over y, product with the
                                   real transform of the disc weights, inverse) and a row pass
                                   (inverse row FFT, update, forward row FFT of the new rows);
-                                  cost independent of the horizon; n = 1024, any kernel and
-                                  radius, periodic boundary, beta2 = 0; AUTO considers it */
+                                  n = 1024 in two launches per step, n = 64 and 128 in one
+                                  launch for the whole solve with the fields in shared memory;
+                                  cost independent of the horizon; any kernel and radius,
+                                  periodic boundary, beta2 = 0; AUTO considers it */
 } mfmc_algo;
 
 /* One fidelity of the model (Section 2, Section 4).  The lattice is n x n on the unit

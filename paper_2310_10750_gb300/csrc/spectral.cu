@@ -345,6 +345,196 @@ timeout:
     }
 }
 
+// ----------------------------------------------------------------------------- small lattices
+// n = 32 E with E = 2 or 4 (n = 64, 128: the paper's meshes h = 1/64 and 1/128): a CTA keeps its
+// samples' fields and half spectra in shared memory for every step (one sample at n = 128, four
+// at n = 64) and writes only the final fields and their OoI.  A warp transforms 32 / E
+// sequences of length n at once, E lanes each: every lane transforms its 32 values (stride E)
+// in registers, multiplies by W_n^(n1 k2), and after an exchange through the warp's scratch
+// takes E-point DFTs across the E lanes (four-step with n = E x 32).
+template <int E>
+struct SmallCfg {
+    static constexpr int N = 32 * E, NH = N / 2 + 1;
+    static constexpr int F = 32 / E;                         // transforms per warp
+    static constexpr int Q = 32 / E;                         // k2 values per lane after the exchange
+    static constexpr int SPC = (128 / N) * (128 / N);        // samples per CTA
+    static constexpr int WARPS = 9;                          // 8 for the row pairs, 9 for the columns
+    static constexpr int SAMPLE_FLOATS = N * N + 2 * N * NH; // the field, then the half spectrum
+    static constexpr size_t SMEM = ((size_t)SPC * SAMPLE_FLOATS + 2 * (WARPS * 1024 + E * 33)) * sizeof(float);
+};
+
+// E lanes per transform (lane t: transform f = t / E, n1 = t % E).  On entry lane (f, n1) holds
+// x_f[n1 + E j] in v[j]; on return X_f[k2 + 32 k1] with k2 = n1 Q + q in v[q E + k1] (Q = 32 / E).
+// scr: the warp's 1024 complex values of scratch; tw: W_n^(n1 k2) at tw[n1 * 33 + k2].
+template <int E, bool INV>
+__device__ __forceinline__ void warp_fft_small(float2 (&v)[kSq], float2 *scr, const float2 *tw, int t) {
+    constexpr int Q = 32 / E;
+    const int f = t / E, n1 = t - f * E;
+    fft32<INV>(v);  // Y_f[n1][k2] = sum_j x_f[n1 + E j] W_32^(j k2), in v[brev5(k2)]
+    // Y_f[n1][k2] W_n^(n1 k2) to scratch element (32 f + ((k2 + f) mod 32)) E + n1
+#pragma unroll
+    for (int k2 = 0; k2 < kSq; ++k2)
+        scr[(f * kSq + ((k2 + f) & 31)) * E + n1] = cmulw<INV>(v[brev5(k2)], tw[n1 * 33 + k2]);
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int k2 = n1 * Q + q;
+        float2 y[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) y[m] = scr[(f * kSq + ((k2 + f) & 31)) * E + m];
+        if constexpr (E == 2) {
+            v[q * 2 + 0] = cadd(y[0], y[1]);
+            v[q * 2 + 1] = csub(y[0], y[1]);
+        } else {  // E = 4: W_4 = -i (inverse: +i)
+            const float2 s02 = cadd(y[0], y[2]), d02 = csub(y[0], y[2]);
+            const float2 s13 = cadd(y[1], y[3]), d13 = csub(y[1], y[3]);
+            const float2 r13 = INV ? make_float2(-d13.y, d13.x) : make_float2(d13.y, -d13.x);
+            v[q * 4 + 0] = cadd(s02, s13);
+            v[q * 4 + 2] = csub(s02, s13);
+            v[q * 4 + 1] = cadd(d02, r13);
+            v[q * 4 + 3] = csub(d02, r13);
+        }
+    }
+    __syncwarp();
+}
+
+// The whole solve of SPC samples per CTA on an n x n lattice, n = 32 E.  Per step: row pass
+// (pairs of rows packed as one complex row, forward transform, split into the two half spectra),
+// column pass (forward over y, product with khatT[kx][ky] = K^(ky, kx) / n^2, inverse), row pass
+// (the two half-spectrum rows of a pair combined, inverse transform: S on both rows, update and
+// projection in place).  Then the final fields to uT (when given) and the per-sample FP64 mean
+// in a fixed order.
+template <int E>
+__global__ void __launch_bounds__(SmallCfg<E>::WARPS * 32, 1)
+    spectral_small_kernel(const float *u0, float *uT, const StepCoef *coef, const float *khatT, const float2 *twg,
+                          int ns, int nsteps, double *ubar, double *ooi) {
+    using C = SmallCfg<E>;
+    constexpr int N = C::N, NH = C::NH, F = C::F, Q = C::Q, SPC = C::SPC;
+    extern __shared__ __align__(16) float sm_small[];
+    float2 *scr_all = reinterpret_cast<float2 *>(sm_small + SPC * C::SAMPLE_FLOATS);
+    float2 *tw = scr_all + C::WARPS * 1024;
+    __shared__ double red[C::WARPS * 32];
+    const int w = threadIdx.x >> 5, t = threadIdx.x & 31, f = t / E, n1 = t - f * E;
+    float2 *scr = scr_all + w * 1024;
+    const int s0 = blockIdx.x * SPC;
+    const int nloc = ns - s0 < SPC ? ns - s0 : SPC;
+    auto fld = [&](int s) { return sm_small + s * C::SAMPLE_FLOATS; };
+    auto spc = [&](int s) { return reinterpret_cast<float2 *>(sm_small + s * C::SAMPLE_FLOATS + N * N); };
+    for (int i = threadIdx.x; i < SPC * N * N; i += blockDim.x) {
+        const int s = i / (N * N), r = i - s * N * N;
+        fld(s)[r] = s < nloc ? u0[(size_t)(s0 + s) * N * N + r] : 0.f;
+    }
+    for (int i = threadIdx.x; i < E * 33; i += blockDim.x) tw[i] = twg[i];
+    __syncthreads();
+    for (int step = 0; step < nsteps; ++step) {
+        if (w < 8) {  // forward row pass: pair p of the CTA's SPC * n / 2 pairs
+            const int p = w * F + f, s = p / (N / 2), y = 2 * (p - s * (N / 2));
+            const float *ua = fld(s) + y * N, *ub = ua + N;
+            float2 v[kSq];
+#pragma unroll
+            for (int j = 0; j < kSq; ++j) v[j] = make_float2(ua[n1 + E * j], ub[n1 + E * j]);
+            warp_fft_small<E, false>(v, scr, tw, t);
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+#pragma unroll
+                for (int k1 = 0; k1 < E; ++k1) scr[f * N + n1 * Q + q + kSq * k1] = v[q * E + k1];
+            __syncwarp();
+            float2 *sa = spc(s) + y * NH, *sb = sa + NH;
+#pragma unroll
+            for (int i = 0; i <= N / 2 / E; ++i) {
+                const int k = n1 + E * i;
+                if (k <= N / 2) {
+                    const float2 zk = scr[f * N + k], zm = scr[f * N + ((N - k) & (N - 1))];
+                    sa[k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+                    sb[k] = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        {  // column pass: slot w + 9 f of the CTA's SPC * (n / 2 + 1) columns
+            const int slot = w + C::WARPS * f;
+            const bool active = slot < SPC * NH && slot / NH < nloc;
+            const int sl = active ? slot : 0, s = sl / NH, c = sl - s * NH;
+            float2 *col = spc(s) + c;  // element ky at col[ky * NH]
+            float2 v[kSq];
+#pragma unroll
+            for (int j = 0; j < kSq; ++j) v[j] = col[(n1 + E * j) * NH];
+            warp_fft_small<E, false>(v, scr, tw, t);
+            const float *kh = khatT + (size_t)c * N;
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+#pragma unroll
+                for (int k1 = 0; k1 < E; ++k1) {
+                    const int k = n1 * Q + q + kSq * k1;
+                    const float kk = __ldg(kh + k);
+                    if (active) col[k * NH] = make_float2(v[q * E + k1].x * kk, v[q * E + k1].y * kk);
+                }
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < kSq; ++j) v[j] = col[(n1 + E * j) * NH];
+            warp_fft_small<E, true>(v, scr, tw, t);
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+#pragma unroll
+                for (int k1 = 0; k1 < E; ++k1)
+                    if (active) col[(n1 * Q + q + kSq * k1) * NH] = v[q * E + k1];
+        }
+        __syncthreads();
+        if (w < 8) {  // inverse row pass and the update
+            const int p = w * F + f, s = p / (N / 2), y = 2 * (p - s * (N / 2));
+            const float2 *sa = spc(s) + y * NH, *sb = sa + NH;
+            float2 v[kSq];
+#pragma unroll
+            for (int j = 0; j < kSq; ++j) {
+                const int k = n1 + E * j;
+                if (k <= N / 2) {
+                    const float2 a = sa[k], b = sb[k];
+                    v[j] = make_float2(a.x - b.y, a.y + b.x);
+                } else {
+                    const float2 a = sa[N - k], b = sb[N - k];
+                    v[j] = make_float2(a.x + b.y, b.x - a.y);
+                }
+            }
+            warp_fft_small<E, true>(v, scr, tw, t);  // S_y + i S_{y+1} at x = n1 Q + q + 32 k1
+            const StepCoef cf = coef[s0 + (s < nloc ? s : 0)];
+            float *ua = fld(s) + y * N, *ub = ua + N;
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+#pragma unroll
+                for (int k1 = 0; k1 < E; ++k1) {
+                    const int x = n1 * Q + q + kSq * k1;
+                    const float2 S = v[q * E + k1];
+                    const float u0v = ua[x], u1v = ub[x];
+                    const float v0 = u0v + fmaf(cf.c1, fmaf(-cf.c0, u0v, S.x), cf.c2 * u0v);
+                    const float v1 = u1v + fmaf(cf.c1, fmaf(-cf.c0, u1v, S.y), cf.c2 * u1v);
+                    ua[x] = fminf(1.f, fmaxf(-1.f, v0));
+                    ub[x] = fminf(1.f, fmaxf(-1.f, v1));
+                }
+        }
+        __syncthreads();
+    }
+    for (int s = 0; s < nloc; ++s) {
+        const float *u = fld(s);
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+            const float x = u[i];
+            acc += (double)x;
+            if (uT) uT[(size_t)(s0 + s) * N * N + i] = x;
+        }
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int i = 0; i < C::WARPS * 32; ++i) tot += red[i];
+            const double mean = tot / ((double)N * N);
+            if (ubar) ubar[s0 + s] = mean;
+            if (ooi) ooi[s0 + s] = 0.5 * (1.0 + mean);
+        }
+        __syncthreads();
+    }
+}
+
 // ----------------------------------------------------------------------------- host side
 struct SpectralState {
     int dev = -1;
@@ -353,6 +543,9 @@ struct SpectralState {
     float2 *spec = nullptr;   // [cap][1024][528]
     float *bufA = nullptr, *bufB = nullptr;
     float2 *tw = nullptr;     // [32][32]: W_1024^(t k) at [k][t]
+    int small_n = 0;          // n = 64 or 128: the resident form's tables
+    float *khat_small = nullptr;   // [n/2 + 1][n]: K^(ky, kx) / n^2 at [kx][ky]
+    float2 *tw_small = nullptr;    // [E][33]: W_n^(n1 k2) at [n1][k2]
 };
 
 void spectral_release(SpectralState *s) {
@@ -362,59 +555,72 @@ void spectral_release(SpectralState *s) {
     cudaFree(s->bufA);
     cudaFree(s->bufB);
     cudaFree(s->tw);
+    cudaFree(s->khat_small);
+    cudaFree(s->tw_small);
     delete s;
 }
 
 bool spectral_supported(const Model &m) {
-    return m.d.n == kN && m.d.bc == MFMC_BC_PERIODIC && m.d.beta2 == 0.0 && 2 * m.R + 1 <= kN;
+    const int n = m.d.n;
+    return (n == kN || n == 128 || n == 64) && m.d.bc == MFMC_BC_PERIODIC && m.d.beta2 == 0.0 && 2 * m.R + 1 <= n;
 }
 
 // K^(ky, kx) = sum_dy cos(2 pi ky dy / n) sum_{dx: (dx, dy) in D} w cos(2 pi kx dx / n) (the
 // sine terms cancel: the disc and the weights are even in dx and in dy), in FP64 on the host,
 // with the weights the FP32 kernels use; divided by n^2 for the two unnormalised inverses.
-static std::vector<float> spectral_khat(const Model &m) {
-    const int n = kN, R = m.R;
+static std::vector<float> spectral_khat(const Model &m, int n) {
+    const int R = m.R, half = n / 2 + 1;
     std::vector<double> cs(n);
     for (int i = 0; i < n; ++i) cs[i] = std::cos(2.0 * M_PI * (double)i / (double)n);
     // A[dy][kx] = sum_dx w(dx, dy) cos(2 pi kx dx / n), dy = 0..R
-    std::vector<double> A((size_t)(R + 1) * kHalf, 0.0);
+    std::vector<double> A((size_t)(R + 1) * half, 0.0);
     for (int dy = 0; dy <= R; ++dy) {
         const int wd = m.widths[dy];
-        for (int kx = 0; kx < kHalf; ++kx) {
+        for (int kx = 0; kx < half; ++kx) {
             double s = 0.0;
             for (int dx = -wd; dx <= wd; ++dx) {
                 const double wt = m.d.kernel == MFMC_KERNEL_CONSTANT ? 1.0 : (double)m.wtab[dx * dx + dy * dy];
                 s += wt * cs[(size_t)(((long long)kx * (dx + n)) % n)];
             }
-            A[(size_t)dy * kHalf + kx] = s;
+            A[(size_t)dy * half + kx] = s;
         }
     }
-    std::vector<float> kh((size_t)kHalf * n);
+    std::vector<float> kh((size_t)half * n);
     const double scale = 1.0 / ((double)n * n);
     for (int ky = 0; ky < n; ++ky)
-        for (int kx = 0; kx < kHalf; ++kx) {
+        for (int kx = 0; kx < half; ++kx) {
             double s = A[kx];  // dy = 0
-            for (int dy = 1; dy <= R; ++dy) s += 2.0 * cs[(size_t)((long long)ky * dy % n)] * A[(size_t)dy * kHalf + kx];
+            for (int dy = 1; dy <= R; ++dy) s += 2.0 * cs[(size_t)((long long)ky * dy % n)] * A[(size_t)dy * half + kx];
             kh[(size_t)kx * n + ky] = (float)(s * scale);
         }
     return kh;
 }
 
-static mfmc_status spectral_prepare(Model &m, size_t ns) {
+// The register transforms' twiddles (c_w32), written once per device before the first
+// spectral launch of either form.
+static mfmc_status spectral_constants() {
     int dev = 0;
     MFMC_CUDA(cudaGetDevice(&dev));
     static std::mutex mu;
     static std::vector<bool> consts_set;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((int)consts_set.size() <= dev) consts_set.resize(dev + 1, false);
+    if (!consts_set[dev]) {
+        float2 w[kSq];
+        for (int k = 0; k < kSq; ++k)
+            w[k] = make_float2((float)std::cos(2.0 * M_PI * k / kSq), (float)-std::sin(2.0 * M_PI * k / kSq));
+        MFMC_CUDA(cudaMemcpyToSymbol(c_w32, w, sizeof(w)));
+        consts_set[dev] = true;
+    }
+    return MFMC_OK;
+}
+
+static mfmc_status spectral_prepare(Model &m, size_t ns) {
+    int dev = 0;
+    MFMC_CUDA(cudaGetDevice(&dev));
     {
-        std::lock_guard<std::mutex> lock(mu);
-        if ((int)consts_set.size() <= dev) consts_set.resize(dev + 1, false);
-        if (!consts_set[dev]) {
-            float2 w[kSq];
-            for (int k = 0; k < kSq; ++k)
-                w[k] = make_float2((float)std::cos(2.0 * M_PI * k / kSq), (float)-std::sin(2.0 * M_PI * k / kSq));
-            MFMC_CUDA(cudaMemcpyToSymbol(c_w32, w, sizeof(w)));
-            consts_set[dev] = true;
-        }
+        const mfmc_status cs = spectral_constants();
+        if (cs != MFMC_OK) return cs;
     }
     if (!m.d_status) {
         MFMC_CUDA(cudaMalloc((void **)&m.d_status, sizeof(int)));
@@ -427,7 +633,7 @@ static mfmc_status spectral_prepare(Model &m, size_t ns) {
         cudaFree(s.tw);
         s.khatT = nullptr;
         s.tw = nullptr;
-        const std::vector<float> kh = spectral_khat(m);
+        const std::vector<float> kh = spectral_khat(m, kN);
         std::vector<float2> tw((size_t)kSq * kSq);
         for (int k = 0; k < kSq; ++k)
             for (int t = 0; t < kSq; ++t) {
@@ -460,9 +666,59 @@ static mfmc_status spectral_prepare(Model &m, size_t ns) {
     return MFMC_OK;
 }
 
+// The resident form for n = 64 and 128: tables once per model, one launch for the whole solve.
+template <int E>
+static mfmc_status run_solve_spectral_small(Model &m, const StepCoef *coef, const float *u0, size_t ns, int nsteps,
+                                            float *uT, double *ubar, double *ooi, cudaStream_t st) {
+    using C = SmallCfg<E>;
+    constexpr int N = C::N;
+    int dev = 0;
+    MFMC_CUDA(cudaGetDevice(&dev));
+    {
+        const mfmc_status cs = spectral_constants();
+        if (cs != MFMC_OK) return cs;
+    }
+    if (!m.spectral) m.spectral = new SpectralState();
+    SpectralState &f = *m.spectral;
+    if (f.dev != dev || f.small_n != N || !f.khat_small) {
+        cudaFree(f.khat_small);
+        cudaFree(f.tw_small);
+        f.khat_small = nullptr;
+        f.tw_small = nullptr;
+        const std::vector<float> kh = spectral_khat(m, N);
+        std::vector<float2> tw((size_t)E * 33, make_float2(0.f, 0.f));
+        for (int n1 = 0; n1 < E; ++n1)
+            for (int k2 = 0; k2 < kSq; ++k2) {
+                const long long e = (long long)n1 * k2 % N;
+                tw[(size_t)n1 * 33 + k2] =
+                    make_float2((float)std::cos(2.0 * M_PI * e / N), (float)-std::sin(2.0 * M_PI * e / N));
+            }
+        MFMC_CUDA(cudaMalloc((void **)&f.khat_small, kh.size() * sizeof(float)));
+        MFMC_CUDA(cudaMemcpy(f.khat_small, kh.data(), kh.size() * sizeof(float), cudaMemcpyHostToDevice));
+        MFMC_CUDA(cudaMalloc((void **)&f.tw_small, tw.size() * sizeof(float2)));
+        MFMC_CUDA(cudaMemcpy(f.tw_small, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        f.small_n = N;
+        f.dev = dev;
+    }
+    auto kern = spectral_small_kernel<E>;
+    MFMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
+    const unsigned grid = (unsigned)((ns + C::SPC - 1) / C::SPC);
+    kern<<<grid, C::WARPS * 32, C::SMEM, st>>>(u0, uT, coef, f.khat_small, f.tw_small, (int)ns, nsteps, ubar, ooi);
+    MFMC_LAUNCHED("spectral launch 4");
+    return MFMC_OK;
+}
+
 mfmc_status run_solve_spectral(Model &m, const StepCoef *coef, const float *u0, size_t ns, int nsteps, float *uT,
                                double *ubar, double *ooi, cudaStream_t st) {
-    if (!spectral_supported(m)) return fail(MFMC_EINVAL, "the spectral path needs n = 1024, a periodic lattice and beta2 = 0");
+    if (!spectral_supported(m))
+        return fail(MFMC_EINVAL, "the spectral path needs n = 64, 128 or 1024, a periodic lattice and beta2 = 0");
+    {
+        int one = 0;
+        MFMC_CUDA(cudaDeviceGetAttribute(&one, cudaDevAttrMaxGridDimX, 0));
+        if (ns > (size_t)one) return fail(MFMC_EINVAL, "batch too large for the spectral path");
+    }
+    if (m.d.n == 128) return run_solve_spectral_small<4>(m, coef, u0, ns, nsteps, uT, ubar, ooi, st);
+    if (m.d.n == 64) return run_solve_spectral_small<2>(m, coef, u0, ns, nsteps, uT, ubar, ooi, st);
     mfmc_status s = spectral_prepare(m, ns);
     if (s != MFMC_OK) return s;
     SpectralState &f = *m.spectral;
