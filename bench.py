@@ -770,9 +770,9 @@ def run_paper(args):
     if args.beta2 == 0:
         fft_models = [mfmc.Model(n=n, delta=d, algo=mfmc.ALGO_FFT, **common) for n, d in levels]
         fft_cost = [_batched_cost(mfmc, m, 256, base + 10 ** 7) for m in fft_models]
-        # the own-FFT spectral form where it exists (n = 64, 128)
+        # the own-FFT spectral form (register transforms on 64 and 128, mixed-radix on 88)
         spec_cost = [_batched_cost(mfmc, mfmc.Model(n=n, delta=d, algo=mfmc.ALGO_SPECTRAL, **common), 256,
-                                   base + 10 ** 7) if n in (64, 128) else None for n, d in levels]
+                                   base + 10 ** 7) for n, d in levels]
     else:
         fft_cost = spec_cost = [None] * len(models)
     paper = {}
@@ -788,6 +788,40 @@ def run_paper(args):
         plans.append({"budget_over_C1": b, "subset": [i + 1 for i in p["idx"]], "m": p["m"], "V": p["V"],
                       "Bmin_over_C1": p["Bmin"] / cost[0], "below_min_budget": p["below_min_budget"],
                       "n_feasible_subsets": p["n_feasible"]})
+    mixed = []
+    if args.beta2 == 0:
+        # the hierarchy in one launch (mfmc_solve_batch_mixed: the resident spectral queue over
+        # every model's samples) beside one mfmc_solve_batch call per model and one call over all
+        # samples; the pilot allocation and the plan at B = 1000 C_1; best of 3 after a warm-up
+        def timed(fn):
+            fn()
+            best, out = 1e30, None
+            for _ in range(3):
+                t = time.perf_counter()
+                out = fn()
+                best = min(best, time.perf_counter() - t)
+            return best, out
+
+        p1000 = mfmc.mfmc_plan(pilot, cost, 1000 * cost[0], 0).as_dict()
+        allocs = {"pilot: 50 samples of each model": [(k, n_pilot) for k in range(len(models))],
+                  "MFMC plan at B = 1000 C_1": [(i, int(k)) for i, k in zip(p1000["idx"], p1000["m"]) if k > 0]}
+        for name, al in allocs.items():
+            seeds = [_seeds(base + 10 ** 8, k, 10 ** 6 * j) for j, (_, k) in enumerate(al)]
+            flat_models = [models[i] for i, k in al for _ in range(k)]
+            flat_seeds = np.concatenate(seeds)
+
+            def per_model():
+                return np.concatenate([mfmc.mfmc_solve_batch([models[i]] * k, seeds[j])[0]
+                                       for j, (i, k) in enumerate(al)])
+
+            t_seq, f_seq = timed(per_model)
+            t_batch, (f_batch, _) = timed(lambda: mfmc.mfmc_solve_batch(flat_models, flat_seeds))
+            t_mixed, (f_mixed, _) = timed(lambda: mfmc.mfmc_solve_batch_mixed(flat_models, flat_seeds))
+            mixed.append({"allocation": name, "models": [i + 1 for i, _ in al], "m": [k for _, k in al],
+                          "per_model_calls_s": t_seq, "one_batch_call_s": t_batch, "mixed_one_launch_s": t_mixed,
+                          "mixed_speedup_vs_per_model_calls": t_seq / t_mixed,
+                          "mixed_speedup_vs_batch_call": t_batch / t_mixed,
+                          "max_rel_ooi_diff_mixed_vs_per_model": float(np.max(np.abs(f_mixed - f_seq) / f_seq))})
     p0 = mfmc.mfmc_plan(pilot, cost, 100 * cost[0], 0).as_dict()
     table = []
     for k, ((n, d), m) in enumerate(zip(levels, models)):
@@ -810,7 +844,7 @@ def run_paper(args):
                                    f"periodic lattice, beta1 = 1, beta2 = {args.beta2:g}; pilot 50 shared seeds",
                        "algo": "autotuned per model (see table1[].algo)" if args.beta2 == 0 else
                                "active-set Newton-CG step (FP64, one CTA per sample)"},
-            "pilot_wall_s": t_pilot, "table1": table, "plans": plans,
+            "pilot_wall_s": t_pilot, "table1": table, "plans": plans, "mixed": mixed,
             "paper_C1_s": 63.089}
     print(json.dumps(line), flush=True)
     return 0

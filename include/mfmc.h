@@ -91,12 +91,14 @@ typedef enum {
                                   periodic boundary only; a comparison point for very large
                                   horizons that AUTO does not pick */,
     MFMC_ALGO_ACTIVE_SET = 9   /* the beta2 > 0 step: per step the explicit convolution (FP64;
-                                  direct below 100 disc points, else by cuFFT), then a
-                                  semismooth Newton (primal-dual active-set) solve of the
-                                  resolvent equation: FP64 fields and residual, each correction
-                                  by FP32 CG preconditioned with a multigrid V-cycle; one CTA
-                                  per sample; the only algorithm for beta2 > 0 (AUTO picks
-                                  it), periodic only */,
+                                  direct below 100 disc points, else spectral: by the solver's
+                                  own transforms for even n <= 128 whose odd part factors into
+                                  3, 5, 7 and 11, by cuFFT otherwise), then a semismooth Newton
+                                  (primal-dual active-set) solve of the resolvent equation,
+                                  started from the previous step's solution: FP64 fields and
+                                  residual, each correction by FP32 CG preconditioned with a
+                                  multigrid V-cycle; one CTA per sample; the only algorithm for
+                                  beta2 > 0 (AUTO picks it), periodic only */,
     MFMC_ALGO_WEIGHTED = 10,   /* register-tiled weighted disc sum over TMA tiles: any radial
                                   kernel (the Gaussian's fastest own path), integer delta/h,
                                   either boundary; |D| FMAs per point without the prefix
@@ -105,10 +107,13 @@ typedef enum {
                                   kernels: per step a column pass (FFT over y, product with the
                                   real transform of the disc weights, inverse) and a row pass
                                   (inverse row FFT, update, forward row FFT of the new rows);
-                                  n = 1024 in two launches per step, n = 64 and 128 in one
-                                  launch for the whole solve with the fields in shared memory;
-                                  cost independent of the horizon; any kernel and radius,
-                                  periodic boundary, beta2 = 0; AUTO considers it */
+                                  n = 1024 in two launches per step; n = 64 and 128 in one
+                                  launch for the whole solve with the fields in shared memory
+                                  (register transforms); any other even n <= 128 whose odd part
+                                  is a product of 3, 5, 7 and 11 (the paper's h = 1/88) the same
+                                  way with mixed-radix transforms; cost independent of the
+                                  horizon; any kernel and radius, periodic boundary,
+                                  beta2 = 0; AUTO considers it */
 } mfmc_algo;
 
 /* One fidelity of the model (Section 2, Section 4).  The lattice is n x n on the unit
@@ -177,6 +182,32 @@ const char *mfmc_version(void);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *mfmc_last_error(void);
+
+/* Per-work-item trace (tracing support; the paper has no counterpart).  When on, the kernels
+ * that take work items from a queue append one record per item to a ring in device memory:
+ * kind 1 = an item (the whole solve of one sample, or of four on n = 64) of the resident spectral queue
+ * (mfmc_solve_batch_mixed on small lattices, MFMC_ALGO_SPECTRAL outside n = 64, 128, 1024),
+ * item = its ticket in the launch's queue; kind 2 = an item (one tile of one sample) of the
+ * mixed-fidelity step queue, item = its ticket, step = the time step; kind 3 = one sample of
+ * the beta2 > 0 solver, item = its index in the batch, step = the steps that launch ran.  t0_ns and
+ * t1_ns are the GPU's global timer (ns) when the item started and ended, sm the SM that ran it. */
+typedef struct {
+    uint64_t t0_ns, t1_ns;
+    uint32_t item, sm, kind, step;
+} mfmc_trace_record;
+
+/* Turn tracing on for the current device with a ring of `capacity` records (0 turns it off
+ * and frees the ring; at most 2^28).  Replaces any earlier ring after waiting for the device.
+ * Without this call, the environment variable MFMC_TRACE=<capacity> turns tracing on at the
+ * first traced launch on each device.  Tracing changes no result; each record costs its kernel
+ * one atomic add and one 32-byte store.  MFMC_EINVAL for a capacity above 2^28. */
+mfmc_status mfmc_trace_enable(size_t capacity);
+
+/* Wait for the current device, copy up to `max` of the records written since the last read
+ * into out[] (host), oldest first, and empty the ring.  *n_out: records copied; *dropped_out:
+ * records written but not copied (overwritten after the ring filled, or beyond max).  Either
+ * pointer may be NULL.  MFMC_EINVAL when tracing is off on the current device. */
+mfmc_status mfmc_trace_read(mfmc_trace_record *out, size_t max, size_t *n_out, uint64_t *dropped_out);
 
 /* Validate a descriptor and create a model handle (host-side only; no device work).
  * Returns MFMC_EINVAL for: NULL pointers, n % 4 != 0 or n outside [8, 16384],
@@ -281,20 +312,32 @@ mfmc_status mfmc_solve_batch(mfmc_model *const *models, const mfmc_sample_params
                              double *ubar_out);
 
 /* The same batch call for a model hierarchy (Section 3: samples of f_1 ... f_K at
- * shared parameters), with the samples of every model that streams through HBM advanced by
- * ONE kernel launch per time step: the (model, sample, tile) items of those models form one
- * work queue, fine model first, that persistent CTAs drain through an atomic ticket
+ * shared parameters), in one of two forms.
+ *
+ * Step queue: with at most 4 distinct models, each with the constant kernel and
+ * R = delta/h in {2, 4, 8, 16}, the samples of every model that streams through HBM are
+ * advanced by ONE kernel launch per time step: the (model, sample, tile) items of those models
+ * form one work queue, fine model first, that persistent CTAs drain through an atomic ticket
  * counter.  Models whose whole field fits in shared memory (the resident kernel, n <= 128)
- * instead run all their steps in one resident launch each, on a second stream concurrent
- * with the step launches.  Same arguments and results as mfmc_solve_batch; the fields of the
- * queued models are bit-identical to those of the TMA prefix kernel with 4 columns per
- * thread, their OoI differs from that solve's only by the FP64 summation order of the tile
- * partials, and resident models give the resident kernel's results.  Limits: at most 4
- * distinct models, each with the constant kernel and R = delta/h in {2, 4, 8, 16}; every
- * sample runs >= 1 step.  Other inputs return MFMC_EINVAL.  The step loop is captured in a
- * CUDA graph on the first call of a shape and replayed by later calls of the same shape.
- * Calls are serialised by a lock; the library keeps the batch buffers until exit.
- * Synchronous. */
+ * instead run all their steps in one resident launch each, on a second stream concurrent with
+ * the step launches.  The fields of the queued models are bit-identical to those of the TMA
+ * prefix kernel with 4 columns per thread, their OoI differs from that solve's only by the
+ * FP64 summation order of the tile partials, and resident models give the resident kernel's
+ * results.  The step loop is captured in a CUDA graph on the first call of a shape and
+ * replayed by later calls of the same shape.
+ *
+ * Resident spectral queue: otherwise, when every model (at most 16) has the periodic lattice,
+ * beta2 = 0, an even n <= 128 whose odd part is a product of 3, 5, 7 and 11, and any kernel and
+ * horizon (the paper's nine models of Section 4 / Table 1, delta/h = 16.5 included), ONE
+ * launch runs every sample's whole solve: persistent CTAs take (model, sample group) items,
+ * heaviest model first, through an atomic ticket counter, and keep the fields in shared memory
+ * for all steps, each item on the form MFMC_ALGO_SPECTRAL uses for its lattice (register
+ * transforms on n = 64, four samples an item, and n = 128; mixed-radix transforms otherwise).
+ * Results equal those of MFMC_ALGO_SPECTRAL's solves of the same samples.
+ *
+ * Same arguments and results as mfmc_solve_batch; every sample runs >= 1 step.  Other inputs
+ * return MFMC_EINVAL.  Calls are serialised by a lock; the library keeps the batch buffers
+ * until exit.  Synchronous. */
 mfmc_status mfmc_solve_batch_mixed(mfmc_model *const *models, const mfmc_sample_params *params,
                                    const uint64_t *seeds, size_t ns, double *ooi_out,
                                    double *ubar_out);

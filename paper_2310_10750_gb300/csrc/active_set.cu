@@ -19,21 +19,31 @@
 // multigrid V-cycle (periodic levels, damped Jacobi smoothing, full weighting and bilinear
 // prolongation: a symmetric positive definite preconditioner).
 //
-// The explicit disc sum is FP64 too: a direct sum for small discs, else through cuFFT (D2Z, a
-// product with the real spectrum of the radial weights, Z2D) between per-step launches, which
-// costs O(n^2 log n) FP64 operations per field instead of O(n^2 |D|).
+// The explicit disc sum is FP64 too: a direct sum for small discs, else spectral, which costs
+// O(n^2 log n) FP64 operations per field instead of O(n^2 |D|): for n <= 128 by the CTA itself
+// (the mixed-radix transforms of smem_fft.cuh, the half spectrum in the shared memory that the
+// coarse multigrid levels use during the Newton iteration), for larger n through cuFFT (D2Z, a
+// product with the real spectrum of the radial weights, Z2D) between per-step launches.
 //
-// One CTA per sample runs every step of its solve (every step of one launch with the direct
-// sum; one step per launch with the spectral sum, the state staying in global scratch between
-// launches); its fine-level vectors live in global scratch, the coarse multigrid levels that fit
-// in shared memory, and the CTA's reductions use a fixed order.  No CTA waits on another.  Every loop is bounded; a
-// Newton iteration that does not converge within its bound sets the status flag (a CG solve
-// that reaches its bound hands its iterate to the next Newton iteration).
+// Newton starts from the previous step's w (the first step from the beta2 = 0 step): the
+// solution moves by O(tau) per step, and on the paper's models this start needs about 40 % fewer
+// corrections than the beta2 = 0 step, whose residual -tau beta2 Lap_h w is large at interfaces.
+//
+// One CTA per sample runs every step of its solve (every step of one launch, except with the
+// cuFFT sums: one step per launch, the state staying in global scratch between launches); its
+// fine-level vectors live in global scratch, the coarse multigrid levels that fit in shared
+// memory, and the CTA's reductions use a fixed order.  No CTA waits on another.  Every loop is
+// bounded; a Newton iteration that does not converge within its bound sets the status flag (a CG
+// solve that reaches its bound hands its iterate to the next Newton iteration).
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
+#include <vector>
 
 #include "mfmc_internal.h"
+#include "smem_fft.cuh"
+#include "trace.cuh"
 
 namespace mfmc {
 
@@ -45,7 +55,7 @@ constexpr int AS_MAX_LEVELS = 8;
 constexpr int AS_NU = 2;              // damped-Jacobi sweeps before and after each coarse correction
 constexpr int AS_NU_COARSE = 16;
 constexpr float AS_OMEGA = 0.8f;
-constexpr int AS_SPECTRAL_MIN_DISC = 100;  // disc points from which the disc sum runs through cuFFT
+constexpr int AS_SPECTRAL_MIN_DISC = 100;  // disc points from which the disc sum is spectral
 
 // Multigrid levels of the CG preconditioner: n_0 = n, halved while even and >= 16 (the coarsest
 // has >= 8 points per side).  Returns the level count; sizes[l] = n_l.
@@ -102,7 +112,13 @@ struct ActiveSetArgs {
     int n, R, nsteps;
     int newton_max, cg_max;  // iteration bounds: Newton passes per step, CG iterations per correction
     int load;     // read u0 into the FP64 field first
-    int g_given;  // the disc sums of u are in g already (spectral form): no direct sum
+    int g_given;  // the disc sums of u are in g already (cuFFT form): no sum in the kernel
+    int warm;     // the launch's first step starts Newton from w in scratch (a step before it ran)
+    int own_fft;  // the disc sums by cta_disc_sums (plan, khat, tw) instead of the direct sum
+    FftPlan plan;
+    const double *khat;  // K^(ky, kx) / n^2 at [ky][n/2 + 1], FP64
+    const double2 *tw;   // W_n^j, j < n
+    TraceBuf trace;
     int finish;   // write uT, ubar and the OoI after the last step
     size_t s0;
     double ahat, chat, tau, beta1, beta2, cF;
@@ -283,6 +299,7 @@ __global__ void __launch_bounds__(AS_NT) active_set_kernel(ActiveSetArgs a) {
     __shared__ float red32[AS_NT / 32 + 1];
     __shared__ int widths[kMaxR + 1];
     const size_t smp = a.s0 + blockIdx.x;
+    const unsigned long long t_start = a.trace.rec ? trace_clock() : 0ull;
     const int n = a.n, R = a.R;
     const int nn = n * n;
     double *U = a.buf + smp * as_per_sample(n);
@@ -293,8 +310,8 @@ __global__ void __launch_bounds__(AS_NT) active_set_kernel(ActiveSetArgs a) {
     int sizes[AS_MAX_LEVELS];
     const int nl = as_levels(n, sizes);
     AsLevel lv[AS_MAX_LEVELS];
+    extern __shared__ __align__(16) float as_smem[];
     {
-        extern __shared__ float as_smem[];
         size_t smem_bytes;
         const int l0 = as_smem_from(n, &smem_bytes);
         float *q = T + nn, *qs = as_smem;  // global levels 1 .. l0 - 1, shared levels l0 ..
@@ -326,7 +343,16 @@ __global__ void __launch_bounds__(AS_NT) active_set_kernel(ActiveSetArgs a) {
         // explicit part g = gamma * u + c_F u (direct sum over the disc, FP64; R < n, so one
         // wrap of each index suffices)
         if (a.g_given) as_for(n, [&](int, int, int i) { G[i] = e2a * G[i] + a.cF * U[i]; });
-        else as_for(n, [&](int y, int x, int i) {
+        else if (a.own_fft) {  // (the coarse levels in shared memory hold nothing between steps)
+            auto ld = [&](int y, int x) { return U[y * n + x]; };
+            auto put = [&](int y, int x, double S) { G[y * n + x] = e2a * S + a.cF * U[y * n + x]; };
+            switch (n) {  // the paper's meshes on compile-time plans
+                case 64: cta_disc_sums<64, double>(a.plan, as_smem, a.khat, a.tw, ld, put); break;
+                case 88: cta_disc_sums<88, double>(a.plan, as_smem, a.khat, a.tw, ld, put); break;
+                case 128: cta_disc_sums<128, double>(a.plan, as_smem, a.khat, a.tw, ld, put); break;
+                default: cta_disc_sums<0, double>(a.plan, as_smem, a.khat, a.tw, ld, put); break;
+            }
+        } else as_for(n, [&](int y, int x, int i) {
             double S = 0.0;
             for (int dy = -R; dy <= R; ++dy) {
                 const int ady = dy < 0 ? -dy : dy, w = widths[ady];
@@ -352,12 +378,15 @@ __global__ void __launch_bounds__(AS_NT) active_set_kernel(ActiveSetArgs a) {
             G[i] = e2a * S + a.cF * U[i];
         });
         __syncthreads();
-        // start: the beta2 = 0 step, w = c_gamma u0 - g
-        as_for(n, [&](int, int, int i) {
-            const double u0 = as_clip((U[i] + tb1 * G[i]) / (1.0 + tb1 * cg));
-            W[i] = cg * u0 - G[i];
-        });
-        __syncthreads();
+        // start: w of the previous step, or at the solve's first step the beta2 = 0 step
+        // w = c_gamma u0 - g
+        if (step == 1 && !a.warm) {
+            as_for(n, [&](int, int, int i) {
+                const double u0 = as_clip((U[i] + tb1 * G[i]) / (1.0 + tb1 * cg));
+                W[i] = cg * u0 - G[i];
+            });
+            __syncthreads();
+        }
         for (int it = 1;; ++it) {
             ++n_newton;
             // FP64 residual F(w), the inactive set, and the right-hand side r = -F of J d = -F
@@ -439,6 +468,7 @@ __global__ void __launch_bounds__(AS_NT) active_set_kernel(ActiveSetArgs a) {
     if (threadIdx.x == 0) {
         atomicAdd(&a.iters[0], n_newton);
         atomicAdd(&a.iters[1], n_cg);
+        trace_put(a.trace, kTraceActiveSet, (uint32_t)smp, (uint32_t)a.nsteps, t_start);
     }
     if (failed) {
         if (threadIdx.x == 0) atomicExch(a.status, 1);
@@ -499,8 +529,35 @@ mfmc_status run_solve_active_set(Model &m, const double *eps_dev, const float *u
     a.beta1 = m.d.beta1;
     a.beta2 = m.d.beta2;
     a.cF = m.d.c_F;
+    // the disc sums: direct for small discs; else spectral, by the CTA's own transforms when the
+    // half spectrum fits in shared memory beside nothing else, else through cuFFT
     size_t smem = 0;
     as_smem_from(m.d.n, &smem);
+    const bool spectral = m.disc >= AS_SPECTRAL_MIN_DISC;
+    FftPlan plan;
+    const bool own = spectral && m.d.n <= kFftMaxN && m.d.n % 2 == 0 && fft_plan(m.d.n, &plan);
+    a.own_fft = own ? 1 : 0;
+    a.plan = plan;
+    a.khat = nullptr;
+    a.tw = nullptr;
+    a.warm = 0;
+    a.trace = trace_buf();
+    if (own) {
+        const int n = m.d.n;
+        if (!m.d_khat64) {
+            const std::vector<double> K = khat64_host(m, n);
+            std::vector<double2> tw(n);
+            for (int j = 0; j < n; ++j)
+                tw[j] = make_double2(std::cos(2.0 * M_PI * j / n), -std::sin(2.0 * M_PI * j / n));
+            MFMC_CUDA(cudaMalloc((void **)&m.d_khat64, K.size() * sizeof(double)));
+            MFMC_CUDA(cudaMemcpy(m.d_khat64, K.data(), K.size() * sizeof(double), cudaMemcpyHostToDevice));
+            MFMC_CUDA(cudaMalloc((void **)&m.d_tw64, tw.size() * sizeof(double2)));
+            MFMC_CUDA(cudaMemcpy(m.d_tw64, tw.data(), tw.size() * sizeof(double2), cudaMemcpyHostToDevice));
+        }
+        a.khat = m.d_khat64;
+        a.tw = m.d_tw64;
+        smem = std::max(smem, fft_smem_bytes<double>(n, AS_NT / 32));
+    }
     MFMC_CUDA(cudaFuncSetAttribute(active_set_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     auto launch = [&](int load, int steps, int g_given, int finish) -> mfmc_status {
         a.load = load;
@@ -514,12 +571,13 @@ mfmc_status run_solve_active_set(Model &m, const double *eps_dev, const float *u
         }
         return MFMC_OK;
     };
-    if (m.disc < AS_SPECTRAL_MIN_DISC || !fft64_available()) return launch(1, nsteps, 0, 1);
-    // spectral disc sums: g of sample s (at u + n^2 in its block) from u, between one-step launches
+    if (!spectral || own || !fft64_available()) return launch(1, nsteps, 0, 1);
+    // cuFFT disc sums: g of sample s (at u + n^2 in its block) from u, between one-step launches
     const size_t nn = (size_t)m.d.n * m.d.n;
     s = launch(1, 0, 0, nsteps == 0);
     for (int k = 1; k <= nsteps && s == MFMC_OK; ++k) {
         s = fft64_disc_sums(m, m.as_buf, per, m.as_buf + nn, per, ns, st);
+        a.warm = k > 1;
         if (s == MFMC_OK) s = launch(0, 1, 1, k == nsteps);
     }
     return s;

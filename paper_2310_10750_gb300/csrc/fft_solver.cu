@@ -237,7 +237,8 @@ mfmc_status run_solve_fft(Model &m, const StepCoef *coef, const float *u0, size_
 
 // ---- FP64 disc sums for the beta2 > 0 solver ----------------------------------------------
 // S_i = sum_{z in D} w_z u_{i+z} for a batch of FP64 fields held in strided per-sample blocks,
-// as IFFT(FFT(u) * Khat).  The weights are radial, hence even in dx and in dy, so
+// as IFFT(FFT(u) * Khat), through cuFFT: the lattices whose half spectrum does not fit in a
+// CTA's shared memory (n > 128; the solver transforms smaller ones itself).  The weights are radial, hence even in dx and in dy, so
 // Khat(kx, ky) = sum_z w_z cos(2 pi kx dx / n) cos(2 pi ky dy / n) is real; it is formed on the
 // host from a table of cos(2 pi j / n), row by row: C(|dy|, kx) = sum_dx w(dx, dy) cos(...),
 // then Khat = sum_dy C(|dy|, kx) cos(...), scaled by 1 / n^2 (the inverse is unnormalised).
@@ -270,6 +271,32 @@ __global__ void fft64_multiply_kernel(cufftDoubleComplex *spec, const double *kh
     }
 }
 
+std::vector<double> khat64_host(const Model &m, int n) {
+    const int nh1 = n / 2 + 1;
+    std::vector<double> cs(n), C((size_t)(m.R + 1) * nh1, 0.0), K((size_t)n * nh1, 0.0);
+    for (int j = 0; j < n; ++j) cs[j] = std::cos(2.0 * M_PI * j / n);
+    for (int ady = 0; ady <= m.R; ++ady) {
+        const int w = m.widths[ady];
+        for (int kx = 0; kx < nh1; ++kx) {
+            double c = 0.0;
+            for (int dx = -w; dx <= w; ++dx) {
+                const double wt = m.d.kernel == MFMC_KERNEL_CONSTANT ? 1.0 : m.wtab64[dx * dx + ady * ady];
+                c += wt * cs[(size_t)(((long)kx * dx) % n + n) % n];
+            }
+            C[(size_t)ady * nh1 + kx] = c;
+        }
+    }
+    const double inv_nn = 1.0 / ((double)n * n);
+    for (int ky = 0; ky < n; ++ky)
+        for (int kx = 0; kx < nh1; ++kx) {
+            double k = 0.0;
+            for (int dy = -m.R; dy <= m.R; ++dy)
+                k += C[(size_t)(dy < 0 ? -dy : dy) * nh1 + kx] * cs[(size_t)(((long)ky * dy) % n + n) % n];
+            K[(size_t)ky * nh1 + kx] = k * inv_nn;
+        }
+    return K;
+}
+
 mfmc_status fft64_disc_sums(Model &m, const double *u, size_t u_dist, double *S, size_t s_dist, size_t ns,
                             cudaStream_t st) {
     const CufftApi &api = cufft_api();
@@ -282,27 +309,7 @@ mfmc_status fft64_disc_sums(Model &m, const double *u, size_t u_dist, double *S,
     if (!m.fft64) m.fft64 = new Fft64State();
     Fft64State &f = *m.fft64;
     if (f.n != n) {
-        std::vector<double> cs(n), C((size_t)(m.R + 1) * nh1, 0.0), K(nh, 0.0);
-        for (int j = 0; j < n; ++j) cs[j] = std::cos(2.0 * M_PI * j / n);
-        for (int ady = 0; ady <= m.R; ++ady) {
-            const int w = m.widths[ady];
-            for (int kx = 0; kx < nh1; ++kx) {
-                double c = 0.0;
-                for (int dx = -w; dx <= w; ++dx) {
-                    const double wt = m.d.kernel == MFMC_KERNEL_CONSTANT ? 1.0 : m.wtab64[dx * dx + ady * ady];
-                    c += wt * cs[(size_t)(((long)kx * dx) % n + n) % n];
-                }
-                C[(size_t)ady * nh1 + kx] = c;
-            }
-        }
-        const double inv_nn = 1.0 / ((double)n * n);
-        for (int ky = 0; ky < n; ++ky)
-            for (int kx = 0; kx < nh1; ++kx) {
-                double k = 0.0;
-                for (int dy = -m.R; dy <= m.R; ++dy)
-                    k += C[(size_t)(dy < 0 ? -dy : dy) * nh1 + kx] * cs[(size_t)(((long)ky * dy) % n + n) % n];
-                K[(size_t)ky * nh1 + kx] = k * inv_nn;
-            }
+        const std::vector<double> K = khat64_host(m, n);
         cudaFree(f.khat);
         f.khat = nullptr;
         MFMC_CUDA(cudaMalloc((void **)&f.khat, nh * sizeof(double)));

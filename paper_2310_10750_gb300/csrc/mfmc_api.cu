@@ -52,6 +52,11 @@ Model::~Model() {
     cudaFree(padB);
     cudaFree(d_status);
     cudaFree(d_wtab64);
+    cudaFree(d_khat64);
+    cudaFree(d_khat32);
+    cudaFree(d_tw32);
+    cudaFree(sr_counter);
+    cudaFree(d_tw64);
     cudaFree(d_wsq);
     cudaFree(as_buf);
     if (gexec) cudaGraphExecDestroy(gexec);

@@ -98,6 +98,12 @@ struct Model {
     FftState *fft = nullptr;  // created by the first FFT-path solve
     Fft64State *fft64 = nullptr;  // created by the first spectral beta2 > 0 solve
     SpectralState *spectral = nullptr;  // created by the first own-FFT spectral solve
+    float *d_khat32 = nullptr;    // resident spectral form: K^ / n^2 at [ky][n/2 + 1] (FP32)
+    float2 *d_tw32 = nullptr;     // and W_n^j, j < n
+    int sr_dev = -1;              // device of those tables
+    int *sr_counter = nullptr;    // its ticket counter
+    double *d_khat64 = nullptr;   // beta2 > 0, own FFT: K^ / n^2 at [ky][n/2 + 1] (FP64)
+    double2 *d_tw64 = nullptr;    // and W_n^j, j < n
     unsigned long long *d_as_iters = nullptr;  // Newton and CG iterations of the last beta2 > 0 solve
     int as_newton_max = kAsNewtonMax;           // iteration bounds of the beta2 > 0 solver
     int as_cg_max = kAsCgMax;
@@ -207,17 +213,39 @@ bool rows_supported(const Model &m, int rx);
 // The TMA pipeline with an explicit tile-shape variant (autotuner).
 mfmc_status run_solve_tma(Model &m, int kahan, int variant, const StepCoef *coef, const float *u0, size_t ns,
                           int nsteps, float *uT, double *ubar, double *ooi, cudaStream_t st);
-// The spectral (cuFFT) form of the disc sum, periodic lattice, any kernel and radius.
-// The own-FFT spectral path (n = 1024, periodic, beta2 = 0).
+// The own-FFT spectral path (periodic, beta2 = 0): n = 1024 streamed, n = 64 and 128 resident in
+// the register-transform form, other even n <= 128 in the resident mixed-radix form.
 bool spectral_supported(const Model &m);
 mfmc_status run_solve_spectral(Model &m, const StepCoef *coef, const float *u0, size_t ns, int nsteps, float *uT,
                                double *ubar, double *ooi, cudaStream_t st);
+// K^(ky, kx) / n^2 of the model's FP32 disc weights (summed in FP64), at [kx][ky].
+std::vector<float> spectral_khat(const Model &m, int n);
+// Resident spectral solves (spectral_resident.cu): one launch over the (model, sample group) items
+// of up to kSrMaxModels models with n <= 128 (register transforms on 64 and 128, mixed-radix
+// transforms on other n).
+constexpr int kSrMaxModels = 16;
+struct SrBatch {
+    const float *u0 = nullptr;      // [ns][n][n]
+    float *uT = nullptr;            // or nullptr
+    double *ubar = nullptr, *ooi = nullptr;
+    const StepCoef *coef = nullptr;
+    const int *steps_ps = nullptr;  // per-sample step counts (device) or nullptr
+    size_t ns = 0;
+    int nsteps = 0;
+};
+bool spectral_resident_supported(const Model &m);
+// counter: one device int the launch may use as its ticket counter (zeroed on st first)
+mfmc_status run_spectral_queue(Model *const *models, const SrBatch *batches, int nm, int *counter, cudaStream_t st);
+mfmc_status run_solve_spectral_resident(Model &m, const StepCoef *coef, const float *u0, size_t ns, int nsteps,
+                                        float *uT, double *ubar, double *ooi, cudaStream_t st);
 // Per-sample FP64 mean (ubar) and OoI of ns fields of n x n, fixed summation order.
 mfmc_status launch_field_ooi(const float *u, size_t ns, int n, double *ubar, double *ooi, cudaStream_t st);
 mfmc_status run_solve_fft(Model &m, const StepCoef *coef, const float *u0, size_t ns, int nsteps, float *uT,
                           double *ubar, double *ooi, cudaStream_t st);
 // FP64 disc sums S = sum_z w_z u_{i+z} of ns fields by cuFFT: u and S are strided per-sample
 // blocks (u_dist, s_dist doubles apart); S may not overlap u.
+// The real transform of the disc weights (FP64 weights), divided by n^2, at [ky][n/2 + 1].
+std::vector<double> khat64_host(const Model &m, int n);
 mfmc_status fft64_disc_sums(Model &m, const double *u, size_t u_dist, double *S, size_t s_dist, size_t ns,
                             cudaStream_t st);
 // The beta2 > 0 step (semismooth Newton per step: FP64 fields and residual, FP32 preconditioned

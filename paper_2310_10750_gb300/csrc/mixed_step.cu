@@ -11,6 +11,10 @@
 // through the queue: each runs all its steps in one resident launch on a second stream,
 // concurrently with the step launches, since streaming their tiles through HBM every step
 // would cost more than keeping them on chip.
+//
+// A hierarchy that this queue does not serve but whose every model fits the resident spectral
+// form (even n <= 128, any kernel and horizon: the paper's nine models of Section 4) runs as one
+// launch of that form over the (model, sample) items of all its models (spectral_resident.cu).
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -22,6 +26,7 @@
 
 #include "mfmc_internal.h"
 #include "tma_step.cuh"
+#include "trace.cuh"
 
 namespace mfmc {
 
@@ -43,6 +48,7 @@ struct MixedArgs {
     int ngroups, total;
     int *counter;            // ticket counter of this step (zeroed before the solve)
     int *status;
+    TraceBuf trace;
 };
 
 struct MixedMaps {
@@ -101,6 +107,7 @@ __global__ void __launch_bounds__(256) mixed_step_kernel(const __grid_constant__
         const int item = ticket;
         __syncthreads();
         if (item >= a.total) break;
+        const unsigned long long t0 = a.trace.rec ? trace_clock() : 0ull;
         int gi = 0;
         while (gi + 1 < a.ngroups && item >= a.begin[gi + 1]) ++gi;
         const TmaArgs &g = a.g[gi];
@@ -118,6 +125,7 @@ __global__ void __launch_bounds__(256) mixed_step_kernel(const __grid_constant__
             if (threadIdx.x == 0) atomicExch(a.status, 1);
             break;
         }
+        if (threadIdx.x == 0) trace_put(a.trace, kTraceMixedStep, (uint32_t)item, (uint32_t)g.step, t0);
     }
 }
 
@@ -171,7 +179,7 @@ struct MixWorkspace {
     cudaStream_t st = nullptr;
     cudaStream_t st_res = nullptr;   // resident-kernel groups, concurrent with the step launches
     cudaEvent_t ev_init = nullptr, ev_res = nullptr;
-    MixGroupBufs g[kMixGroups];
+    MixGroupBufs g[kSrMaxModels];
     int *counters = nullptr;
     size_t counters_cap = 0;
     int *status = nullptr;
@@ -188,7 +196,7 @@ static MixWorkspace &mix_ws() {
 static mfmc_status ensure_group(MixGroupBufs &b, const Model &m, size_t k, bool padded, cudaStream_t st,
                                 uint64_t *generation) {
     MixGeom geo{};
-    if (!mix_geom(m.R, &geo)) return fail(MFMC_EINVAL, "no mixed-batch tile shape for R = %d", m.R);
+    if (padded && !mix_geom(m.R, &geo)) return fail(MFMC_EINVAL, "no mixed-batch tile shape for R = %d", m.R);
     if (b.cap >= k && b.n == m.d.n && b.R == m.R && (b.padded || !padded)) return MFMC_OK;
     ++*generation;
     MFMC_CUDA(cudaStreamSynchronize(st));
@@ -230,21 +238,31 @@ extern "C" mfmc_status mfmc_solve_batch_mixed(mfmc_model *const *models, const m
     if (ns > (size_t)kMaxNs) return fail(MFMC_EINVAL, "too many samples");
     std::vector<mfmc_model *> order;
     std::map<mfmc_model *, std::vector<size_t>> groups;
+    bool tma_route = true, spec_route = true;
     for (size_t i = 0; i < ns; ++i) {
         mfmc_model *m = models[i];
         if (!m) return fail(MFMC_EINVAL, "NULL model at sample %zu", i);
-        MixGeom geo;
-        if (m->d.kernel != MFMC_KERNEL_CONSTANT || m->d.bc != MFMC_BC_PERIODIC || !m->integer_R || m->d.beta2 > 0.0 ||
-            !mix_geom(m->R, &geo))
-            return fail(MFMC_EINVAL, "the one-launch mixed batch runs periodic constant-kernel beta2 = 0 models with "
-                                     "R in {2, 4, 8, 16}");
-        if (!groups.count(m)) order.push_back(m);
+        if (!groups.count(m)) {
+            MixGeom geo;
+            tma_route = tma_route && m->d.kernel == MFMC_KERNEL_CONSTANT && m->d.bc == MFMC_BC_PERIODIC &&
+                        m->integer_R && m->d.beta2 == 0.0 && mix_geom(m->R, &geo);
+            spec_route = spec_route && spectral_resident_supported(*m);
+            order.push_back(m);
+        }
         groups[m].push_back(i);
     }
-    if (order.size() > (size_t)kMixGroups) return fail(MFMC_EINVAL, "at most %d models per mixed batch", kMixGroups);
-    // heaviest model first in the queue: its items are taken first
-    std::stable_sort(order.begin(), order.end(), [](mfmc_model *a, mfmc_model *b) {
-        return (double)a->d.n * a->d.n * (2 * a->R + 1) > (double)b->d.n * b->d.n * (2 * b->R + 1);
+    tma_route = tma_route && order.size() <= (size_t)kMixGroups;
+    spec_route = !tma_route && spec_route && order.size() <= (size_t)kSrMaxModels;
+    if (!tma_route && !spec_route)
+        return fail(MFMC_EINVAL, "the one-launch mixed batch runs up to %d periodic constant-kernel beta2 = 0 models "
+                                 "with R in {2, 4, 8, 16}, or up to %d periodic beta2 = 0 models with even n <= 128 "
+                                 "(odd part a product of 3, 5, 7, 11) and 2R + 1 <= n",
+                    kMixGroups, kSrMaxModels);
+    // heaviest model first in the queue: its items are taken first (the spectral form's cost does
+    // not depend on the horizon)
+    std::stable_sort(order.begin(), order.end(), [&](mfmc_model *a, mfmc_model *b) {
+        const double ra = spec_route ? 1.0 : 2 * a->R + 1, rb = spec_route ? 1.0 : 2 * b->R + 1;
+        return (double)a->d.n * a->d.n * ra > (double)b->d.n * b->d.n * rb;
     });
     MixWorkspace &W = mix_ws();
     std::lock_guard<std::mutex> lk(W.mu);
@@ -266,7 +284,7 @@ extern "C" mfmc_status mfmc_solve_batch_mixed(mfmc_model *const *models, const m
     for (int g = 0; g < ng; ++g) {
         mfmc_model *m = order[g];
         const auto &idx = groups[m];
-        resident[g] = algo_supported(*m, MFMC_ALGO_RESIDENT) ? 1 : 0;
+        resident[g] = spec_route || algo_supported(*m, MFMC_ALGO_RESIDENT) ? 1 : 0;
         if (!resident[g]) queue.push_back(g);
         mfmc_status s = ensure_group(W.g[g], *m, idx.size(), !resident[g], st, &W.generation);
         if (s != MFMC_OK) return s;
@@ -280,13 +298,13 @@ extern "C" mfmc_status mfmc_solve_batch_mixed(mfmc_model *const *models, const m
         if (!resident[g]) max_steps = std::max(max_steps, group_steps[g]);
     }
     const int nq = (int)queue.size();
-    if ((size_t)max_steps > W.counters_cap) {
+    if ((size_t)std::max(max_steps, 1) > W.counters_cap) {
         MFMC_CUDA(cudaStreamSynchronize(st));
         ++W.generation;
         cudaFree(W.counters);
         W.counters = nullptr;
-        MFMC_CUDA(cudaMalloc((void **)&W.counters, max_steps * sizeof(int)));
-        W.counters_cap = max_steps;
+        MFMC_CUDA(cudaMalloc((void **)&W.counters, std::max(max_steps, 1) * sizeof(int)));
+        W.counters_cap = std::max(max_steps, 1);
     }
     if (!W.status) {
         MFMC_CUDA(cudaMalloc((void **)&W.status, sizeof(int)));
@@ -320,7 +338,25 @@ extern "C" mfmc_status mfmc_solve_batch_mixed(mfmc_model *const *models, const m
     if (any_resident) {
         MFMC_CUDA(cudaEventRecord(W.ev_init, st));
         MFMC_CUDA(cudaStreamWaitEvent(W.st_res, W.ev_init, 0));
-        for (int g = 0; g < ng; ++g) {
+        if (spec_route) {  // every model: one launch over all (model, sample) items
+            std::vector<Model *> ms(ng);
+            std::vector<SrBatch> bs(ng);
+            for (int g = 0; g < ng; ++g) {
+                MixGroupBufs &b = W.g[g];
+                const size_t k = groups[order[g]].size();
+                ms[g] = order[g];
+                bs[g].u0 = b.u0;
+                bs[g].ubar = b.out + k;
+                bs[g].ooi = b.out;
+                bs[g].coef = b.coef;
+                bs[g].steps_ps = b.steps;
+                bs[g].ns = k;
+                bs[g].nsteps = group_steps[g];
+            }
+            mfmc_status s = run_spectral_queue(ms.data(), bs.data(), ng, W.counters, W.st_res);
+            if (s != MFMC_OK) return s;
+        }
+        for (int g = 0; g < ng && !spec_route; ++g) {
             if (!resident[g]) continue;
             MixGroupBufs &b = W.g[g];
             const size_t k = groups[order[g]].size();
@@ -339,6 +375,8 @@ extern "C" mfmc_status mfmc_solve_batch_mixed(mfmc_model *const *models, const m
             key.push_back((uintptr_t)W.g[g].tb.padA);
         }
         key.push_back((uintptr_t)W.counters);
+        const TraceBuf trace = trace_buf();  // the captured launches write to the ring of their capture
+        key.push_back((uintptr_t)trace.rec);
         if (!(W.gexec && W.gkey == key)) {
             if (W.gexec) cudaGraphExecDestroy(W.gexec);
             W.gexec = nullptr;
@@ -377,6 +415,7 @@ extern "C" mfmc_status mfmc_solve_batch_mixed(mfmc_model *const *models, const m
             a.ngroups = nq;
             a.total = total;
             a.status = W.status;
+            a.trace = trace;
             const int grid = std::max(1, std::min(total, sms * std::max(1, per)));
             cudaGraph_t graph = nullptr;
             MFMC_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));

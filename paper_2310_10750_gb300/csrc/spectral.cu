@@ -1,4 +1,6 @@
-// Spectral step on this library's own FFT kernels (MFMC_ALGO_SPECTRAL), n = 1024.
+// Spectral step on this library's own FFT kernels (MFMC_ALGO_SPECTRAL): n = 1024 here, n = 64 and
+// 128 in the resident register-transform form below, other even n <= 128 in the resident
+// mixed-radix form (spectral_resident.cu).
 //
 // On the periodic lattice the nodal quadrature (gamma * u)_i = sum_{z in D} w_z u_{i+z}
 // (Section 2) is a circular convolution, so S = IFFT2(FFT2(u) * K^) with K^ the transform of
@@ -29,6 +31,7 @@
 #include <vector>
 
 #include "mfmc_internal.h"
+#include "spectral_queue.cuh"
 #include "tma_step.cuh"
 
 namespace mfmc {
@@ -403,21 +406,26 @@ __device__ __forceinline__ void warp_fft_small(float2 (&v)[kSq], float2 *scr, co
 // column pass (forward over y, product with khatT[kx][ky] = K^(ky, kx) / n^2, inverse), row pass
 // (the two half-spectrum rows of a pair combined, inverse transform: S on both rows, update and
 // projection in place).  Then the final fields to uT (when given) and the per-sample FP64 mean
-// in a fixed order.
-template <int E>
-__global__ void __launch_bounds__(SmallCfg<E>::WARPS * 32, 1)
-    spectral_small_kernel(const float *u0, float *uT, const StepCoef *coef, const float *khatT, const float2 *twg,
-                          int ns, int nsteps, double *ubar, double *ooi) {
+// in a fixed order.  The samples s0 .. s0 + nloc - 1 (nloc <= SPC) by the CTA's C::WARPS warps;
+// with STEPS, sample s takes steps_ps[s] steps (a sample whose steps are done keeps its field
+// while the others go on), else every sample nsteps.  sm_small: C::SMEM bytes of shared memory;
+// red: C::WARPS * 32 doubles.
+template <int E, bool STEPS>
+__device__ __forceinline__ void small_solve(const float *u0, float *uT, const StepCoef *coef, const float *khatT,
+                                            const float2 *twg, int s0, int nloc, const int *steps_ps, int nsteps,
+                                            double *ubar, double *ooi, float *sm_small, double *red) {
     using C = SmallCfg<E>;
     constexpr int N = C::N, NH = C::NH, F = C::F, Q = C::Q, SPC = C::SPC;
-    extern __shared__ __align__(16) float sm_small[];
     float2 *scr_all = reinterpret_cast<float2 *>(sm_small + SPC * C::SAMPLE_FLOATS);
     float2 *tw = scr_all + C::WARPS * 1024;
-    __shared__ double red[C::WARPS * 32];
     const int w = threadIdx.x >> 5, t = threadIdx.x & 31, f = t / E, n1 = t - f * E;
     float2 *scr = scr_all + w * 1024;
-    const int s0 = blockIdx.x * SPC;
-    const int nloc = ns - s0 < SPC ? ns - s0 : SPC;
+    auto steps_of = [&](int s) { return s >= nloc ? 0 : steps_ps[s0 + s]; };
+    int kmax = nsteps;
+    if constexpr (STEPS) {
+        kmax = 0;
+        for (int s = 0; s < nloc; ++s) kmax = max(kmax, steps_of(s));
+    }
     auto fld = [&](int s) { return sm_small + s * C::SAMPLE_FLOATS; };
     auto spc = [&](int s) { return reinterpret_cast<float2 *>(sm_small + s * C::SAMPLE_FLOATS + N * N); };
     for (int i = threadIdx.x; i < SPC * N * N; i += blockDim.x) {
@@ -426,7 +434,7 @@ __global__ void __launch_bounds__(SmallCfg<E>::WARPS * 32, 1)
     }
     for (int i = threadIdx.x; i < E * 33; i += blockDim.x) tw[i] = twg[i];
     __syncthreads();
-    for (int step = 0; step < nsteps; ++step) {
+    for (int step = 0; step < kmax; ++step) {
         if (w < 8) {  // forward row pass: pair p of the CTA's SPC * n / 2 pairs
             const int p = w * F + f, s = p / (N / 2), y = 2 * (p - s * (N / 2));
             const float *ua = fld(s) + y * N, *ub = ua + N;
@@ -499,6 +507,8 @@ __global__ void __launch_bounds__(SmallCfg<E>::WARPS * 32, 1)
             warp_fft_small<E, true>(v, scr, tw, t);  // S_y + i S_{y+1} at x = n1 Q + q + 32 k1
             const StepCoef cf = coef[s0 + (s < nloc ? s : 0)];
             float *ua = fld(s) + y * N, *ub = ua + N;
+            bool live = true;
+            if constexpr (STEPS) live = step < steps_of(s);  // else the sample's steps are done
 #pragma unroll
             for (int q = 0; q < Q; ++q)
 #pragma unroll
@@ -508,8 +518,10 @@ __global__ void __launch_bounds__(SmallCfg<E>::WARPS * 32, 1)
                     const float u0v = ua[x], u1v = ub[x];
                     const float v0 = u0v + fmaf(cf.c1, fmaf(-cf.c0, u0v, S.x), cf.c2 * u0v);
                     const float v1 = u1v + fmaf(cf.c1, fmaf(-cf.c0, u1v, S.y), cf.c2 * u1v);
-                    ua[x] = fminf(1.f, fmaxf(-1.f, v0));
-                    ub[x] = fminf(1.f, fmaxf(-1.f, v1));
+                    if (live) {
+                        ua[x] = fminf(1.f, fmaxf(-1.f, v0));
+                        ub[x] = fminf(1.f, fmaxf(-1.f, v1));
+                    }
                 }
         }
         __syncthreads();
@@ -532,6 +544,100 @@ __global__ void __launch_bounds__(SmallCfg<E>::WARPS * 32, 1)
             if (ooi) ooi[s0 + s] = 0.5 * (1.0 + mean);
         }
         __syncthreads();
+    }
+}
+
+template <int E>
+__global__ void __launch_bounds__(SmallCfg<E>::WARPS * 32, 1)
+    spectral_small_kernel(const float *u0, float *uT, const StepCoef *coef, const float *khatT, const float2 *twg,
+                          int ns, int nsteps, double *ubar, double *ooi) {
+    using C = SmallCfg<E>;
+    extern __shared__ __align__(16) float sm_small[];
+    __shared__ double red[C::WARPS * 32];
+    const int s0 = blockIdx.x * C::SPC;
+    const int nloc = ns - s0 < C::SPC ? ns - s0 : C::SPC;
+    small_solve<E, false>(u0, uT, coef, khatT, twg, s0, nloc, nullptr, nsteps, ubar, ooi, sm_small, red);
+}
+
+// ----------------------------------------------------------------------------- the queue
+// One sample's whole solve on the mixed-radix transforms (any even n <= 128 they serve): the
+// field in shared memory, per step the disc sums of cta_disc_sums written straight into the
+// update and projection (the pair's rows are no longer read by the transforms then), at the end
+// the field to uT and the FP64 mean in a fixed order.  N > 0: n == N on the compile-time plan.
+template <int N>
+__device__ __noinline__ void sq_solve_generic(const SqModelDev &M, int s, float *smem, double *red) {
+    const int n = M.plan.n, nn = n * n;
+    float *u = smem;
+    void *fsm = smem + nn;  // n even: n^2 floats keep the next region 16-byte aligned
+    const float *src = M.u0 + (size_t)s * nn;
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) u[i] = src[i];
+    const StepCoef cf = M.coef[s];
+    const int steps = M.steps_ps ? M.steps_ps[s] : M.nsteps;
+    for (int k = 0; k < steps; ++k)
+        cta_disc_sums<N, float>(
+            M.plan, fsm, M.khat, M.tw, [&](int y, int x) { return u[y * n + x]; },
+            [&](int y, int x, float S) {
+                const float uv = u[y * n + x];
+                const float v = uv + fmaf(cf.c1, fmaf(-cf.c0, uv, S), cf.c2 * uv);
+                u[y * n + x] = fminf(1.f, fmaxf(-1.f, v));
+            });
+    __syncthreads();
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) {
+        const float x = u[i];
+        acc += (double)x;
+        if (M.uT) M.uT[(size_t)s * nn + i] = x;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int i = 0; i < kSqThreads; ++i) tot += red[i];
+        const double mean = tot / (double)nn;
+        if (M.ubar) M.ubar[s] = mean;
+        if (M.ooi) M.ooi[s] = 0.5 * (1.0 + mean);
+    }
+    __syncthreads();  // the field and red are free for the next item
+}
+
+// Persistent CTAs take (model, sample group) items through an atomic ticket counter, heaviest
+// model first (the host orders the models), and run each with the fastest form for its lattice.
+__global__ void __launch_bounds__(kSqThreads, 1) spectral_queue_kernel(const __grid_constant__ SqArgs a) {
+    extern __shared__ __align__(16) float sq_smem[];
+    __shared__ double red[kSqThreads];
+    __shared__ int item;
+    for (;;) {
+        if (threadIdx.x == 0) item = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int it = item;
+        __syncthreads();  // every thread has read the ticket before thread 0 takes the next
+        if (it >= a.total) break;
+        const unsigned long long t0 = a.trace.rec ? trace_clock() : 0ull;
+        int k = 0;
+        while (k + 1 < a.nm && it >= a.begin[k + 1]) ++k;
+        const SqModelDev &M = a.m[k];
+        const int local = it - a.begin[k];
+        if (M.kind == kSqSmall128) {
+            if (M.steps_ps)
+                small_solve<4, true>(M.u0, M.uT, M.coef, M.khat, M.tw, local, 1, M.steps_ps, M.nsteps, M.ubar, M.ooi,
+                                     sq_smem, red);
+            else
+                small_solve<4, false>(M.u0, M.uT, M.coef, M.khat, M.tw, local, 1, nullptr, M.nsteps, M.ubar, M.ooi,
+                                      sq_smem, red);
+        } else if (M.kind == kSqSmall64) {
+            const int s0 = local * SmallCfg<2>::SPC, nloc = min(SmallCfg<2>::SPC, M.ns - s0);
+            if (M.steps_ps)
+                small_solve<2, true>(M.u0, M.uT, M.coef, M.khat, M.tw, s0, nloc, M.steps_ps, M.nsteps, M.ubar, M.ooi,
+                                     sq_smem, red);
+            else
+                small_solve<2, false>(M.u0, M.uT, M.coef, M.khat, M.tw, s0, nloc, nullptr, M.nsteps, M.ubar, M.ooi,
+                                      sq_smem, red);
+        } else if (M.plan.n == 88) {
+            sq_solve_generic<88>(M, local, sq_smem, red);
+        } else {
+            sq_solve_generic<0>(M, local, sq_smem, red);
+        }
+        if (threadIdx.x == 0) trace_put(a.trace, kTraceSpectralQueue, (uint32_t)it, 0, t0);
     }
 }
 
@@ -562,13 +668,14 @@ void spectral_release(SpectralState *s) {
 
 bool spectral_supported(const Model &m) {
     const int n = m.d.n;
-    return (n == kN || n == 128 || n == 64) && m.d.bc == MFMC_BC_PERIODIC && m.d.beta2 == 0.0 && 2 * m.R + 1 <= n;
+    return ((n == kN || n == 128 || n == 64) && m.d.bc == MFMC_BC_PERIODIC && m.d.beta2 == 0.0 && 2 * m.R + 1 <= n) ||
+           spectral_resident_supported(m);
 }
 
 // K^(ky, kx) = sum_dy cos(2 pi ky dy / n) sum_{dx: (dx, dy) in D} w cos(2 pi kx dx / n) (the
 // sine terms cancel: the disc and the weights are even in dx and in dy), in FP64 on the host,
 // with the weights the FP32 kernels use; divided by n^2 for the two unnormalised inverses.
-static std::vector<float> spectral_khat(const Model &m, int n) {
+std::vector<float> spectral_khat(const Model &m, int n) {
     const int R = m.R, half = n / 2 + 1;
     std::vector<double> cs(n);
     for (int i = 0; i < n; ++i) cs[i] = std::cos(2.0 * M_PI * (double)i / (double)n);
@@ -666,10 +773,10 @@ static mfmc_status spectral_prepare(Model &m, size_t ns) {
     return MFMC_OK;
 }
 
-// The resident form for n = 64 and 128: tables once per model, one launch for the whole solve.
+// The register form's tables for n = 32 E (once per model and device): K^ / n^2 at [kx][ky] and
+// W_n^(n1 k2) at [n1][k2]; the register transforms' constants first.
 template <int E>
-static mfmc_status run_solve_spectral_small(Model &m, const StepCoef *coef, const float *u0, size_t ns, int nsteps,
-                                            float *uT, double *ubar, double *ooi, cudaStream_t st) {
+static mfmc_status small_tables(Model &m, const float **khatT, const float2 **twp) {
     using C = SmallCfg<E>;
     constexpr int N = C::N;
     int dev = 0;
@@ -700,10 +807,51 @@ static mfmc_status run_solve_spectral_small(Model &m, const StepCoef *coef, cons
         f.small_n = N;
         f.dev = dev;
     }
+    *khatT = f.khat_small;
+    *twp = f.tw_small;
+    return MFMC_OK;
+}
+
+mfmc_status spectral_small_tables(Model &m, const float **khatT, const float2 **tw) {
+    if (m.d.n == 128) return small_tables<4>(m, khatT, tw);
+    if (m.d.n == 64) return small_tables<2>(m, khatT, tw);
+    return fail(MFMC_EINVAL, "the register-transform form serves n = 64 and 128");
+}
+
+size_t spectral_queue_smem(int kind, int n) {
+    if (kind == kSqSmall128) return SmallCfg<4>::SMEM;
+    if (kind == kSqSmall64) return SmallCfg<2>::SMEM;
+    return (size_t)n * n * sizeof(float) + fft_smem_bytes<float>(n, kSqThreads / 32);
+}
+
+int spectral_queue_blocks_per_sm(size_t smem) {
+    cudaFuncSetAttribute(spectral_queue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, spectral_queue_kernel, kSqThreads, smem);
+    (void)cudaGetLastError();  // a failed query must not be reported by a later launch check
+    return e == cudaSuccess && per > 0 ? per : 1;
+}
+
+mfmc_status launch_spectral_queue(const SqArgs &a, int grid, size_t smem, cudaStream_t st) {
+    MFMC_CUDA(cudaFuncSetAttribute(spectral_queue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    spectral_queue_kernel<<<grid, kSqThreads, smem, st>>>(a);
+    MFMC_LAUNCHED("spectral queue launch");
+    return MFMC_OK;
+}
+
+// The resident form for n = 64 and 128: tables once per model, one launch for the whole solve.
+template <int E>
+static mfmc_status run_solve_spectral_small(Model &m, const StepCoef *coef, const float *u0, size_t ns, int nsteps,
+                                            float *uT, double *ubar, double *ooi, cudaStream_t st) {
+    using C = SmallCfg<E>;
+    const float *khatT = nullptr;
+    const float2 *tw = nullptr;
+    const mfmc_status s = small_tables<E>(m, &khatT, &tw);
+    if (s != MFMC_OK) return s;
     auto kern = spectral_small_kernel<E>;
     MFMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
     const unsigned grid = (unsigned)((ns + C::SPC - 1) / C::SPC);
-    kern<<<grid, C::WARPS * 32, C::SMEM, st>>>(u0, uT, coef, f.khat_small, f.tw_small, (int)ns, nsteps, ubar, ooi);
+    kern<<<grid, C::WARPS * 32, C::SMEM, st>>>(u0, uT, coef, khatT, tw, (int)ns, nsteps, ubar, ooi);
     MFMC_LAUNCHED("spectral launch 4");
     return MFMC_OK;
 }
@@ -711,7 +859,8 @@ static mfmc_status run_solve_spectral_small(Model &m, const StepCoef *coef, cons
 mfmc_status run_solve_spectral(Model &m, const StepCoef *coef, const float *u0, size_t ns, int nsteps, float *uT,
                                double *ubar, double *ooi, cudaStream_t st) {
     if (!spectral_supported(m))
-        return fail(MFMC_EINVAL, "the spectral path needs n = 64, 128 or 1024, a periodic lattice and beta2 = 0");
+        return fail(MFMC_EINVAL, "the spectral path needs n = 1024 or an even n <= 128 whose odd part factors into 3, "
+                                 "5, 7 and 11, a periodic lattice and beta2 = 0");
     {
         int one = 0;
         MFMC_CUDA(cudaDeviceGetAttribute(&one, cudaDevAttrMaxGridDimX, 0));
@@ -719,6 +868,7 @@ mfmc_status run_solve_spectral(Model &m, const StepCoef *coef, const float *u0, 
     }
     if (m.d.n == 128) return run_solve_spectral_small<4>(m, coef, u0, ns, nsteps, uT, ubar, ooi, st);
     if (m.d.n == 64) return run_solve_spectral_small<2>(m, coef, u0, ns, nsteps, uT, ubar, ooi, st);
+    if (m.d.n != kN) return run_solve_spectral_resident(m, coef, u0, ns, nsteps, uT, ubar, ooi, st);
     mfmc_status s = spectral_prepare(m, ns);
     if (s != MFMC_OK) return s;
     SpectralState &f = *m.spectral;

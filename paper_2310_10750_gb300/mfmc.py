@@ -133,6 +133,16 @@ _sig("mfmc_server_destroy", None, [_vp])
 _sig("mfmc_solve_fields_noalloc", _st, [_vp, _vp, _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp])
 
 
+class mfmc_trace_record(ctypes.Structure):
+    _fields_ = [("t0_ns", ctypes.c_uint64), ("t1_ns", ctypes.c_uint64), ("item", ctypes.c_uint32),
+                ("sm", ctypes.c_uint32), ("kind", ctypes.c_uint32), ("step", ctypes.c_uint32)]
+
+
+_sig("mfmc_trace_enable", _st, [ctypes.c_size_t])
+_sig("mfmc_trace_read", _st, [ctypes.POINTER(mfmc_trace_record), ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t),
+                              ctypes.POINTER(ctypes.c_uint64)])
+
+
 def _check(status):
     if status != MFMC_OK:
         raise MfmcError(status, _L.mfmc_last_error().decode())
@@ -220,6 +230,26 @@ def mfmc_model_solver_stats(model: Model):
     nw, cgi = ctypes.c_uint64(0), ctypes.c_uint64(0)
     _check(_L.mfmc_model_solver_stats(model.handle, ctypes.byref(nw), ctypes.byref(cgi)))
     return int(nw.value), int(cgi.value)
+
+
+TRACE_SPECTRAL_QUEUE, TRACE_MIXED_STEP, TRACE_ACTIVE_SET = 1, 2, 3
+
+
+def mfmc_trace_enable(capacity: int):
+    """Per-work-item trace on the current device with a ring of `capacity` records (0: off)."""
+    _check(_L.mfmc_trace_enable(capacity))
+
+
+def mfmc_trace_read(max_records: int = 1 << 20):
+    """Records written since the last read (oldest first) as a numpy structured array with
+    fields t0_ns, t1_ns, item, sm, kind, step, and the count of records not returned."""
+    buf = (mfmc_trace_record * max_records)()
+    n, dropped = ctypes.c_size_t(0), ctypes.c_uint64(0)
+    _check(_L.mfmc_trace_read(buf, max_records, ctypes.byref(n), ctypes.byref(dropped)))
+    dt = np.dtype([("t0_ns", np.uint64), ("t1_ns", np.uint64), ("item", np.uint32), ("sm", np.uint32),
+                   ("kind", np.uint32), ("step", np.uint32)])
+    arr = np.frombuffer(bytes(buf)[:n.value * ctypes.sizeof(mfmc_trace_record)], dtype=dt).copy()
+    return arr, int(dropped.value)
 
 
 def make_params(ns, eps=None, theta=None, nsteps=None):

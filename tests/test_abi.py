@@ -122,3 +122,11 @@ def test_host_setters_and_version(lib):
     assert (m.info().band_height, m.info().columns_per_thread) == (64, 4)
     m.set_band_height(0, 4)                      # 0: the batch's rows split evenly over the warps
     assert m.info().band_height == 0
+
+
+def test_trace_argument_checks_on_host(lib):
+    # rejected before any device call, so these run without a GPU
+    _, mfmc = lib
+    assert mfmc._L.mfmc_trace_enable((1 << 28) + 1) == mfmc.MFMC_EINVAL
+    assert "2^28" in mfmc.mfmc_last_error()
+    assert mfmc._L.mfmc_trace_read(None, 5, None, None) == mfmc.MFMC_EINVAL

@@ -137,12 +137,18 @@ def test_mixed_rejects_unsupported(gpu_lib):
     extra = mf.Model(n=128, delta=8 / 128, nsteps=4, **COMMON)
     with pytest.raises(mf.MfmcError):   # five distinct models
         mf.mfmc_solve_batch_mixed(gs + [extra], np.arange(5, dtype=np.uint64))
-    r3 = mf.Model(n=64, delta=3 / 64, nsteps=4, **COMMON)
-    with pytest.raises(mf.MfmcError):   # R outside {2, 4, 8, 16}
+    r3 = mf.Model(n=136, delta=3 / 136, nsteps=4, **COMMON)
+    with pytest.raises(mf.MfmcError):   # R outside {2, 4, 8, 16} and n > 128
         mf.mfmc_solve_batch_mixed([r3], [1])
-    gauss = mf.Model(n=64, delta=8 / 64, kernel=1, delta_hf=0.25, nsteps=4, **COMMON)
-    with pytest.raises(mf.MfmcError):   # Gaussian kernel
+    gauss = mf.Model(n=144, delta=8 / 144, kernel=1, delta_hf=0.25, nsteps=4, **COMMON)
+    with pytest.raises(mf.MfmcError):   # Gaussian kernel and n > 128
         mf.mfmc_solve_batch_mixed([gauss], [1])
+    many = [mf.Model(n=64, delta=(3 + k) / 64, nsteps=4, **COMMON) for k in range(17)]
+    with pytest.raises(mf.MfmcError):   # 17 models for the resident spectral queue (at most 16)
+        mf.mfmc_solve_batch_mixed(many, np.arange(17, dtype=np.uint64))
+    b2 = mf.Model(n=64, delta=8 / 64, beta2=0.05, nsteps=4, **COMMON)
+    with pytest.raises(mf.MfmcError):   # beta2 > 0
+        mf.mfmc_solve_batch_mixed([b2], [1])
     zero = mf.Model(n=64, delta=4 / 64, nsteps=0, **COMMON)
     with pytest.raises(mf.MfmcError):   # no step to take
         mf.mfmc_solve_batch_mixed([zero], [1])
@@ -150,3 +156,53 @@ def test_mixed_rejects_unsupported(gpu_lib):
     f, _ = mf.mfmc_solve_batch_mixed([gs[3]], [5])
     fr, _, _, _ = oracle_model(64, 2, 4).solve_sample(5)
     assert abs(f[0] - fr) <= 1e-5 * fr
+
+
+# The paper's hierarchy (Section 4, Table 1): Gaussian kernel, h in {1/128, 1/88, 1/64} x delta in
+# {0.25, 0.1875, 0.125} (delta/h = 16.5 on h = 1/88), nuclei IC.  The TMA queue does not serve it;
+# every model fits the resident spectral form, so one launch runs the samples of all nine.
+PAPER = [(128, 0.25), (128, 0.1875), (88, 0.1875), (88, 0.25), (128, 0.125), (88, 0.125),
+         (64, 0.1875), (64, 0.25), (64, 0.125)]
+GAUSS = dict(kernel=1, delta_hf=0.25, eps=0.0421900462, tau=0.01, ic=2)
+
+
+def test_mixed_paper_hierarchy_matches_oracle(gpu_lib):
+    mf = gpu_lib
+    steps = 15
+    gs = [mf.Model(n=n, delta=d, nsteps=steps, **GAUSS) for n, d in PAPER]
+    pick = [8, 0, 2, 5, 1, 7, 3, 6, 4, 0, 2, 8]
+    seeds = np.arange(len(pick), dtype=np.uint64) + 2023
+    f, ubar = mf.mfmc_solve_batch_mixed([gs[k] for k in pick], seeds)
+    for i, k in enumerate(pick):
+        n, d = PAPER[k]
+        fr, mean, _, _ = O.OracleModel(n=n, delta=d, nsteps=steps, **GAUSS).solve_sample(int(seeds[i]))
+        assert abs(f[i] - fr) <= 1e-5 * fr, (i, n, d, f[i], fr)
+        assert abs(ubar[i] - mean) <= 2e-5 * fr
+
+
+def test_mixed_paper_hierarchy_matches_per_model_spectral_solves(gpu_lib):
+    # against per-model MFMC_ALGO_SPECTRAL solves: on h = 1/88 the same resident mixed-radix
+    # kernel (identical results); on 1/64 and 1/128 the register-transform form (FP32 rounding of
+    # two different transforms); per-sample step counts; a repeated call is bitwise identical
+    mf = gpu_lib
+    steps = 40
+    gs = [mf.Model(n=n, delta=d, nsteps=steps, **GAUSS) for n, d in PAPER]
+    ref = [mf.Model(n=n, delta=d, nsteps=steps, algo=mf.ALGO_SPECTRAL, **GAUSS) for n, d in PAPER]
+    pick = [k for k in range(9) for _ in range(3)]
+    seeds = np.arange(len(pick), dtype=np.uint64) + 9000
+    f, ubar = mf.mfmc_solve_batch_mixed([gs[k] for k in pick], seeds)
+    fr, ur = mf.mfmc_solve_batch([ref[k] for k in pick], seeds)
+    for i, k in enumerate(pick):
+        if PAPER[k][0] == 88:
+            assert f[i] == fr[i] and ubar[i] == ur[i], i
+        else:
+            assert abs(f[i] - fr[i]) <= 1e-6 * fr[i], i
+    f2, _ = mf.mfmc_solve_batch_mixed([gs[k] for k in pick], seeds)
+    assert np.array_equal(f, f2)
+    steps_ps = [1 + (7 * i) % steps for i in range(len(pick))]
+    p = mf.make_params(len(pick), nsteps=steps_ps)
+    fp, _ = mf.mfmc_solve_batch_mixed([gs[k] for k in pick], seeds, params=p)
+    for i in (0, 4, 8, 13, 20, 26):
+        n, d = PAPER[pick[i]]
+        fo, _, _, _ = O.OracleModel(n=n, delta=d, nsteps=steps_ps[i], **GAUSS).solve_sample(int(seeds[i]))
+        assert abs(fp[i] - fo) <= 1e-5 * fo, (i, steps_ps[i])

@@ -1,6 +1,6 @@
 """The spectral step on the library's own FFT kernels (MFMC_ALGO_SPECTRAL: n = 1024 in two
-passes per step, n = 64 and 128 resident in shared memory) against the FP64 oracle's direct
-disc sums.
+passes per step, n = 64 and 128 resident in shared memory with register transforms, other even
+n <= 128 resident with mixed-radix transforms) against the FP64 oracle's direct disc sums.
 
 Tolerance: the transforms round in FP32.  A 1024-point transform by 32 x 32 with radix-2
 stages has 10 rounded butterfly levels and FP32 twiddles, so each transform adds about
@@ -92,8 +92,11 @@ def test_spectral_matches_the_cufft_path_and_is_deterministic(gpu_lib):
 
 def test_spectral_rejects_unsupported_models(gpu_lib):
     mf = gpu_lib
-    for kw in (dict(n=512, delta=8 / 512), dict(n=96, delta=8 / 96), dict(n=N, delta=8 / N, bc=mf.BC_COLLAR, bc_value=-1.0),
-               dict(n=N, delta=8 / N, beta2=0.05)):
+    # 512 and 136: neither 1024 nor <= 128; 52 = 4 x 13 (13 is not a radix); 36 with a disc wider
+    # than the lattice; the collar boundary; beta2 > 0
+    for kw in (dict(n=512, delta=8 / 512), dict(n=136, delta=8 / 136), dict(n=52, delta=8 / 52),
+               dict(n=36, delta=18 / 36), dict(n=N, delta=8 / N, bc=mf.BC_COLLAR, bc_value=-1.0),
+               dict(n=96, delta=8 / 96, bc=mf.BC_COLLAR, bc_value=-1.0), dict(n=N, delta=8 / N, beta2=0.05)):
         with pytest.raises(Exception):
             mf.Model(algo=mf.ALGO_SPECTRAL, nsteps=1, **kw)
 
@@ -177,3 +180,49 @@ def test_spectral_small_lattice_first_in_a_fresh_process(gpu_lib):
     r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     assert float(r.stdout.strip().splitlines()[-1]) <= 1e-6
+
+
+@pytest.mark.parametrize("n,delta,kernel,ns", [(88, 11 / 88, 1, 3), (88, 0.1875, 1, 2), (96, 8 / 96, 0, 3),
+                                               (120, 20 / 120, 0, 2), (44, 5 / 44, 1, 4), (100, 9 / 100, 0, 1)])
+def test_spectral_mixed_radix_lattices_one_step(gpu_lib, n, delta, kernel, ns):
+    # the resident mixed-radix form: radices 11 4 2 (88, also at the non-integer delta/h = 16.5),
+    # 3 4 4 2 (96), 5 3 4 2 (120), 11 4 (44), 5 5 4 (100); nuclei IC (obstacle active)
+    mf = gpu_lib
+    kw = dict(n=n, delta=delta, eps=0.02, tau=5e-3, nsteps=1, ic=2)
+    if kernel == 1:
+        kw.update(kernel=1, delta_hf=0.25)
+    g = mf.Model(algo=mf.ALGO_SPECTRAL, **kw)
+    o = O.OracleModel(**kw)
+    seeds = np.arange(ns, dtype=np.uint64) + 3 * n
+    u0, uT, f, ubar = gpu_solve(mf, g, seeds)
+    eps = mf.mfmc_sample_eps(g, seeds)
+    for i in range(ns):
+        ref = o.step(u0[i], float(eps[i]))
+        assert np.abs(uT[i] - ref).max() <= 4e-6 * max(1.0, np.abs(u0[i]).max()), i
+        assert abs(f[i] - 0.5 * (1.0 + ref.mean())) <= 1e-5 * 0.5 * (1.0 + ref.mean())
+    assert np.abs(uT).max() <= 1.0 and (uT == 1.0).any()   # the +1 bound is active around the nuclei
+
+
+@pytest.mark.parametrize("delta", [0.1875, 0.25, 0.125])
+def test_spectral_paper_88_models(gpu_lib, delta):
+    # Table 1's models 3 (delta/h = 16.5), 4 and 6 on h = 1/88: 12 steps against the oracle;
+    # 100 steps against cuFFT's transforms; a repeated call is bitwise identical
+    mf = gpu_lib
+    g = mf.Model(n=88, delta=delta, nsteps=12, algo=mf.ALGO_SPECTRAL, **GAUSS)
+    o = O.OracleModel(n=88, delta=delta, nsteps=12, **GAUSS)
+    seeds = np.arange(3, dtype=np.uint64) + 41
+    _, uT, f, _ = gpu_solve(mf, g, seeds)
+    for i, s in enumerate(seeds):
+        fr, _, ur, _ = o.solve_sample(int(s))
+        assert abs(f[i] - fr) <= 1e-5 * fr
+        assert np.abs(uT[i] - ur).max() <= 12 * 4e-6 * math.exp(0.12)
+    kw = dict(n=88, delta=delta, nsteps=100, **GAUSS)
+    gs = mf.Model(algo=mf.ALGO_SPECTRAL, **kw)
+    gf = mf.Model(algo=mf.ALGO_FFT, **kw)
+    seeds = np.arange(5, dtype=np.uint64) + 77
+    _, us, fs, _ = gpu_solve(mf, gs, seeds)
+    _, uf, ff, _ = gpu_solve(mf, gf, seeds)
+    _, us2, fs2, _ = gpu_solve(mf, gs, seeds)
+    assert np.array_equal(us, us2) and np.array_equal(fs, fs2)
+    assert np.abs(fs - ff).max() <= 1e-6 * ff.max()
+    assert np.abs(us - uf).max() <= 100 * 4e-6 * math.exp(1.0)
