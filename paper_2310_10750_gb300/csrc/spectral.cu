@@ -362,7 +362,10 @@ struct SmallCfg {
     static constexpr int Q = 32 / E;                         // k2 values per lane after the exchange
     static constexpr int SPC = (128 / N) * (128 / N);        // samples per CTA
     static constexpr int WARPS = 9;                          // 8 for the row pairs, 9 for the columns
-    static constexpr int SAMPLE_FLOATS = N * N + 2 * N * NH; // the field, then the half spectrum
+    // the field in rows of RS = N + 1 floats (the row pairs a warp transforms then start in
+    // different banks), then the half spectrum (N RS is even: 8-byte aligned)
+    static constexpr int RS = N + 1;
+    static constexpr int SAMPLE_FLOATS = N * RS + 2 * N * NH;
     static constexpr size_t SMEM = ((size_t)SPC * SAMPLE_FLOATS + 2 * (WARPS * 1024 + E * 33)) * sizeof(float);
 };
 
@@ -427,17 +430,17 @@ __device__ __forceinline__ void small_solve(const float *u0, float *uT, const St
         for (int s = 0; s < nloc; ++s) kmax = max(kmax, steps_of(s));
     }
     auto fld = [&](int s) { return sm_small + s * C::SAMPLE_FLOATS; };
-    auto spc = [&](int s) { return reinterpret_cast<float2 *>(sm_small + s * C::SAMPLE_FLOATS + N * N); };
+    auto spc = [&](int s) { return reinterpret_cast<float2 *>(sm_small + s * C::SAMPLE_FLOATS + N * C::RS); };
     for (int i = threadIdx.x; i < SPC * N * N; i += blockDim.x) {
         const int s = i / (N * N), r = i - s * N * N;
-        fld(s)[r] = s < nloc ? u0[(size_t)(s0 + s) * N * N + r] : 0.f;
+        fld(s)[(r / N) * C::RS + r % N] = s < nloc ? u0[(size_t)(s0 + s) * N * N + r] : 0.f;
     }
     for (int i = threadIdx.x; i < E * 33; i += blockDim.x) tw[i] = twg[i];
     __syncthreads();
     for (int step = 0; step < kmax; ++step) {
         if (w < 8) {  // forward row pass: pair p of the CTA's SPC * n / 2 pairs
             const int p = w * F + f, s = p / (N / 2), y = 2 * (p - s * (N / 2));
-            const float *ua = fld(s) + y * N, *ub = ua + N;
+            const float *ua = fld(s) + y * C::RS, *ub = ua + C::RS;
             float2 v[kSq];
 #pragma unroll
             for (int j = 0; j < kSq; ++j) v[j] = make_float2(ua[n1 + E * j], ub[n1 + E * j]);
@@ -506,7 +509,7 @@ __device__ __forceinline__ void small_solve(const float *u0, float *uT, const St
             }
             warp_fft_small<E, true>(v, scr, tw, t);  // S_y + i S_{y+1} at x = n1 Q + q + 32 k1
             const StepCoef cf = coef[s0 + (s < nloc ? s : 0)];
-            float *ua = fld(s) + y * N, *ub = ua + N;
+            float *ua = fld(s) + y * C::RS, *ub = ua + C::RS;
             bool live = true;
             if constexpr (STEPS) live = step < steps_of(s);  // else the sample's steps are done
 #pragma unroll
@@ -530,7 +533,7 @@ __device__ __forceinline__ void small_solve(const float *u0, float *uT, const St
         const float *u = fld(s);
         double acc = 0.0;
         for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
-            const float x = u[i];
+            const float x = u[(i / N) * C::RS + i % N];
             acc += (double)x;
             if (uT) uT[(size_t)(s0 + s) * N * N + i] = x;
         }
