@@ -366,28 +366,33 @@ struct SmallCfg {
     // different banks), then the half spectrum (N RS is even: 8-byte aligned)
     static constexpr int RS = N + 1;
     static constexpr int SAMPLE_FLOATS = N * RS + 2 * N * NH;
-    static constexpr size_t SMEM = ((size_t)SPC * SAMPLE_FLOATS + 2 * (WARPS * 1024 + E * 33)) * sizeof(float);
+    // a warp's scratch (complex values): the exchange of warp_fft_small (1024) and the forward
+    // row pass's staging of its F transforms, each padded by one value (F (N + 1) >= 1024)
+    static constexpr int SCR = F * (N + 1);
+    static constexpr size_t SMEM = ((size_t)SPC * SAMPLE_FLOATS + 2 * (WARPS * SCR + E * 33)) * sizeof(float);
 };
 
 // E lanes per transform (lane t: transform f = t / E, n1 = t % E).  On entry lane (f, n1) holds
 // x_f[n1 + E j] in v[j]; on return X_f[k2 + 32 k1] with k2 = n1 Q + q in v[q E + k1] (Q = 32 / E).
 // scr: the warp's 1024 complex values of scratch; tw: W_n^(n1 k2) at tw[n1 * 33 + k2].
+// The exchange stores element (f, k2, n1) in slot n1 ^ (k2 / Q) of its row of E, so that both
+// the stores (fixed k2) and the loads (k2 = n1 Q + q, fixed q and m) touch every bank once.
 template <int E, bool INV>
 __device__ __forceinline__ void warp_fft_small(float2 (&v)[kSq], float2 *scr, const float2 *tw, int t) {
     constexpr int Q = 32 / E;
     const int f = t / E, n1 = t - f * E;
     fft32<INV>(v);  // Y_f[n1][k2] = sum_j x_f[n1 + E j] W_32^(j k2), in v[brev5(k2)]
-    // Y_f[n1][k2] W_n^(n1 k2) to scratch element (32 f + ((k2 + f) mod 32)) E + n1
+    // Y_f[n1][k2] W_n^(n1 k2) to scratch element (32 f + ((k2 + f) mod 32)) E + (n1 ^ (k2 / Q))
 #pragma unroll
     for (int k2 = 0; k2 < kSq; ++k2)
-        scr[(f * kSq + ((k2 + f) & 31)) * E + n1] = cmulw<INV>(v[brev5(k2)], tw[n1 * 33 + k2]);
+        scr[(f * kSq + ((k2 + f) & 31)) * E + (n1 ^ (k2 / Q))] = cmulw<INV>(v[brev5(k2)], tw[n1 * 33 + k2]);
     __syncwarp();
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int k2 = n1 * Q + q;
         float2 y[E];
 #pragma unroll
-        for (int m = 0; m < E; ++m) y[m] = scr[(f * kSq + ((k2 + f) & 31)) * E + m];
+        for (int m = 0; m < E; ++m) y[m] = scr[(f * kSq + ((k2 + f) & 31)) * E + (m ^ n1)];  // k2 / Q = n1
         if constexpr (E == 2) {
             v[q * 2 + 0] = cadd(y[0], y[1]);
             v[q * 2 + 1] = csub(y[0], y[1]);
@@ -420,9 +425,9 @@ __device__ __forceinline__ void small_solve(const float *u0, float *uT, const St
     using C = SmallCfg<E>;
     constexpr int N = C::N, NH = C::NH, F = C::F, Q = C::Q, SPC = C::SPC;
     float2 *scr_all = reinterpret_cast<float2 *>(sm_small + SPC * C::SAMPLE_FLOATS);
-    float2 *tw = scr_all + C::WARPS * 1024;
+    float2 *tw = scr_all + C::WARPS * C::SCR;
     const int w = threadIdx.x >> 5, t = threadIdx.x & 31, f = t / E, n1 = t - f * E;
-    float2 *scr = scr_all + w * 1024;
+    float2 *scr = scr_all + w * C::SCR;
     auto steps_of = [&](int s) { return s >= nloc ? 0 : steps_ps[s0 + s]; };
     int kmax = nsteps;
     if constexpr (STEPS) {
@@ -448,14 +453,14 @@ __device__ __forceinline__ void small_solve(const float *u0, float *uT, const St
 #pragma unroll
             for (int q = 0; q < Q; ++q)
 #pragma unroll
-                for (int k1 = 0; k1 < E; ++k1) scr[f * N + n1 * Q + q + kSq * k1] = v[q * E + k1];
+                for (int k1 = 0; k1 < E; ++k1) scr[f * (N + 1) + n1 * Q + q + kSq * k1] = v[q * E + k1];
             __syncwarp();
             float2 *sa = spc(s) + y * NH, *sb = sa + NH;
 #pragma unroll
             for (int i = 0; i <= N / 2 / E; ++i) {
                 const int k = n1 + E * i;
                 if (k <= N / 2) {
-                    const float2 zk = scr[f * N + k], zm = scr[f * N + ((N - k) & (N - 1))];
+                    const float2 zk = scr[f * (N + 1) + k], zm = scr[f * (N + 1) + ((N - k) & (N - 1))];
                     sa[k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
                     sb[k] = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
                 }
