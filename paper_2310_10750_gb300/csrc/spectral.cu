@@ -610,7 +610,10 @@ __device__ __noinline__ void sq_solve_generic(const SqModelDev &M, int s, float 
 
 // Persistent CTAs take (model, sample group) items through an atomic ticket counter, heaviest
 // model first (the host orders the models), and run each with the fastest form for its lattice.
-__global__ void __launch_bounds__(kSqThreads, 1) spectral_queue_kernel(const __grid_constant__ SqArgs a) {
+// SMALL: the launch has register-form items (n = 64, 128), whose 160-odd registers allow one CTA
+// per SM; without them the mixed-radix items alone fit two CTAs per SM.
+template <bool SMALL>
+__global__ void __launch_bounds__(kSqThreads, SMALL ? 1 : 2) spectral_queue_kernel(const __grid_constant__ SqArgs a) {
     extern __shared__ __align__(16) float sq_smem[];
     __shared__ double red[kSqThreads];
     __shared__ int item;
@@ -625,14 +628,14 @@ __global__ void __launch_bounds__(kSqThreads, 1) spectral_queue_kernel(const __g
         while (k + 1 < a.nm && it >= a.begin[k + 1]) ++k;
         const SqModelDev &M = a.m[k];
         const int local = it - a.begin[k];
-        if (M.kind == kSqSmall128) {
+        if (SMALL && M.kind == kSqSmall128) {
             if (M.steps_ps)
                 small_solve<4, true>(M.u0, M.uT, M.coef, M.khat, M.tw, local, 1, M.steps_ps, M.nsteps, M.ubar, M.ooi,
                                      sq_smem, red);
             else
                 small_solve<4, false>(M.u0, M.uT, M.coef, M.khat, M.tw, local, 1, nullptr, M.nsteps, M.ubar, M.ooi,
                                       sq_smem, red);
-        } else if (M.kind == kSqSmall64) {
+        } else if (SMALL && M.kind == kSqSmall64) {
             const int s0 = local * SmallCfg<2>::SPC, nloc = min(SmallCfg<2>::SPC, M.ns - s0);
             if (M.steps_ps)
                 small_solve<2, true>(M.u0, M.uT, M.coef, M.khat, M.tw, s0, nloc, M.steps_ps, M.nsteps, M.ubar, M.ooi,
@@ -832,17 +835,19 @@ size_t spectral_queue_smem(int kind, int n) {
     return (size_t)n * n * sizeof(float) + fft_smem_bytes<float>(n, kSqThreads / 32);
 }
 
-int spectral_queue_blocks_per_sm(size_t smem) {
-    cudaFuncSetAttribute(spectral_queue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+int spectral_queue_blocks_per_sm(bool small, size_t smem) {
+    auto kern = small ? spectral_queue_kernel<true> : spectral_queue_kernel<false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per = 0;
-    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, spectral_queue_kernel, kSqThreads, smem);
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kSqThreads, smem);
     (void)cudaGetLastError();  // a failed query must not be reported by a later launch check
     return e == cudaSuccess && per > 0 ? per : 1;
 }
 
-mfmc_status launch_spectral_queue(const SqArgs &a, int grid, size_t smem, cudaStream_t st) {
-    MFMC_CUDA(cudaFuncSetAttribute(spectral_queue_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    spectral_queue_kernel<<<grid, kSqThreads, smem, st>>>(a);
+mfmc_status launch_spectral_queue(bool small, const SqArgs &a, int grid, size_t smem, cudaStream_t st) {
+    auto kern = small ? spectral_queue_kernel<true> : spectral_queue_kernel<false>;
+    MFMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, kSqThreads, smem, st>>>(a);
     MFMC_LAUNCHED("spectral queue launch");
     return MFMC_OK;
 }

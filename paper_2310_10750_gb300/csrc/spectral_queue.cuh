@@ -5,7 +5,8 @@
 // solve of spectral.cu (small_solve); items of any other n run the mixed-radix solve of
 // smem_fft.cuh (one sample; the paper's n = 88 on its compile-time plan).  The CTA has the
 // register form's nine warps, and its shared memory is the largest any of the launch's models
-// needs.  Kernel and launcher in spectral.cu, host set-up in spectral_resident.cu.
+// needs; a launch without register-form items uses a form of the kernel that fits two CTAs per
+// SM.  Kernel and launcher in spectral.cu, host set-up in spectral_resident.cu.
 #pragma once
 
 #include "mfmc_internal.h"
@@ -44,8 +45,9 @@ size_t spectral_queue_smem(int kind, int n);
 // The register form's tables of a model with n = 64 or 128 (made once per model and device; the
 // register transforms' constants are written on the device first).
 mfmc_status spectral_small_tables(Model &m, const float **khatT, const float2 **tw);
-// CTAs of the queue kernel that fit on one SM with `smem` bytes of dynamic shared memory.
-int spectral_queue_blocks_per_sm(size_t smem);
-mfmc_status launch_spectral_queue(const SqArgs &a, int grid, size_t smem, cudaStream_t st);
+// CTAs of the queue kernel that fit on one SM with `smem` bytes of dynamic shared memory; small:
+// the launch has register-form items (the kernel form that carries them).
+int spectral_queue_blocks_per_sm(bool small, size_t smem);
+mfmc_status launch_spectral_queue(bool small, const SqArgs &a, int grid, size_t smem, cudaStream_t st);
 
 }  // namespace mfmc

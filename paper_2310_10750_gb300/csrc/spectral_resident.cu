@@ -60,6 +60,7 @@ mfmc_status run_spectral_queue(Model *const *models, const SrBatch *batches, int
     SqArgs a{};
     size_t smem = 0;
     long long total = 0;
+    bool small = false;
     for (int k = 0; k < nm; ++k) {
         Model &m = *models[k];
         if (!spectral_resident_supported(m))
@@ -70,6 +71,7 @@ mfmc_status run_spectral_queue(Model *const *models, const SrBatch *batches, int
         const int n = m.d.n;
         d.kind = n == 128 ? kSqSmall128 : (n == 64 ? kSqSmall64 : kSqGeneric);
         d.spc = d.kind == kSqSmall64 ? 4 : 1;
+        small = small || d.kind != kSqGeneric;
         if (d.kind == kSqGeneric) {
             mfmc_status s = sr_tables(m);
             if (s != MFMC_OK) return s;
@@ -104,9 +106,9 @@ mfmc_status run_spectral_queue(Model *const *models, const SrBatch *batches, int
     MFMC_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
     a.counter = counter;
     a.trace = trace_buf();
-    const int per = spectral_queue_blocks_per_sm(smem);
+    const int per = spectral_queue_blocks_per_sm(small, smem);
     const int grid = (int)std::min<long long>(total, (long long)sms * per);
-    return launch_spectral_queue(a, grid, smem, st);
+    return launch_spectral_queue(small, a, grid, smem, st);
 }
 
 mfmc_status run_solve_spectral_resident(Model &m, const StepCoef *coef, const float *u0, size_t ns, int nsteps,
