@@ -69,16 +69,6 @@ __host__ __device__ inline int as_levels(int n, int *sizes) {
     return L;
 }
 
-// Doubles of scratch per sample: the FP64 fine-level vectors, then (two floats per double) the
-// FP32 fine-level vectors and, per coarser level, v, f, r and m.
-__host__ __device__ inline size_t as_per_sample(int n) {
-    int sz[AS_MAX_LEVELS];
-    const int L = as_levels(n, sz);
-    size_t f = (size_t)AS_VEC32 * n * n;
-    for (int l = 1; l < L; ++l) f += (size_t)4 * sz[l] * sz[l];
-    return (size_t)AS_VEC64 * n * n + (f + 1) / 2;
-}
-
 // The coarse levels from as_smem_from(n) on live in dynamic shared memory (at most
 // AS_SMEM_BUDGET bytes): their passes are short, and each then costs a shared-memory round trip
 // and a barrier instead of a global one.  Returns that level and sets *bytes.
@@ -98,13 +88,28 @@ __host__ __device__ inline int as_smem_from(int n, size_t *bytes) {
     return l0;
 }
 
+// Doubles of scratch per sample: the FP64 fine-level vectors, then (two floats per double) the
+// FP32 fine-level vectors and, per coarser level that does not live in shared memory, v, f, r
+// and m (the levels from as_smem_from(n) on take no global scratch, which keeps a batch's
+// working set smaller for L2).
+__host__ __device__ inline size_t as_per_sample(int n) {
+    int sz[AS_MAX_LEVELS];
+    as_levels(n, sz);
+    size_t smem_bytes;
+    const int l0 = as_smem_from(n, &smem_bytes);
+    size_t f = (size_t)AS_VEC32 * n * n;
+    for (int l = 1; l < l0; ++l) f += (size_t)4 * sz[l] * sz[l];
+    return (size_t)AS_VEC64 * n * n + (f + 1) / 2;
+}
+
 struct ActiveSetArgs {
     const float *u0;
     float *uT;
     double *ubar, *ooi;
     const double *eps;   // per sample, or nullptr: eps_nominal
     double eps_nominal;
-    double *buf;         // [ns][as_per_sample(n)]
+    double *buf;         // [ns][per]
+    size_t per;          // as_per_sample(n)
     int *status;         // set to 1 when an iteration bound is reached
     unsigned long long *iters;  // [2]: Newton and CG iterations, added by every CTA
     const double *wtab;  // Gaussian: FP64 weight / eps^2 by r^2; nullptr: constant kernel
@@ -302,7 +307,7 @@ __global__ void __launch_bounds__(AS_NT) active_set_kernel(ActiveSetArgs a) {
     const unsigned long long t_start = a.trace.rec ? trace_clock() : 0ull;
     const int n = a.n, R = a.R;
     const int nn = n * n;
-    double *U = a.buf + smp * as_per_sample(n);
+    double *U = a.buf + smp * a.per;
     double *G = U + nn, *W = G + nn;
     float *D = reinterpret_cast<float *>(W + nn);
     float *Rr = D + nn, *Pp = Rr + nn, *Q = Pp + nn, *M = Q + nn, *Z = M + nn, *T = Z + nn;
@@ -515,6 +520,7 @@ mfmc_status run_solve_active_set(Model &m, const double *eps_dev, const float *u
     a.eps = eps_dev;
     a.eps_nominal = m.d.eps;
     a.buf = m.as_buf;
+    a.per = per;
     a.status = m.d_status;
     a.iters = m.d_as_iters;
     a.wtab = m.d.kernel == MFMC_KERNEL_GAUSSIAN ? m.d_wtab64 : nullptr;
