@@ -113,7 +113,8 @@ def test_active_set_stationary_batch_and_rejections(gpu_lib):
 SUM_CASES = [dict(n=48, delta=5 / 48, kernel=0),                 # 81 disc points: direct sum
              dict(n=48, delta=6 / 48, kernel=0),                 # 113 points: own transforms, 48 = 4 4 3
              dict(n=88, delta=0.1875, kernel=1, delta_hf=0.25),  # delta/h = 16.5: own, 88 = 4 2 11
-             dict(n=52, delta=6 / 52, kernel=0)]                 # 52 = 4 13: through cuFFT
+             dict(n=52, delta=6 / 52, kernel=0),                 # 52 = 4 13: through cuFFT
+             dict(n=40, delta=6 / 40, kernel=1, delta_hf=0.25)]  # 113 points: own, 40 = 5 4 2
 
 
 @pytest.mark.parametrize("case", range(len(SUM_CASES)))

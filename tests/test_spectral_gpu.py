@@ -183,10 +183,11 @@ def test_spectral_small_lattice_first_in_a_fresh_process(gpu_lib):
 
 
 @pytest.mark.parametrize("n,delta,kernel,ns", [(88, 11 / 88, 1, 3), (88, 0.1875, 1, 2), (96, 8 / 96, 0, 3),
-                                               (120, 20 / 120, 0, 2), (44, 5 / 44, 1, 4), (100, 9 / 100, 0, 1)])
+                                               (120, 20 / 120, 0, 2), (44, 5 / 44, 1, 4), (100, 9 / 100, 0, 1),
+                                               (56, 7 / 56, 1, 3)])
 def test_spectral_mixed_radix_lattices_one_step(gpu_lib, n, delta, kernel, ns):
     # the resident mixed-radix form: radices 11 4 2 (88, also at the non-integer delta/h = 16.5),
-    # 3 4 4 2 (96), 5 3 4 2 (120), 11 4 (44), 5 5 4 (100); nuclei IC (obstacle active)
+    # 3 4 4 2 (96), 5 3 4 2 (120), 11 4 (44), 5 5 4 (100), 7 4 2 (56); nuclei IC (obstacle active)
     mf = gpu_lib
     kw = dict(n=n, delta=delta, eps=0.02, tau=5e-3, nsteps=1, ic=2)
     if kernel == 1:
