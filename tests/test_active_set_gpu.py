@@ -52,7 +52,7 @@ def test_active_set_one_step_elementwise(gpu_lib, case):
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
-def test_active_set_solve_matches_oracle(gpu_lib, case):
+def test_active_set_solve_matches_oracle(gpu_lib, ooi_errors, case):
     mf = gpu_lib
     steps = 15
     kw = dict(CASES[case], eps=0.04219, nsteps=steps, ic=2, beta2=0.05)
@@ -69,6 +69,8 @@ def test_active_set_solve_matches_oracle(gpu_lib, case):
     assert newton - len(seeds) * steps <= cg <= 30 * (newton - len(seeds) * steps)
     for i, s in enumerate(seeds):
         fr, mean, ur, _ = B2.solve_sample(o, int(s), 0.05, steps)
+        ooi_errors.add("beta2 = 0.05 active-set step (nuclei IC; direct and spectral disc sums)", f[i], fr,
+                       ubar[i], mean, np.abs(uT[i] - ur).max())
         assert abs(f[i] - fr) <= 1e-8 * fr
         assert abs(ubar[i] - mean) <= 2e-8
         assert np.abs(uT[i] - ur).max() <= 1e-6
@@ -118,7 +120,7 @@ SUM_CASES = [dict(n=48, delta=5 / 48, kernel=0),                 # 81 disc point
 
 
 @pytest.mark.parametrize("case", range(len(SUM_CASES)))
-def test_active_set_direct_and_spectral_disc_sums(gpu_lib, case):
+def test_active_set_direct_and_spectral_disc_sums(gpu_lib, ooi_errors, case):
     mf = gpu_lib
     steps = 8
     kw = dict(SUM_CASES[case], eps=0.04219, tau=0.01, nsteps=steps, ic=2, beta2=0.05)
@@ -128,6 +130,8 @@ def test_active_set_direct_and_spectral_disc_sums(gpu_lib, case):
     u0, uT, f, ubar = gpu_solve(mf, g, seeds)
     for i, s in enumerate(seeds):
         fr, mean, ur, _ = B2.solve_sample(o, int(s), 0.05, steps)
+        ooi_errors.add("beta2 = 0.05 active-set step (nuclei IC; direct and spectral disc sums)", f[i], fr,
+                       ubar[i], mean, np.abs(uT[i] - ur).max())
         assert abs(f[i] - fr) <= 1e-8 * fr
         assert abs(ubar[i] - mean) <= 2e-8
         assert np.abs(uT[i] - ur).max() <= 1e-6

@@ -44,7 +44,7 @@ def _fixture():
 
 
 @pytest.mark.slow
-def test_large_hf_samples_0_to_3_100_steps_fp32_and_kahan(gpu_lib):
+def test_large_hf_samples_0_to_3_100_steps_fp32_and_kahan(gpu_lib, ooi_errors):
     # samples 0..3 of the large configuration, 100 steps, against the FP64 oracle's solutions
     # stored by tests/golden/make_large_hf_fixture.py (OoI, mean and u at 512 fixed points):
     # the autotuned path (the own-FFT spectral form at this horizon), the plain FP32 prefix sums
@@ -71,6 +71,8 @@ def test_large_hf_samples_0_to_3_100_steps_fp32_and_kahan(gpu_lib):
         torch.cuda.synchronize()
         f, m, u = ooi.cpu().numpy(), ubar.cpu().numpy(), uT.cpu().numpy().astype(np.float64)
         for i, (_, fr, mr, ur) in enumerate(ref):
+            ooi_errors.add("1024x1024, R=32, 100 steps (autotuned, FP32 prefix and compensated forms)", f[i], fr,
+                           m[i], mr, np.abs(u[i][pts[:, 0], pts[:, 1]] - ur).max())
             assert abs(f[i] - fr) <= 1e-9 * fr, (algo, i)
             assert abs(m[i] - mr) <= 1e-5 * abs(mr) + 1e-9, (algo, i)
             assert np.abs(u[i][pts[:, 0], pts[:, 1]] - ur).max() <= tol, (algo, i)

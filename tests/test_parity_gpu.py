@@ -117,7 +117,7 @@ def test_one_step_elementwise(gpu_lib, algo, n, R):
 
 # --------------------------------------------------------------------------- solves
 @pytest.mark.parametrize("algo", ALGOS + ["auto", "rows"])
-def test_plain_mc_config_64_R4(gpu_lib, algo):
+def test_plain_mc_config_64_R4(gpu_lib, ooi_errors, algo):
     # 64 x 64, delta = 4h, constant kernel, eps ~ U[0.024, 0.036], tau = 1e-3, 200 steps,
     # u0 i.i.d. U[-0.05, 0.05]; 32 samples
     mf = gpu_lib
@@ -130,6 +130,8 @@ def test_plain_mc_config_64_R4(gpu_lib, algo):
     growth = math.exp(1.0 * 200 * 1e-3)
     for i, s in enumerate(seeds):
         fr, mean, ur, eps = o.solve_sample(int(s))
+        ooi_errors.add("64x64, R=4, 200 steps, uniform IC (every kernel path)", f[i], fr, ubar[i], mean,
+                       np.abs(uT[i] - ur).max())
         assert abs(f[i] - fr) <= 1e-5 * fr
         tol = 200 * 4e-6 * 0.05 * growth
         assert np.abs(uT[i] - ur).max() <= tol
@@ -236,7 +238,7 @@ def _gpu_batch_of_config(mf, n, R, steps, ns, algo="auto", ic=1, base=0):
 
 
 @pytest.mark.slow
-def test_single_fidelity_256_R8_full_size_sampled(gpu_lib):
+def test_single_fidelity_256_R8_full_size_sampled(gpu_lib, ooi_errors):
     # 256 x 256, delta = 8h, 1000 steps, 512 samples in one launch configuration (the one
     # the benchmark times); the oracle checks every 64th sample and the last element by element
     # and every sample is checked by the exact linear-regime identity of the mean.
@@ -255,6 +257,8 @@ def test_single_fidelity_256_R8_full_size_sampled(gpu_lib):
         assert abs(ubar[i] - pred) <= 1e-6 * np.abs(u0[i]).max() + 1e-9
     for i in list(range(0, ns, 64)) + [ns - 1]:
         fr, mean, ur, _ = o.solve_sample(int(seeds[i]))
+        ooi_errors.add("256x256, R=8, 1000 steps, smoothed-noise IC, 512-sample batch", f[i], fr, ubar[i], mean,
+                       np.abs(uT[i] - ur).max())
         assert abs(f[i] - fr) <= 1e-5 * fr
         assert abs(ubar[i] - mean) <= 1e-5 * abs(mean) + 1e-9
         assert np.abs(uT[i] - ur).max() <= steps * 4e-6 * 0.05 * math.e
@@ -262,7 +266,7 @@ def test_single_fidelity_256_R8_full_size_sampled(gpu_lib):
 
 @pytest.mark.slow
 @pytest.mark.parametrize("n,R", [(512, 16), (128, 4), (64, 2)])
-def test_hierarchy_levels_sampled(gpu_lib, n, R):
+def test_hierarchy_levels_sampled(gpu_lib, ooi_errors, n, R):
     # the MFMC hierarchy with delta = 1/32 and a shared 512^2 base field
     mf = gpu_lib
     g, o = _gpu_batch_of_config(mf, n, R, 1000 if n < 512 else 200, 16, base=512)
@@ -270,6 +274,8 @@ def test_hierarchy_levels_sampled(gpu_lib, n, R):
     u0, uT, f, ubar = gpu_solve(mf, g, seeds)
     for i in (0, 15):
         fr, mean, ur, _ = o.solve_sample(int(seeds[i]))
+        ooi_errors.add(f"{n}x{n}, R={R}, {1000 if n < 512 else 200} steps, hierarchy level (512^2 base field)",
+                       f[i], fr, ubar[i], mean, np.abs(uT[i] - ur).max())
         assert abs(f[i] - fr) <= 1e-5 * fr
         assert abs(ubar[i] - mean) <= 1e-5 * abs(mean) + 1e-9
         assert np.abs(uT[i] - ur).max() <= (1000 if n < 512 else 200) * 4e-6 * math.e
