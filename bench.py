@@ -495,10 +495,11 @@ def run_hierarchy(args):
     return 0
 
 
-def serving_metrics(mfmc, total):
+def serving_metrics(mfmc, total, load=0.8):
     """Poisson stream of solve requests of mixed fidelity (64^2 .. 1024^2 in 40/30/20/8/2 %,
     delta = 1/32, 500-2000 steps each) through the continuous-batching server: the capacity
-    (2000 requests submitted at once), then `total` requests at 0.8 x that capacity."""
+    (2000 requests submitted at once), then `total` requests at `load` x that capacity (above 1:
+    an overload, in which requests wait for slots and the latencies grow with the backlog)."""
     import numpy as np
     rng = np.random.default_rng(20231016 + 1000003 * 3)
     sizes = [64, 128, 256, 512, 1024]
@@ -536,12 +537,12 @@ def serving_metrics(mfmc, total):
     cap_n = min(2000, total)
     st_cap, wall_cap = run_stream(cap_n, 0.0)              # all at once: capacity
     capacity = cap_n / wall_cap
-    st, wall = run_stream(total, 0.8 * capacity)
-    return {"workload": f"{total} requests, Poisson at 0.8 x measured capacity, n in 64..1024 (40/30/20/8/2 %), "
-                        "R = n/32, 500-2000 steps, 120 GB budget",
+    st, wall = run_stream(total, load * capacity)
+    return {"workload": f"{total} requests, Poisson at {load:g} x measured capacity, n in 64..1024 "
+                        "(40/30/20/8/2 %), R = n/32, 500-2000 steps, 120 GB budget",
             "p50_latency_s": st["p50_latency_s"], "p99_latency_s": st["p99_latency_s"],
             "mean_latency_s": st["mean_latency_s"], "samples_per_s": st["samples_per_s"],
-            "capacity_samples_per_s": capacity, "arrival_rate": 0.8 * capacity, "wall_s": wall,
+            "capacity_samples_per_s": capacity, "arrival_rate": load * capacity, "wall_s": wall,
             "completed": st["completed"], "peak_inflight": st["peak_inflight"], "peak_bytes": st["peak_bytes"]}
 
 
@@ -549,7 +550,7 @@ def run_serving(args):
     from paper_2310_10750_gb300 import build as pkg_build
     pkg_build.build()
     from paper_2310_10750_gb300 import mfmc
-    sv = serving_metrics(mfmc, args.requests)
+    sv = serving_metrics(mfmc, args.requests, args.load)
     line = {"metric": "p50/p99 solve latency (serving)", "value": sv["p99_latency_s"], "unit": "s (p99)",
             "higher_is_better": False, "data": "synthetic", "config": {"workload": sv["workload"]}}
     line.update({k: v for k, v in sv.items() if k != "workload"})
@@ -862,6 +863,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="headline only: skip the serving, per-fidelity and MFMC measurements")
     ap.add_argument("--requests", type=int, default=20000, help="serving: requests in the stream")
+    ap.add_argument("--load", type=float, default=0.8, help="serving: arrival rate over the measured capacity")
     ap.add_argument("--beta2", type=float, default=0.0, help="paper: beta2 of the nine models (the paper's 0.05)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
