@@ -130,3 +130,32 @@ def test_trace_argument_checks_on_host(lib):
     assert mfmc._L.mfmc_trace_enable((1 << 28) + 1) == mfmc.MFMC_EINVAL
     assert "2^28" in mfmc.mfmc_last_error()
     assert mfmc._L.mfmc_trace_read(None, 5, None, None) == mfmc.MFMC_EINVAL
+
+
+STRUCTS = ["mfmc_model_desc", "mfmc_sample_params", "mfmc_model_info", "mfmc_plan_t", "mfmc_server_stats",
+           "mfmc_trace_record"]
+
+
+def test_binding_struct_layouts_match_the_header(lib, tmp_path):
+    # The ctypes mirrors of the boundary's structs must have the C compiler's size and field
+    # offsets for include/mfmc.h (a field added, dropped or reordered on one side only would
+    # shift every field after it).  Compiled as C by gcc on the host, no GPU.
+    _, mf = lib
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "mfmc.h"', 'int main(void) {']
+    for s in STRUCTS:
+        lines.append(f'    printf("{s} %zu\\n", sizeof({s}));')
+        for name, _ in getattr(mf, s)._fields_:
+            lines.append(f'    printf("{s}.{name} %zu\\n", offsetof({s}, {name}));')
+    lines += ['    return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)],
+                   check=True, capture_output=True, text=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    for s in STRUCTS:
+        cls = getattr(mf, s)
+        assert int(got[s]) == ctypes.sizeof(cls), s
+        for name, _ in cls._fields_:
+            assert int(got[f"{s}.{name}"]) == getattr(cls, name).offset, (s, name)
