@@ -159,3 +159,19 @@ def test_binding_struct_layouts_match_the_header(lib, tmp_path):
         assert int(got[s]) == ctypes.sizeof(cls), s
         for name, _ in cls._fields_:
             assert int(got[f"{s}.{name}"]) == getattr(cls, name).offset, (s, name)
+
+
+def test_binding_signatures_match_the_header(lib):
+    # every entry point the header declares has a binding whose argument count and return
+    # kind (status, void, string) are the declaration's
+    _, mf = lib
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    decls = re.findall(r"(mfmc_status|void|const char\s*\*)\s*(mfmc_\w+)\s*\(([^;{]*?)\)\s*;", text)
+    assert sorted(d[1] for d in decls) == declared_functions()
+    for ret, name, params in decls:
+        p = params.strip()
+        nargs = 0 if p in ("", "void") else p.count(",") + 1
+        f = getattr(mf._L, name)
+        assert f.argtypes is not None and len(f.argtypes) == nargs, name
+        want = {"mfmc_status": ctypes.c_int, "void": None}.get(ret, ctypes.c_char_p)
+        assert f.restype is want, (name, f.restype)
