@@ -379,7 +379,7 @@ def _seeds(base, count, offset=0):
 
 
 def _batched_cost(mfmc, model, ns, seed_base):
-    """GPU seconds per sample of a batched solve (fields built on the device), and the OoIs."""
+    """GPU seconds per sample of a batched solve (fields built on the device)."""
     import numpy as np
     import torch
     n = model.n
@@ -558,17 +558,39 @@ def run_serving(args):
     return 0
 
 
+def fidelity_roofline(mfmc, n, algo, pts_per_s, peak_gbs, sm_max):
+    """Fractions of a fidelity's step roofline: the HBM term (algorithmic bytes per point-step at
+    the measured copy bandwidth: 8 B of field for the streamed disc-sum kernels; the half
+    spectrum read and written by both passes plus the field for the streamed spectral form;
+    none for the forms that keep the whole solve on chip) and the ALU term in units of the
+    prefix form's 4R + 9 instructions per point against 152 SMs x 128 FP32 lanes."""
+    R = n // 32
+    on_chip = algo == mfmc.ALGO_RESIDENT or (algo == mfmc.ALGO_SPECTRAL and n <= 128)
+    if algo == mfmc.ALGO_SPECTRAL and not on_chip:
+        bytes_pt = (4 * n * (n // 2 + 1) * 8 + 2 * n * n * 4) / (n * n)
+    else:
+        bytes_pt = 8.0
+    return {"hbm_frac": None if on_chip else pts_per_s * bytes_pt / (peak_gbs * 1e9),
+            "hbm_bytes_per_point_step": None if on_chip else bytes_pt,
+            "alu_frac_prefix_model": pts_per_s * (4 * R + 9) / (152 * 128 * sm_max * 1e6)}
+
+
 def fidelity_rates(mfmc):
     """Batched samples/s of each fidelity of the serving mix (delta = 1/32: n = 64 .. 1024,
-    R = n/32, 1000 steps, smoothed-noise IC), each batch large enough to fill the GPU."""
+    R = n/32, 1000 steps, smoothed-noise IC), each batch large enough to fill the GPU, with the
+    fractions of its step roofline."""
+    peak_gbs, sm_max, _ = load_peaks()
     base = 20231016 + 1000003 * 6
     out = {}
     for n, bs in ((64, 4096), (128, 2048), (256, 512), (512, 128), (1024, 64)):
         m = mfmc.Model(n=n, delta=(n // 32) / n, eps=0.02, eps_lo=0.016, eps_hi=0.024, tau=1e-3, nsteps=1000,
                        ic=mfmc.IC_SMOOTHED_GAUSS, ic_amp=0.05)
         c = _batched_cost(mfmc, m, bs, base)
-        out[f"{n}x{n}_R{n // 32}"] = {"samples_per_s": 1.0 / c, "batch": bs, "algo": m.info().algo,
-                                      "grid_pt_updates_per_s": n * n * 1000 / c}
+        algo = m.info().algo
+        pps = n * n * 1000 / c
+        out[f"{n}x{n}_R{n // 32}"] = {"samples_per_s": 1.0 / c, "batch": bs, "algo": algo,
+                                      "grid_pt_updates_per_s": pps,
+                                      "roofline": fidelity_roofline(mfmc, n, algo, pps, peak_gbs, sm_max)}
     return out
 
 
