@@ -365,7 +365,12 @@ def run_ours(args):
             line["cpu_baseline"], sols = cpu_baseline()
             line["oracle_check"] = oracle_check(mfmc, sols, algo_req)
         if not args.no_extras and ws == 1:
-            line.update(extra_metrics(mfmc, model, algo_req, ns, ms_step, args))
+            # the metric's other parts run after the headline is measured; a failure among them
+            # is reported in the line instead of losing the line
+            try:
+                line.update(extra_metrics(mfmc, model, algo_req, ns, ms_step, args))
+            except Exception as e:  # noqa: BLE001
+                line["extras_error"] = f"{type(e).__name__}: {e}"
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
