@@ -96,3 +96,45 @@ def test_argument_errors(mf):
         mf.mfmc_plan_from_stats(rho, sigma, C, 0.5)                       # below one f_1 sample
     assert e.value.status == mf.MFMC_EBUDGET
     assert mf._L.mfmc_plan_from_stats(2, None, None, None, 1.0, 0, None, 0, None) == mf.MFMC_EINVAL
+
+
+def test_random_hierarchies_match_the_oracle(mf):
+    # statistics the ordering and feasibility rules have to sort out: models in any order,
+    # correlations of either sign (only rho^2 orders them), costs that do not fall with
+    # rho^2 (infeasible subsets), equal |rho| (ties broken by model index), and budgets
+    # from below one high-fidelity sample to far above B_min, through every policy
+    rng = np.random.default_rng(2310)
+    checked = below = 0
+    for case in range(240):
+        K = int(rng.integers(2, 10))
+        rho = rng.uniform(0.2, 0.9999, K) * rng.choice([-1.0, 1.0], K)
+        if case % 7 == 0:
+            rho[int(rng.integers(1, K))] = -rho[int(rng.integers(1, K))]    # an exact |rho| tie
+        rho[0] = 1.0
+        sigma = rng.uniform(0.1, 3.0, K)
+        C = np.concatenate([[1.0], rng.uniform(1e-4, 0.8, K - 1)])
+        if not M.enumerate_subsets(list(rho), list(C))[1]:
+            # no surrogate subset meets Eq. (conditionb): nothing to select (the paper is
+            # silent; the library reports it as MFMC_EBUDGET)
+            with pytest.raises(mf.MfmcError) as e:
+                mf.mfmc_plan_from_stats(rho, sigma, C, 1e5, 0)
+            assert e.value.status == mf.MFMC_EBUDGET and "no feasible" in mf.mfmc_last_error()
+            continue
+        for B in (0.5, 1.5, 3.0, 20.0, 500.0, 1e5):
+            for policy in (0, 1, 2):
+                ref = M.select(list(rho), list(sigma), list(C), B, policy=policy)
+                if ref is None:
+                    with pytest.raises(mf.MfmcError) as e:
+                        mf.mfmc_plan_from_stats(rho, sigma, C, B, policy)
+                    assert e.value.status == mf.MFMC_EBUDGET, (case, B, policy)
+                    continue
+                same_plan(mf.mfmc_plan_from_stats(rho, sigma, C, B, policy).as_dict(), ref)
+                checked += 1
+                below += ref.below_min_budget
+        # an explicit subset of f_1 and at least one surrogate, in the order of Eq. (conditiona)
+        pick = set(int(i) for i in rng.choice(np.arange(1, K), size=int(rng.integers(1, K)), replace=False))
+        sub = [i for i in M.order_models(list(rho)) if i == 0 or i in pick]
+        ref = M.select(list(rho), list(sigma), list(C), 1e4, policy=3, explicit=sub)
+        if ref is not None:
+            same_plan(mf.mfmc_plan_from_stats(rho, sigma, C, 1e4, 3, explicit=sub).as_dict(), ref)
+    assert checked > 2000 and below > 50
