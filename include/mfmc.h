@@ -79,9 +79,10 @@ typedef enum {
     MFMC_ALGO_PLAIN = 5,       /* reference form: one sample per launch, direct   */
     MFMC_ALGO_PREFIX_TMA = 6,  /* prefix form, persistent CTAs, TMA double-buffered
                                   tiles of a ghost-framed field                   */
-    MFMC_ALGO_ROWS = 7         /* row streaming: each warp streams a 128-column strip down
-                                  its share of the batch's rows through its own TMA chunk
-                                  ring; a lane owns 4 columns and keeps a ring of 2R+1
+    MFMC_ALGO_ROWS = 7         /* row streaming: one CTA per SM walks its share of the
+                                  batch's rows (groups of 2048/n samples) down through a ring of
+                                  TMA chunks of whole rows; a warp takes a 128-column strip
+                                  of one sample, a lane 4 columns with a ring of 2R+1
                                   accumulators, every staged row summed once per segment
                                   (constant kernel, R in {2,4,6,8}, n % 128 == 0)  */,
     MFMC_ALGO_FFT = 8          /* spectral form of the disc sum: cuFFT transforms (a library,
