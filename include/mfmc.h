@@ -243,10 +243,11 @@ mfmc_status mfmc_model_set_iteration_limits(mfmc_model *model, int newton_max, i
  * (for measurements and tests).  MFMC_EINVAL for an unknown variant. */
 mfmc_status mfmc_model_set_tile_variant(mfmc_model *model, int variant);
 
-/* Pin the work split of the row-streaming kernel: rows = rows per work range (>= 8; ranges
- * are taken in (sample, strip, row) order, warp w owning ranges w, w + W, ...), or 0 for the
- * batch's rows split evenly over the resident warps (the default); columns_per_thread must
- * be 4.  MFMC_EINVAL otherwise. */
+/* Pin the work split of the row-streaming kernel: rows = rows per work range (>= 8; the
+ * batch's rows, in (sample group, row) order, cut into ranges of that many rows that the CTAs
+ * take in turn: CTA c owns ranges c, c + G, ...), or 0 for the rows split evenly over the
+ * resident CTAs, halo rows counted (the default); columns_per_thread must be 4.  MFMC_EINVAL
+ * otherwise. */
 mfmc_status mfmc_model_set_band_height(mfmc_model *model, int rows, int columns_per_thread);
 
 /* Host-side resolution of each sample's eps (model eps, eps range draw, or
