@@ -385,7 +385,9 @@ mfmc_status mfmc_pilot_stats(int K, int n, const double *ooi_dev, double *mean,
  * below-minimum-budget branch of Section 4; 1 smallest V regardless of B_min (Case 1);
  * 2 smallest B_min (Case 3); 3 the explicit subset (explicit_idx[0..explicit_len-1],
  * starting with 0).  Returns MFMC_EBUDGET when no subset fits B (the Section 4
- * requirement B >= sum_l l C_{i_l}). */
+ * requirement B >= sum_l l C_{i_l}), and when no subset with a surrogate meets
+ * Eq. (conditionb) (policies 0-2: nothing to select).  With K = 1 the plan is plain Monte
+ * Carlo. */
 mfmc_status mfmc_plan(int K, int n_pilot, const double *pilot_ooi, const double *costs,
                       double budget, int policy, const int *explicit_idx, int explicit_len,
                       mfmc_plan_t *out);
